@@ -1,0 +1,163 @@
+"""Seeded synthetic workloads: problem set-ups and initial data.
+
+This module holds no arithmetic of the time-integration method or of the
+spatial discretization.  It describes the workloads (PDE, domain, element
+grids, polynomial degrees, collocation node sets, time step rule) and
+evaluates closed-form initial data at node coordinates that the caller
+supplies.  The same functions feed both the CUDA library and the CPU
+oracle, so both see bit-identical inputs.
+
+Random numbers come from numpy's PCG64 generator with seed
+2504185260 + workload id.
+"""
+import math
+
+import numpy as np
+
+SEED_BASE = 2504185260
+
+
+def rng_for(workload_id, extra=0):
+    return np.random.default_rng(SEED_BASE + int(workload_id) + 1000 * int(extra))
+
+
+# ---------------------------------------------------------------------------
+# Workload descriptions (the five synthetic set-ups)
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    # 1D linear convection-diffusion, exact damped/shifted Fourier modes
+    "convdiff1d": dict(
+        id=1, pde="convdiff", dim=1, ncomp=1, adv=(1.0, 0.0), nu=0.01,
+        lo=(0.0, 0.0), hi=(2 * math.pi, 0.0),
+        levels=[dict(nel=(16, 1), P=2, M=3), dict(nel=(16, 1), P=4, M=5)],
+        nodes="lobatto", dt=0.05, nsteps=40, ncycles=4, start="cascade"),
+    # 2D viscous Burgers, 2 components, 32x32 elements, P = 7
+    "burgers2d": dict(
+        id=2, pde="burgers", dim=2, ncomp=2, nu=5e-3,
+        lo=(0.0, 0.0), hi=(1.0, 1.0),
+        levels=[dict(nel=(32, 32), P=3, M=3), dict(nel=(32, 32), P=7, M=5)],
+        nodes="radau_right", cfl=0.5, nsteps=100, ncycles=3, start="cascade",
+        fourier_K=4, fourier_amp=0.05),
+    # 2D Euler isentropic vortex, 64x64 elements, P = 7/5/3
+    "euler_vortex": dict(
+        id=3, pde="euler", dim=2, ncomp=4, gamma=1.4,
+        lo=(-10.0, -10.0), hi=(10.0, 10.0),
+        levels=[dict(nel=(64, 64), P=3, M=2), dict(nel=(64, 64), P=5, M=3),
+                dict(nel=(64, 64), P=7, M=5)],
+        nodes="lobatto", cfl=0.5, nsteps=200, ncycles=3, start="fmg1",
+        vortex_beta=5.0, mach=0.5, angle_deg=45.0),
+}
+
+
+# ---------------------------------------------------------------------------
+# Closed-form initial data
+# ---------------------------------------------------------------------------
+def convdiff1d_exact(X, t, nu=0.01, a=1.0):
+    """u = e^{-nu t} sin(x - a t) + 0.5 e^{-9 nu t} sin(3 (x - a t))."""
+    return (np.exp(-nu * t) * np.sin(X - a * t)
+            + 0.5 * np.exp(-9.0 * nu * t) * np.sin(3.0 * (X - a * t)))[None]
+
+
+def fourier_modes(rng, K, ncomp):
+    """All integer (kx, ky) != 0 with |k| <= K; per component a, b ~ U[-1, 1]."""
+    modes = []
+    for kx in range(-K, K + 1):
+        for ky in range(-K, K + 1):
+            if (kx, ky) == (0, 0) or kx * kx + ky * ky > K * K:
+                continue
+            a = rng.uniform(-1.0, 1.0, size=ncomp)
+            b = rng.uniform(-1.0, 1.0, size=ncomp)
+            modes.append((kx, ky, a, b))
+    return modes
+
+
+def eval_fourier(modes, X, Y, amp, ncomp):
+    out = np.zeros((ncomp,) + X.shape)
+    for kx, ky, a, b in modes:
+        ph = 2.0 * math.pi * (kx * X + ky * Y)
+        c, s = np.cos(ph), np.sin(ph)
+        for q in range(ncomp):
+            out[q] += amp * (a[q] * c + b[q] * s)
+    return out
+
+
+def burgers2d_initial(X, Y, seed_extra=0, K=4, amp=0.05):
+    base = np.stack([np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y),
+                     -np.cos(2 * math.pi * X) * np.sin(2 * math.pi * Y)])
+    modes = fourier_modes(rng_for(2, seed_extra), K, 2)
+    return base + eval_fourier(modes, X, Y, amp, 2)
+
+
+def isentropic_vortex(X, Y, t=0.0, gamma=1.4, beta=5.0, mach=0.5, angle_deg=45.0,
+                      lo=(-10.0, -10.0), hi=(10.0, 10.0)):
+    """Conserved variables of the isentropic vortex translated by v_inf t on
+    the periodic box (free stream rho = p = 1, |v_inf| = Mach * sqrt(gamma))."""
+    vinf = mach * math.sqrt(gamma)
+    ang = math.radians(angle_deg)
+    vx0, vy0 = vinf * math.cos(ang), vinf * math.sin(ang)
+    Lx, Ly = hi[0] - lo[0], hi[1] - lo[1]
+    # vortex centre at the origin at t = 0, moved by v_inf t, wrapped
+    xc = (0.0 + vx0 * t - lo[0]) % Lx + lo[0]
+    yc = (0.0 + vy0 * t - lo[1]) % Ly + lo[1]
+    dx = (X - xc + Lx / 2) % Lx - Lx / 2
+    dy = (Y - yc + Ly / 2) % Ly - Ly / 2
+    r2 = dx * dx + dy * dy
+    f = beta / (2 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    vx = vx0 - dy * f
+    vy = vy0 + dx * f
+    T = 1.0 - (gamma - 1.0) * beta ** 2 / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    E = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy)
+    return np.stack([rho, rho * vx, rho * vy, E])
+
+
+def max_wave_speed(pde, u, gamma=1.4, adv=(1.0, 0.0)):
+    """Largest characteristic speed of the initial data (sets dt from CFL)."""
+    if pde == "convdiff":
+        return max(abs(adv[0]), abs(adv[1]))
+    if pde == "burgers":
+        return float(2.0 * np.max(np.abs(u)))
+    if pde == "euler":
+        rho = u[0]
+        vx, vy = u[1] / rho, u[2] / rho
+        p = (gamma - 1.0) * (u[3] - 0.5 * rho * (vx * vx + vy * vy))
+        c = np.sqrt(gamma * p / rho)
+        return float(max(np.max(np.abs(vx) + c), np.max(np.abs(vy) + c)))
+    raise ValueError(pde)
+
+
+def cfl_dt(cfl, h_elem, P, speed):
+    """dt = CFL * dx / lam_max with dx = h_e / (2 delta), delta = P^2
+    (the CFL definition of the numerical experiments, Sec. 8)."""
+    return cfl * (h_elem / (2.0 * P * P)) / speed
+
+
+def initial_state(name, X, Y, seed_extra=0):
+    w = WORKLOADS[name]
+    if name == "convdiff1d":
+        return convdiff1d_exact(X, 0.0, w["nu"], w["adv"][0])
+    if name == "burgers2d":
+        return burgers2d_initial(X, Y, seed_extra, w["fourier_K"], w["fourier_amp"])
+    if name == "euler_vortex":
+        return isentropic_vortex(X, Y, 0.0, w["gamma"], w["vortex_beta"], w["mach"],
+                                 w["angle_deg"], w["lo"], w["hi"])
+    raise ValueError(name)
+
+
+def scaled(name, nel=None, P=None, levels=None):
+    """A copy of a workload with a different element grid (all levels) and/or
+    level list, for small parity cases."""
+    import copy
+    w = copy.deepcopy(WORKLOADS[name])
+    if levels is not None:
+        w["levels"] = levels
+    if nel is not None:
+        for lv in w["levels"]:
+            lv["nel"] = tuple(nel)
+    return w
+
+
+def random_field(shape, seed, scale=1.0):
+    """Seeded smooth-free random nodal data for operator-level parity tests."""
+    return scale * np.random.default_rng(SEED_BASE + 77 + int(seed)).standard_normal(shape)
