@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark: fine-level DOF-sweeps/s of SI-MLSDC time steps on GB300.
+
+Workload (default): 2D viscous Burgers, 2 components, periodic [0,1]^2,
+nu = 5e-3, 32x32 elements, fine P = 7 / coarse P = 3, Radau-Right 5/3
+collocation nodes, SI(2), Cascade start, 3 V-cycles + final fine post-sweep
+per step (4 fine sweeps), dt from CFL 0.5.  One "step" = one time step
+through the C ABI (sisdc_step): every row of the hot path runs in it.
+
+Output: one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (bounded samples of the same workload).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fine-level DOF-sweeps/s"
+UNIT = "DOF-sweeps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sisdc", choices=["sisdc", "reference"])
+    ap.add_argument("--workload", default="burgers2d")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cg-rtol", type=float, default=1e-12)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="8x8 elements (profiling case)")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2504_18526_gb300 import inputs
+    w = inputs.scaled(args.workload, nel=(8, 8) if args.small else None)
+    return w
+
+
+def fine_dofs(w):
+    lv = w["levels"][-1]
+    nq = lv["P"] + 1
+    n = lv["nel"][0] * (lv["nel"][1] if w["dim"] == 2 else 1) * nq ** w["dim"]
+    return n * w["ncomp"]
+
+
+def initial_data(w, X, Y):
+    from paper_2504_18526_gb300 import inputs
+    name = [k for k, v in inputs.WORKLOADS.items() if v["id"] == w["id"]][0]
+    u0 = inputs.initial_state(name, X, Y)
+    lv = w["levels"][-1]
+    h = (w["hi"][0] - w["lo"][0]) / lv["nel"][0]
+    if "cfl" in w:
+        dt = inputs.cfl_dt(w["cfl"], h, lv["P"], inputs.max_wave_speed(w["pde"], u0, w.get("gamma", 1.4),
+                                                                          w.get("adv", (1, 0))))
+    else:
+        dt = w["dt"]
+    return u0, dt
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle sample (run in a single-threaded child process)
+# ---------------------------------------------------------------------------
+def oracle_sample(args):
+    import numpy as np
+    from tests.helpers import oracle_ml
+    w = workload(args)
+    om = oracle_ml(w, rtol=args.cg_rtol)
+    sp = om.levels[-1].space
+    X, Y = sp.coords()
+    u0, dt = initial_data(w, X, Y)
+    ncyc = w["ncycles"]
+    reps = max(1, args.steps)
+    t0 = time.perf_counter()
+    u = u0
+    for _ in range(reps):
+        u = om.step(u, dt, ncyc, start=w["start"])
+    el = time.perf_counter() - t0
+    sweeps = ncyc + 1
+    print(json.dumps({"seconds": el, "steps": reps, "dof_sweeps": fine_dofs(w) * sweeps * reps,
+                      "finite": bool(np.all(np.isfinite(u)))}))
+
+
+def run_oracle_child(args, steps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--steps", str(steps),
+           "--workload", args.workload, "--cg-rtol", str(args.cg_rtol)] + (["--small"] if args.small else [])
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    for _ in range(args.warmup):
+        run_oracle_child(args, 1)
+    tot_s, tot_d = 0.0, 0
+    for _ in range(args.steps):
+        r = run_oracle_child(args, 1)
+        tot_s += r["seconds"]
+        tot_d += r["dof_sweeps"]
+    v = tot_d / tot_s
+    sample = "%d oracle time steps (1 per bench step) of the %s workload, FP64 numpy, 1 thread" % (
+        args.steps, args.workload)
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": args.workload, "fine_dofs": fine_dofs(w), "levels": w["levels"],
+                      "fine_sweeps_per_step": w["ncycles"] + 1},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "cpu": cpu_model()},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel):
+    """dram bytes per launch from a committed ncu summary, if it matches the
+    current kernel source (hash line)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel)
+    src = os.path.join(ROOT, "paper_2504_18526_gb300", "csrc", "ops_sipg.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for ln in open(path):
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != h:
+            return None, None
+        return float(kv["dram_bytes_per_node_iter"]), float(kv.get("dram_bytes_per_launch_fixed_per_node", 0))
+    except Exception:
+        return None, None
+
+
+# PCG kernel algorithmic bytes (FP64): per node, setup = read rhs terms
+# (nterms, 5 on average in a sweep) + x, write r: ~7 streams; per iteration
+# the minimal CG traffic of 7 streams (read p, x, r, Ap, write Ap, x, r, p
+# fused as in standard CG accounting) -> 7 * 8 bytes per node and iteration.
+PCG_ITER_STREAMS = 7
+PCG_SETUP_STREAMS = 7
+
+
+def main_arm(args):
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import sisdc as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        from paper_2504_18526_gb300.build import build
+        build()
+    if dist:
+        dist.barrier()
+    S.load()
+
+    w = workload(args)
+    prec = S.SISDC_MIXED if args.precision == "mixed" else S.SISDC_FP64
+    stream = torch.cuda.Stream(device=dev)
+    use_graph = 0 if args.no_graph else 1
+    ctx = S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
+                    use_graph=use_graph)
+    nc, n, M = ctx.info(-1)
+    hx, hy = np.zeros(n), np.zeros(n)
+    S.sisdc_level_coords(ctx.levels[-1], hx, hy)
+    lv = w["levels"][-1]
+    shp = (lv["nel"][1] if w["dim"] == 2 else 1, lv["nel"][0], lv["P"] + 1 if w["dim"] == 2 else 1, lv["P"] + 1)
+    u0, dt = initial_data(w, hx.reshape(shp), hy.reshape(shp))
+    start = S.START_IDS[w["start"]]
+    ncyc = w["ncycles"]
+    nv = nc * n
+    dofs_per_step = nv * (ncyc + 1)
+    du = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    torch.cuda.synchronize()
+
+    def step(u):
+        S.sisdc_step(ctx.ctx, u, 0.0, dt, ncyc, start, 1)
+
+    for _ in range(args.warmup):
+        step(du)
+    S.sisdc_sync(ctx.ctx)
+    S.sisdc_reset_stats(ctx.ctx)
+
+    # ---- timed region: K steps, L2 flushed between steps -------------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        evs[k][0].record(stream)
+        step(du)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    S.sisdc_sync(ctx.ctx)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    stats = S.sisdc_get_stats(ctx.ctx)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * dofs_per_step * args.steps / (ms * 1e-3)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region --
+    h_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_e2e = torch.empty_like(du)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ke = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t_e2e = 0.0
+    for k in range(ke):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            d_e2e.copy_(h_in, non_blocking=True)
+        S.sisdc_step(ctx.ctx, d_e2e, 0.0, dt, ncyc, start, 1)
+        with torch.cuda.stream(stream):
+            h_out.copy_(d_e2e, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e += e0.elapsed_time(e1)
+    S.sisdc_sync(ctx.ctx)
+    e2e_val = world * dofs_per_step * ke / (t_e2e * 1e-3)
+    ctx.close()
+
+    # ---- dominant kernel: live CUDA-event timing of the PCG launches (eager) --
+    kctx = S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
+                     use_graph=0)
+    dk = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+    for _ in range(2):
+        S.sisdc_step(kctx.ctx, dk, 0.0, dt, ncyc, start, 1)
+    S.sisdc_sync(kctx.ctx)
+    S.sisdc_reset_stats(kctx.ctx)
+    S.sisdc_set_kernel_timing(kctx.ctx, True, len(w["levels"]) - 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        S.sisdc_step(kctx.ctx, dk, 0.0, dt, ncyc, start, 1)
+    kt = S.sisdc_get_kernel_timing(kctx.ctx)
+    eager_s = time.perf_counter() - t0
+    kstats = S.sisdc_get_stats(kctx.ctx)
+    S.sisdc_sync(kctx.ctx)
+    kctx.close()
+    launches_per_step = kstats["launches"] / args.steps
+    hbm_peak, peak_kind = measured_peaks()
+    alg_bytes = 8.0 * (PCG_SETUP_STREAMS * nv * kt["launches"] + PCG_ITER_STREAMS * kt["nodes_x_iters"])
+    per_launch_bytes = alg_bytes / max(1, kt["launches"])
+    avg_ms = kt["ms"] / max(1, kt["launches"])
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    tr_iter, tr_fixed = profile_traffic("k_pcg")
+    traffic = None
+    if tr_iter is not None:
+        traffic = (tr_fixed * nv * kt["launches"] + tr_iter * kt["nodes_x_iters"]) / max(1, kt["launches"])
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            r = run_oracle_child(args, 1 if not args.small else 3)
+            cpu = {"value": r["dof_sweeps"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "%d full time step(s) of the %s workload by the FP64 numpy oracle "
+                             "(single-threaded BLAS), %.1f s" % (r["steps"], args.workload, r["seconds"]),
+                   "cpu": cpu_model()}
+        except Exception as e:   # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == S.SISDC_FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + (" (8x8 elements)" if args.small else ""),
+                   "fine_dofs": nv, "levels": w["levels"], "nodes": w["nodes"], "dt": dt,
+                   "ncycles": ncyc, "fine_sweeps_per_step": ncyc + 1, "start": w["start"],
+                   "si_stages": 2, "cg_rtol": args.cg_rtol, "cuda_graph": bool(use_graph),
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_pcg (fine level)", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "avg_launch_us": avg_ms * 1e3,
+                     "launches": kt["launches"], "avg_iters": kt["iters"] / max(1, kt["launches"]),
+                     "kernel_share_of_step": kt["ms"] / max(1e-9, eager_s * 1e3)},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nv * 8, "d2h_bytes_per_step": nv * 8},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "cg": {"solves_per_step": stats["cg_solves"] / args.steps,
+               "iters_per_solve": stats["cg_iters"] / max(1, stats["cg_solves"]),
+               "max_iters": stats["cg_max_iters"]},
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.oracle_sample:
+        oracle_sample(a)
+    elif a.impl == "reference":
+        reference_arm(a)
+    else:
+        main_arm(a)

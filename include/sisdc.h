@@ -1,0 +1,232 @@
+/*
+ * sisdc.h -- C ABI of the GB300 (sm_103a) semi-implicit multilevel SDC library.
+ *
+ * The library advances a system of conservation laws
+ *     d_t u = f(u) = -div F_c(u) + (diffusion)                  (Sec. 2)
+ * discretised by DG-SEM on periodic uniform meshes (Sec. 6) with the
+ * semi-implicit multilevel spectral deferred correction method SI-MLSDC
+ * (Sec. 3-4): incremental SI(1)/SI(2) sweeps over the collocation nodes
+ * (Sec. 3.3, Algorithm 1), FAS coupling of space-time levels (Sec. 4.1,
+ * eq. ml-cm:incremental:fas-mg:rhs), V-cycles (Algorithm 2) and Cascade/FMG
+ * starts (Algorithms 3-4).  Every arithmetic step runs in CUDA kernels on
+ * the GPU; there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * State layout.  A solution on one level is a double array
+ *     u[c][e][j][i]      c < ncomp, e = ey*nel_x + ex, j < NQY, i < NQ
+ * with NQ = P+1 GLL nodes per direction (i fastest), NQY = NQ in 2D and 1
+ * in 1D; N = nel * NQ * NQY nodes per component, NV = ncomp * N values.
+ * An array over the collocation nodes m = 1..M of a level is U[m-1][NV]
+ * (the node t_0 is not stored; u_0 is passed separately, Sec. 3.1).
+ *
+ * Memory.  Pointers named d_* are DEVICE pointers on the current CUDA
+ * device, owned by the caller, and must stay valid until the work queued
+ * on the context stream has finished.  Pointers named h_* are HOST
+ * pointers, read or written synchronously.  Level work arrays are owned by
+ * the library (cudaMalloc at sisdc_create_level, freed by sisdc_destroy).
+ *
+ * Streams and errors.  All device work is queued on the stream given to
+ * sisdc_create and runs asynchronously; calls return after queuing.  Every
+ * entry point returns a sisdc_status; on failure a message is available from
+ * sisdc_last_error.  Conditions detected on the device (a CG solve that hit
+ * its iteration cap, a non-finite residual, a grid-barrier timeout) are
+ * recorded in a device flag and reported by the next sisdc_sync.  No C++
+ * exception crosses the ABI.
+ */
+#ifndef SISDC_H
+#define SISDC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sisdc_ctx_s* sisdc_ctx;
+typedef struct sisdc_level_s* sisdc_level;
+
+typedef enum {
+    SISDC_OK = 0,
+    SISDC_E_ARG = -1,       /* invalid argument                                  */
+    SISDC_E_CUDA = -2,      /* CUDA runtime error                                */
+    SISDC_E_NOCONV = -3,    /* an implicit solve reached cg_maxit                */
+    SISDC_E_TIMEOUT = -4,   /* a bounded device wait gave up                     */
+    SISDC_E_NONFINITE = -5, /* NaN/Inf met in a solve                            */
+    SISDC_E_OOM = -6,       /* device allocation failed                          */
+    SISDC_E_STATE = -7      /* call out of order (e.g. no level created)         */
+} sisdc_status;
+
+/* Collocation node sets (Sec. 3.1). */
+typedef enum { SISDC_RADAU_RIGHT = 0, SISDC_LOBATTO = 1 } sisdc_nodes;
+
+/* PDEs (Sec. 2 and the workloads): scalar convection-diffusion with constant
+ * velocity adv, two-component viscous Burgers with flux u (x) u, 2D
+ * compressible Euler with a perfect gas of ratio gamma. */
+typedef enum {
+    SISDC_PDE_CONVDIFF = 0,
+    SISDC_PDE_BURGERS = 1,
+    SISDC_PDE_EULER = 2
+} sisdc_pde;
+
+/* SISDC_FP64: every step in FP64.  SISDC_MIXED: operator applications and
+ * CG matvecs in FP32; SDC residual, S.F quadrature, FAS tau, CG inner
+ * products and the iterative-refinement residual of the implicit solve in
+ * FP64.  Inputs and outputs are FP64 in both modes. */
+typedef enum { SISDC_FP64 = 0, SISDC_MIXED = 1 } sisdc_precision;
+
+/* Start strategies (Sec. 4.7): constant spread of u_0, predictor on all
+ * levels, Cascade (Algorithm 3), FMG with one cycle per added level
+ * (Algorithm 4; identical to Cascade for two levels). */
+typedef enum {
+    SISDC_START_SPREAD = 0,
+    SISDC_START_PREDICTOR = 1,
+    SISDC_START_CASCADE = 2,
+    SISDC_START_FMG1 = 3
+} sisdc_start;
+
+/* One space-time level Q_l = Omega_l x T_l (Sec. 6.1): a periodic box
+ * [lo, hi] split into nel[0] x nel[1] equal elements (nel[1] = 1 in 1D) of
+ * degree P (1..8) and M collocation nodes (1..8; >= 2 for Lobatto). */
+typedef struct {
+    int dim;
+    int nel[2];
+    int P;
+    int M;
+    int nodes;          /* sisdc_nodes */
+    double lo[2];
+    double hi[2];
+} sisdc_level_desc;
+
+typedef struct {
+    int pde;            /* sisdc_pde                                          */
+    int ncomp;          /* must match the PDE: 1, 2 or 4                      */
+    double nu;          /* diffusivity nu (convdiff, Burgers)                 */
+    double gamma;       /* ratio of specific heats (Euler)                    */
+    double adv[2];      /* convection velocity (convdiff)                     */
+    int precision;      /* sisdc_precision                                    */
+    int si_stages;      /* 1 = SI(1), 2 = SI(2)  (Sec. 3.3)                   */
+    double cg_rtol;     /* relative tolerance of the implicit solves          */
+    int cg_maxit;       /* iteration cap of the implicit solves               */
+    int Nc;             /* coarse sweeps per V-cycle (Algorithm 2; default 2) */
+    int use_graph;      /* 1: sisdc_step replays a captured CUDA graph        */
+} sisdc_problem;
+
+typedef struct {
+    long long cg_solves;     /* implicit solves                               */
+    long long cg_iters;      /* CG iterations summed over solves              */
+    long long cg_max_iters;  /* largest iteration count of one solve          */
+    long long cg_noconv;     /* solves that stopped at cg_maxit               */
+    long long ir_steps;      /* iterative-refinement steps (SISDC_MIXED)      */
+    long long sweeps[8];     /* correction/predictor sweeps per level index   */
+    long long launches;      /* kernels launched by the library               */
+} sisdc_stats;
+
+/* --- context and levels --------------------------------------------------- */
+
+/* Create a context bound to the current CUDA device and to the CUDA stream
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * problem struct is copied.  SISDC_E_ARG for an inconsistent problem. */
+sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ctx* out);
+void sisdc_destroy(sisdc_ctx ctx);
+
+/* Add a level (Sec. 6.1).  Levels must be added from coarse (l = 1) to fine
+ * (l = L); adjacent levels must share the element grid (p-coarsening in
+ * space, Sec. 6.2) and node kind (p-coarsening in time).  Work arrays are
+ * allocated here (SISDC_E_OOM on failure).  The handle lives until
+ * sisdc_destroy. */
+sisdc_status sisdc_create_level(sisdc_ctx ctx, const sisdc_level_desc* desc, sisdc_level* out);
+
+/* Sizes of a level: components, nodes per component N, collocation nodes M. */
+sisdc_status sisdc_level_info(sisdc_level lv, int* ncomp, long long* nodes, int* M);
+
+/* Physical coordinates of the level's GLL nodes in the state layout
+ * (h_x, h_y: host arrays of N doubles; h_y may be NULL in 1D). */
+sisdc_status sisdc_level_coords(sisdc_level lv, double* h_x, double* h_y);
+
+/* The library's own tables for this level (host arrays, each may be NULL):
+ * collocation nodes tau[M] on [0,1]; node-to-node weights
+ * w^nn[M*M] (Sec. 3.2, eq. nn_weights, row m = node); GLL nodes gll[NQ],
+ * weights w[NQ] and differentiation matrix D[NQ*NQ] (row-major). */
+sisdc_status sisdc_level_tables(sisdc_level lv, double* h_tau, double* h_wnn,
+                                double* h_gll, double* h_w, double* h_D);
+
+/* --- single operators (for verification and external drivers) ------------- */
+
+/* d_c = c(d_u) = -div F_c(u): strong-form DG-SEM convective operator with a
+ * Rusanov (local Lax-Friedrichs) face flux (Sec. 2, Sec. 6). */
+sisdc_status sisdc_apply_conv(sisdc_level lv, const double* d_u, double* d_c);
+
+/* d_Lu = L d_u with L = -M^{-1} A, A the SIPG stiffness (per component). */
+sisdc_status sisdc_apply_lap(sisdc_level lv, const double* d_u, double* d_Lu);
+
+/* Solve (I - c L) x = rhs, i.e. (M + c A) x = M rhs, by Jacobi-preconditioned
+ * CG; d_x holds the initial guess on entry and the solution on exit.  The
+ * iteration count is written to *h_iters (synchronises the stream) when
+ * h_iters is not NULL. */
+sisdc_status sisdc_solve(sisdc_level lv, double c, const double* d_rhs, double* d_x, int* h_iters);
+
+/* --- the method ------------------------------------------------------------ */
+
+/* SI(1)/SI(2) predictor sweep (Sec. 3.3, eqs. sdc:incremental_predictor_si1
+ * and _si2): fills d_U[M][NV] from d_u0[NV] over the slab of length dt. */
+sisdc_status sisdc_predict(sisdc_level lv, const double* d_u0, double* d_U, double dt);
+
+/* nsweeps incremental SI-MLSDC correction sweeps (Algorithm 1,
+ * eq. ml-sdc:incremental) on d_U[M][NV] in place, with FAS right-hand side
+ * d_g[M][NV] (NULL = 0).  Each call starts from f(d_U) of its input. */
+sisdc_status sisdc_sweep(sisdc_level lv, const double* d_u0, double* d_U, const double* d_g,
+                         double dt, int nsweeps);
+
+/* FAS residual d_r = g - F^nn(U) (Sec. 4.3, eq. MLSDC:incremental:residual),
+ * F^nn_m(U) = U_m - U_{m-1} - dt sum_i w^nn_{m,i} f(U_i), U_0 = u_0. */
+sisdc_status sisdc_residual(sisdc_level lv, const double* d_u0, const double* d_U,
+                            const double* d_g, double dt, double* d_r);
+
+/* Space-time transfer between a level and the next finer one (Sec. 4.2,
+ * Sec. 6.2).  op: 0 = interpolation I (coarse d_in[Mc] -> fine d_out[Mf]),
+ * 1 = solution projection P (fine -> coarse, embedded interpolation),
+ * 2 = residual restriction R = I^T (fine -> coarse), 3 = projection of one
+ * state in space only (fine d_in[NV_f] -> coarse d_out[NV_c]). */
+sisdc_status sisdc_transfer(sisdc_level fine, sisdc_level coarse, int op,
+                            const double* d_in, double* d_out);
+
+/* One MLSDC V-cycle (Algorithm 2) over all levels of the context with N_c
+ * coarse sweeps.  The finest level's iterate d_U[M][NV] (and its initial
+ * value d_u0) are caller-owned; coarse levels use library storage. */
+sisdc_status sisdc_vcycle(sisdc_ctx ctx, const double* d_u0, double* d_U, double dt, int Nc);
+
+/* One time step of length dt (Sec. 4.7): start strategy `start`
+ * (sisdc_start), ncycles V-cycles, and a final fine post-sweep when
+ * post_sweep != 0; d_u[NV] (finest level) holds u(t) on entry and
+ * u(t+dt) = u_{L,M} on exit.  With a single level this is single-level SDC:
+ * predictor plus ncycles sweeps.  t is the time at the start of the step
+ * (unused by the autonomous PDEs supported here). */
+sisdc_status sisdc_step(sisdc_ctx ctx, double* d_u, double t, double dt, int ncycles,
+                        int start, int post_sweep);
+
+/* Wait for the context stream; report device-side conditions (NOCONV,
+ * TIMEOUT, NONFINITE) recorded since the previous sisdc_sync and clear them. */
+sisdc_status sisdc_sync(sisdc_ctx ctx);
+
+/* Counters since creation or the last reset (synchronises the stream). */
+sisdc_status sisdc_get_stats(sisdc_ctx ctx, sisdc_stats* out);
+sisdc_status sisdc_reset_stats(sisdc_ctx ctx);
+
+/* Measurement hook.  When enabled (eager mode only: use_graph = 0), every
+ * launch of the implicit-solve kernel on level index `level` (-1 = all
+ * levels) is bracketed by CUDA events on the context stream and its CG
+ * iteration count is recorded.  sisdc_get_kernel_timing synchronises the
+ * stream, returns the summed kernel time in ms, the number of timed
+ * launches, their summed iterations and sum(iterations * NV of the level),
+ * and restarts the count. */
+sisdc_status sisdc_set_kernel_timing(sisdc_ctx ctx, int enable, int level);
+sisdc_status sisdc_get_kernel_timing(sisdc_ctx ctx, double* h_ms_total, long long* h_launches,
+                                     long long* h_iters, long long* h_nodes_x_iters);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* sisdc_last_error(sisdc_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SISDC_H */

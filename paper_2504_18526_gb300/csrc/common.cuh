@@ -1,0 +1,160 @@
+// Internal device helpers shared by the SI-MLSDC kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sisdc {
+
+constexpr int NQMAX = 9;      // P <= 8
+constexpr int MMAX = 8;       // collocation nodes per level
+constexpr int MAXTERMS = 8;   // terms of a fused linear combination
+
+// Device error codes (mirrors sisdc_status, stored as a positive flag bitmask).
+enum DevErr : int { DEV_NOCONV = 1, DEV_TIMEOUT = 2, DEV_NONFINITE = 4 };
+
+// Stats slots (long long).
+enum StatSlot : int { ST_SOLVES = 0, ST_ITERS = 1, ST_MAXIT = 2, ST_NOCONV = 3, ST_IR = 4, ST_N = 8 };
+
+// A coefficient a = a0 + a2 * lam^2, lam read from device memory when given.
+// Used for the nu_tilde-dependent factors dt_m nu_tilde(u) with
+// nu_tilde = nu_d + dt_m/2 * lam_max(u)^2.
+struct Coef {
+    double a0;
+    double a2;
+    const double* lam;
+};
+
+__device__ __forceinline__ double coef_value(const Coef& c) {
+    double v = c.a0;
+    if (c.lam) { double l = *c.lam; v += c.a2 * l * l; }
+    return v;
+}
+
+// Geometry and tables of one level, passed by value.
+struct Geo {
+    int dim, nq, nqy, q;          // nodes per direction / per element
+    int nex, ney, nel, ncomp;
+    long long N;                  // nodes per component = nel * q
+    double hx, hy;                // element sizes
+    double taux, tauy;            // SIPG penalties 2 (P+1)^2 / h
+    const double* D;              // [nq*nq] d l_j/dxi at xi_i (device)
+    const double* K;              // [nq*nq] D^T W D (device)
+    const double* w;              // [nq] GLL weights (device)
+    const double* dline_x;        // [nq] diagonal of the 1D SIPG line operator (x)
+    const double* dline_y;        // [nq] (y)
+};
+
+// Deterministic block reduction (fixed shuffle tree, fixed warp order).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum over the block; result valid in thread 0. `scratch` >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? scratch[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? scratch[lane] : 0.0;
+        r = warp_max(r);
+    }
+    return r;
+}
+
+// Max of non-negative doubles through their bit patterns (monotone for x >= 0).
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    if (!(v >= 0.0)) v = __longlong_as_double(0x7ff8000000000000LL);   // NaN marks trouble
+    atomicMax(reinterpret_cast<unsigned long long*>(addr),
+              static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for cooperative launches with a bounded wait.
+// count/gen live in device memory (zero-initialised once).  On timeout the
+// block records DEV_TIMEOUT in *err and returns false; callers then leave
+// the kernel, so that every wait in the grid ends.
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == nb - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (*vgen == g) {
+                if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                    atomicOr(err, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok && ((*(volatile int*)err & DEV_TIMEOUT) == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum of gridDim.x partials in a fixed order; every block gets the same bits.
+__device__ __forceinline__ double grid_total(const double* partials, double* scratch) {
+    __shared__ double s_tot;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+            v += *((volatile const double*)(partials + b));
+        v = warp_sum(v);
+        if (threadIdx.x == 0) s_tot = v;
+    }
+    __syncthreads();
+    const double r = s_tot;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace sisdc

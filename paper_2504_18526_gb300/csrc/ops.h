@@ -1,0 +1,97 @@
+// Internal launch interface of the SI-MLSDC kernels (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace sisdc {
+
+// ---- SIPG diffusion (ops_sipg.cu) -------------------------------------------
+enum ApplyMode : int { APPLY_A = 0, APPLY_LAP = 1, APPLY_LAP_F = 2, APPLY_OP = 3 };
+
+struct ApplyArgs {
+    Geo g;
+    const double* u;
+    const double* tr;     // traces of u (from launch_traces)
+    double* out;
+    double* out2;         // APPLY_LAP_F: F = cc + nu * Lu
+    const double* cc;
+    double nu;
+    Coef c;               // APPLY_OP: Mass u + c A u
+    int mode;
+};
+
+struct PCGArgs {
+    Geo g;
+    double* x;            // initial guess in, solution out
+    double* r;
+    double* p;
+    double* Ap;
+    double* trx;          // trace buffer for x
+    double* trp;          // trace buffer for p
+    int nterms;           // right-hand side b = sum_t coef_t * in_t (nodal)
+    const double* in[MAXTERMS];
+    Coef coef[MAXTERMS];
+    Coef cimp;            // system (M + c A) x = M b
+    double* part;         // 4 * gridDim partial sums
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* err;
+    long long* stats;
+    double rtol;
+    int maxit;
+    int* iters_out;       // iteration count of this solve (nullable)
+};
+
+cudaError_t launch_traces(const Geo& g, const double* u, double* tr, cudaStream_t s);
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+// Grid size for the cooperative PCG kernel of this geometry (0 if unsupported).
+int pcg_grid(const Geo& g, int* block);
+cudaError_t launch_pcg(const PCGArgs& a, int grid, int block, cudaStream_t s);
+
+// ---- convective operator (ops_conv.cu) -------------------------------------
+enum ConvMode : int { CONV_OUT = 0, CONV_DELTA = 1 };
+
+struct ConvArgs {
+    Geo g;
+    int pde;              // sisdc_pde
+    double gamma;
+    double ax, ay;
+    const double* u;
+    double* out;          // c(u) (CONV_OUT, or also in CONV_DELTA when not null)
+    double* cache;        // CONV_DELTA: delta = c - cache; cache = c
+    double* delta;
+    double* lam;          // max spectral radius (atomic max), may be null
+    int mode;
+};
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s);
+
+// ---- elementwise and transfer kernels (ops_misc.cu) -------------------------
+struct LinArgs {          // out[idx] = sum_t coef_t * in_t[idx], idx < n
+    long long n;
+    int nterms;
+    const double* in[MAXTERMS];
+    Coef coef[MAXTERMS];
+    double* out;
+};
+cudaError_t launch_lincomb(const LinArgs& a, cudaStream_t s);
+
+// Q[m] = dt * sum_i W[m][i] F[i] for m < M (arrays of n values)
+cudaError_t launch_quad(const double* F, double* Q, const double* W, int M, double dt,
+                        long long n, cudaStream_t s);
+
+// r[m] = (g ? g[m] : 0) - (U[m] - U[m-1] - Q[m]),  U[-1] = u0   (sign = +1)
+// r[m] = U[m] - U[m-1] - Q[m]                                     (sign = 0, g ignored)
+cudaError_t launch_fnn(const double* u0, const double* U, const double* Q, const double* g,
+                       double* r, int M, long long n, int residual, cudaStream_t s);
+
+struct TransferArgs {
+    int dim, nqi, nqo, Mi, Mo, ncomp, nel;
+    const double* S;      // [nqo*nqi] per-direction space matrix (device)
+    const double* Tt;     // [Mo*Mi] time matrix (device)
+    const double* in;     // [Mi][ncomp][nel][nqi^dim]
+    double* out;          // [Mo][ncomp][nel][nqo^dim]
+    int add;              // out += instead of out =
+};
+cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s);
+
+}  // namespace sisdc

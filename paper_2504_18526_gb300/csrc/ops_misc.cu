@@ -1,0 +1,138 @@
+// Elementwise SDC kernels and space-time transfers (sm_103a).
+//
+// * lincomb: fused right-hand sides of the SI sweeps (Sec. 3.3, Sec. 4.3).
+// * quad:    the S.F product Q_m = dt sum_i w^nn_{m,i} F_i for all m at once
+//            (Sec. 3.2, eq. cm:incremental), FP64 accumulation.
+// * fnn:     F^nn_m(U) = U_m - U_{m-1} - Q_m (eq. cm:incremental:op) and the
+//            FAS residual r = g - F^nn(U) (eq. MLSDC:incremental:residual).
+// * transfer: I, P, R = I^T as (space (x) space) (x) time tensor products
+//            applied per element (Sec. 4.2, Sec. 6.2).
+#include "ops.h"
+
+namespace sisdc {
+
+static inline unsigned ew_grid(long long n, int bs) {
+    long long g = (n + bs - 1) / bs;
+    if (g > 152LL * 32) g = 152LL * 32;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+__global__ void k_lincomb(const __grid_constant__ LinArgs a) {
+    __shared__ double sc[MAXTERMS];
+    if (threadIdx.x < MAXTERMS) sc[threadIdx.x] = threadIdx.x < a.nterms ? coef_value(a.coef[threadIdx.x]) : 0.0;
+    __syncthreads();
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int t = 0; t < a.nterms; ++t) v += sc[t] * a.in[t][idx];
+        a.out[idx] = v;
+    }
+}
+
+cudaError_t launch_lincomb(const LinArgs& a, cudaStream_t s) {
+    k_lincomb<<<ew_grid(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+struct QuadArgs {
+    const double* F;
+    double* Q;
+    double W[MMAX * MMAX];
+    int M;
+    double dt;
+    long long n;
+};
+
+__global__ void k_quad(const __grid_constant__ QuadArgs a) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double f[MMAX];
+        for (int i = 0; i < a.M; ++i) f[i] = a.F[i * a.n + idx];
+        for (int m = 0; m < a.M; ++m) {
+            double s = 0.0;
+            for (int i = 0; i < a.M; ++i) s += a.W[m * a.M + i] * f[i];
+            a.Q[m * a.n + idx] = a.dt * s;
+        }
+    }
+}
+
+cudaError_t launch_quad(const double* F, double* Q, const double* W, int M, double dt, long long n,
+                        cudaStream_t s) {
+    QuadArgs a;
+    a.F = F;
+    a.Q = Q;
+    for (int t = 0; t < M * M; ++t) a.W[t] = W[t];
+    a.M = M;
+    a.dt = dt;
+    a.n = n;
+    k_quad<<<ew_grid(n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_fnn(const double* u0, const double* U, const double* Q, const double* g, double* r,
+                      int M, long long n, int residual) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double prev = u0[idx];
+        for (int m = 0; m < M; ++m) {
+            const double cur = U[m * n + idx];
+            const double fnn = cur - prev - Q[m * n + idx];
+            r[m * n + idx] = residual ? ((g ? g[m * n + idx] : 0.0) - fnn) : fnn;
+            prev = cur;
+        }
+    }
+}
+
+cudaError_t launch_fnn(const double* u0, const double* U, const double* Q, const double* g, double* r,
+                       int M, long long n, int residual, cudaStream_t s) {
+    k_fnn<<<ew_grid(n, 256), 256, 0, s>>>(u0, U, Q, g, r, M, n, residual);
+    return cudaGetLastError();
+}
+
+__global__ void k_transfer(const TransferArgs a) {
+    __shared__ double sS[NQMAX * NQMAX];
+    __shared__ double sT[MMAX * MMAX];
+    for (int t = threadIdx.x; t < a.nqo * a.nqi; t += blockDim.x) sS[t] = a.S[t];
+    for (int t = threadIdx.x; t < a.Mo * a.Mi; t += blockDim.x) sT[t] = a.Tt[t];
+    __syncthreads();
+    const int qi = a.dim == 2 ? a.nqi * a.nqi : a.nqi;
+    const int qo = a.dim == 2 ? a.nqo * a.nqo : a.nqo;
+    const long long nvi = (long long)a.ncomp * a.nel * qi;
+    const long long nvo = (long long)a.ncomp * a.nel * qo;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nvo;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long ec = idx / qo;
+        const int node = (int)(idx - ec * qo);
+        const int io = node % a.nqo, jo = node / a.nqo;
+        double sp[MMAX];
+        for (int n = 0; n < a.Mi; ++n) {
+            const double* in = a.in + n * nvi + ec * qi;
+            double s = 0.0;
+            if (a.dim == 2) {
+                for (int b = 0; b < a.nqi; ++b) {
+                    double t = 0.0;
+                    for (int c = 0; c < a.nqi; ++c) t += sS[io * a.nqi + c] * in[b * a.nqi + c];
+                    s += sS[jo * a.nqi + b] * t;
+                }
+            } else {
+                for (int c = 0; c < a.nqi; ++c) s += sS[io * a.nqi + c] * in[c];
+            }
+            sp[n] = s;
+        }
+        for (int m = 0; m < a.Mo; ++m) {
+            double v = 0.0;
+            for (int n = 0; n < a.Mi; ++n) v += sT[m * a.Mi + n] * sp[n];
+            double* o = a.out + m * nvo + idx;
+            *o = a.add ? *o + v : v;
+        }
+    }
+}
+
+cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s) {
+    const int qo = a.dim == 2 ? a.nqo * a.nqo : a.nqo;
+    k_transfer<<<ew_grid((long long)a.ncomp * a.nel * qo, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sisdc

@@ -1,0 +1,900 @@
+// Host orchestration and C ABI of the SI-MLSDC library.
+//
+// All arithmetic runs in the kernels of ops_*.cu; this file queues them on
+// the context stream in the order of the method:
+//   sweep     Algorithm 1 with the SI(1)/SI(2) deltas (Sec. 3.3, Sec. 4.3)
+//   predictor eqs. sdc:incremental_predictor_si1/_si2
+//   vcycle    Algorithm 2 (FAS right-hand side, eq. ml-cm:incremental:fas-mg:rhs)
+//   start     Algorithms 3 (Cascade) and 4 (FMG, one cycle per added level)
+// The cached f, c and L u of the previous sweep (Sec. 3.3 implementation
+// remark) live in per-level device arrays; the nu_tilde factors are read by
+// the kernels from device-side spectral-radius slots, so a whole time step
+// is queued without a host synchronisation and can be captured as one CUDA
+// graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sisdc.h"
+#include "ops.h"
+#include "tables.h"
+
+using namespace sisdc;
+
+struct sisdc_level_s {
+    sisdc_ctx_s* ctx = nullptr;
+    int index = 0;
+    sisdc_level_desc desc{};
+    LevelTables tab;
+    Geo geo{};
+    int nq = 0, nqy = 0, Q = 0, M = 0, nel = 0;
+    long long N = 0, NV = 0;
+    double* d_tab = nullptr;
+    double* d_mem = nullptr;
+    // state and caches
+    double *U = nullptr, *u0 = nullptr;
+    double *F = nullptr, *CC = nullptr, *LU = nullptr, *Qb = nullptr, *G = nullptr, *V = nullptr, *R = nullptr;
+    double *c0 = nullptr, *dC = nullptr, *tmpc = nullptr;
+    double *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *trx = nullptr, *trp = nullptr;
+    double* lam = nullptr;      // [2][MMAX+1]: old, new spectral radius slots
+    int pcg_grid = 0, pcg_block = 0;
+    bool valid = false;         // caches match (u0, U)
+    const double* cache_u0 = nullptr;
+    const double* cache_U = nullptr;
+    // transfers to the next coarser level
+    double *d_Ix = nullptr, *d_Px = nullptr, *d_Rx = nullptr;
+    double *d_It = nullptr, *d_Pt = nullptr, *d_Rt = nullptr, *d_one = nullptr;
+};
+
+struct sisdc_ctx_s {
+    sisdc_problem prob{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;   // created when graphs are requested on the NULL stream
+    std::vector<sisdc_level_s*> levels;
+    // kernel timing (measurement hook): events around implicit-solve launches
+    bool timing = false;
+    int timing_level = -1;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_level;
+    size_t ev_used = 0;
+    int* d_iters = nullptr;              // iterations of each timed launch
+    size_t iters_cap = 0;
+    unsigned* d_bar = nullptr;
+    int* d_err = nullptr;
+    long long* d_stats = nullptr;
+    double* d_part = nullptr;
+    int max_grid = 0;
+    std::string err;
+    long long launches = 0;
+    long long sweeps[8] = {0};
+    // captured step
+    cudaGraphExec_t gexec = nullptr;
+    double* g_u = nullptr;
+    double g_dt = 0.0;
+    int g_ncycles = -1, g_start = -1, g_post = -1;
+};
+
+namespace {
+
+struct Fail {
+    sisdc_status st;
+};
+
+void check(sisdc_ctx_s* c, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        throw Fail{SISDC_E_CUDA};
+    }
+}
+
+sisdc_status fail(sisdc_ctx_s* c, sisdc_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+double nu_d(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER ? 0.0 : p.nu; }
+double nu_phys(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER ? 0.0 : p.nu; }
+
+double* lam_old(sisdc_level_s* lv, int slot) { return lv->lam + slot; }
+double* lam_new(sisdc_level_s* lv, int slot) { return lv->lam + (MMAX + 1) + slot; }
+
+double* Um(sisdc_level_s* lv, double* U, int m) { return U + (long long)m * lv->NV; }
+const double* Um(sisdc_level_s* lv, const double* U, int m) { return U + (long long)m * lv->NV; }
+
+// ---- kernel wrappers ---------------------------------------------------------
+void k_conv(sisdc_level_s* lv, const double* u, double* out, double* lam, int mode = CONV_OUT,
+            double* cache = nullptr, double* delta = nullptr) {
+    sisdc_ctx_s* c = lv->ctx;
+    ConvArgs a{};
+    a.g = lv->geo;
+    a.pde = c->prob.pde;
+    a.gamma = c->prob.gamma;
+    a.ax = c->prob.adv[0];
+    a.ay = c->prob.adv[1];
+    a.u = u;
+    a.out = out;
+    a.cache = cache;
+    a.delta = delta;
+    a.lam = lam;
+    a.mode = mode;
+    check(c, launch_conv(a, c->stream), "conv kernel");
+    c->launches++;
+}
+
+void k_lap(sisdc_level_s* lv, const double* u, double* out, int mode, double* out2 = nullptr,
+           const double* cc = nullptr, Coef cf = Coef{0.0, 0.0, nullptr}) {
+    sisdc_ctx_s* c = lv->ctx;
+    check(c, launch_traces(lv->geo, u, lv->trx, c->stream), "trace kernel");
+    ApplyArgs a{};
+    a.g = lv->geo;
+    a.u = u;
+    a.tr = lv->trx;
+    a.out = out;
+    a.out2 = out2;
+    a.cc = cc;
+    a.nu = nu_phys(c->prob);
+    a.c = cf;
+    a.mode = mode;
+    check(c, launch_apply(a, c->stream), "SIPG apply kernel");
+    c->launches += 2;
+}
+
+struct Terms {
+    int n = 0;
+    const double* in[MAXTERMS];
+    Coef cf[MAXTERMS];
+    void add(const double* p, double a0, double a2 = 0.0, const double* lam = nullptr) {
+        in[n] = p;
+        cf[n] = Coef{a0, a2, lam};
+        ++n;
+    }
+};
+
+void k_pcg(sisdc_level_s* lv, double* x, const Terms& t, Coef cimp) {
+    sisdc_ctx_s* c = lv->ctx;
+    PCGArgs a{};
+    a.g = lv->geo;
+    a.x = x;
+    a.r = lv->cg_r;
+    a.p = lv->cg_p;
+    a.Ap = lv->cg_Ap;
+    a.trx = lv->trx;
+    a.trp = lv->trp;
+    a.nterms = t.n;
+    for (int q = 0; q < t.n; ++q) {
+        a.in[q] = t.in[q];
+        a.coef[q] = t.cf[q];
+    }
+    a.cimp = cimp;
+    a.part = c->d_part;
+    a.bar_count = c->d_bar;
+    a.bar_gen = c->d_bar + 1;
+    a.err = c->d_err;
+    a.stats = c->d_stats;
+    a.rtol = c->prob.cg_rtol;
+    a.maxit = c->prob.cg_maxit;
+    a.iters_out = nullptr;
+    const bool timed = c->timing && (c->timing_level < 0 || c->timing_level == lv->index);
+    if (timed) {
+        const size_t k = c->ev_used / 2;
+        if (c->ev_used + 2 > c->ev.size()) {
+            for (int q = 0; q < 2; ++q) {
+                cudaEvent_t e;
+                check(c, cudaEventCreate(&e), "event create");
+                c->ev.push_back(e);
+            }
+        }
+        if (k >= c->iters_cap) {
+            const size_t cap = c->iters_cap ? 2 * c->iters_cap : 1024;
+            int* p = nullptr;
+            check(c, cudaStreamSynchronize(c->stream), "sync");
+            check(c, cudaMalloc(&p, cap * sizeof(int)), "timing buffer");
+            if (c->d_iters) {
+                check(c, cudaMemcpy(p, c->d_iters, c->iters_cap * sizeof(int), cudaMemcpyDeviceToDevice), "copy");
+                cudaFree(c->d_iters);
+            }
+            c->d_iters = p;
+            c->iters_cap = cap;
+        }
+        a.iters_out = c->d_iters + k;
+        c->ev_level.push_back(lv->index);
+        check(c, cudaEventRecord(c->ev[c->ev_used], c->stream), "event record");
+    }
+    check(c, launch_pcg(a, lv->pcg_grid, lv->pcg_block, c->stream), "PCG kernel");
+    if (timed) {
+        check(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream), "event record");
+        c->ev_used += 2;
+    }
+    c->launches++;
+}
+
+void k_lin(sisdc_level_s* lv, double* out, const Terms& t, long long n = -1) {
+    LinArgs a{};
+    a.n = n < 0 ? lv->NV : n;
+    a.nterms = t.n;
+    for (int q = 0; q < t.n; ++q) {
+        a.in[q] = t.in[q];
+        a.coef[q] = t.cf[q];
+    }
+    a.out = out;
+    check(lv->ctx, launch_lincomb(a, lv->ctx->stream), "lincomb kernel");
+    lv->ctx->launches++;
+}
+
+void copy_d2d(sisdc_level_s* lv, double* dst, const double* src, long long n) {
+    if (dst == src) return;
+    check(lv->ctx, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, lv->ctx->stream),
+          "device copy");
+}
+
+// transfer between lv (fine) and its coarser level
+enum { T_INTERP = 0, T_PROJECT = 1, T_RESTRICT = 2, T_PROJECT_SPACE = 3 };
+void k_transfer(sisdc_level_s* fine, int op, const double* in, double* out, int add) {
+    sisdc_level_s* coarse = fine->ctx->levels[fine->index - 1];
+    TransferArgs a{};
+    a.dim = fine->desc.dim;
+    a.ncomp = fine->ctx->prob.ncomp;
+    a.nel = fine->nel;
+    a.in = in;
+    a.out = out;
+    a.add = add;
+    switch (op) {
+        case T_INTERP:
+            a.nqi = coarse->nq; a.nqo = fine->nq; a.Mi = coarse->M; a.Mo = fine->M;
+            a.S = fine->d_Ix; a.Tt = fine->d_It;
+            break;
+        case T_PROJECT:
+            a.nqi = fine->nq; a.nqo = coarse->nq; a.Mi = fine->M; a.Mo = coarse->M;
+            a.S = fine->d_Px; a.Tt = fine->d_Pt;
+            break;
+        case T_RESTRICT:
+            a.nqi = fine->nq; a.nqo = coarse->nq; a.Mi = fine->M; a.Mo = coarse->M;
+            a.S = fine->d_Rx; a.Tt = fine->d_Rt;
+            break;
+        default:
+            a.nqi = fine->nq; a.nqo = coarse->nq; a.Mi = 1; a.Mo = 1;
+            a.S = fine->d_Px; a.Tt = fine->d_one;
+            break;
+    }
+    check(fine->ctx, launch_transfer(a, fine->ctx->stream), "transfer kernel");
+    fine->ctx->launches++;
+}
+
+Coef cimp_coef(sisdc_level_s* lv, double dtm, const double* lam) {
+    return Coef{dtm * nu_d(lv->ctx->prob), 0.5 * dtm * dtm, lam};
+}
+
+// ---- method building blocks ----------------------------------------------------
+// Caches f(U_m), c(U_m), L U_m, c(u0) and the spectral-radius slots of (u0, U).
+void refresh(sisdc_level_s* lv, const double* u0, const double* U) {
+    sisdc_ctx_s* c = lv->ctx;
+    check(c, cudaMemsetAsync(lv->lam, 0, 2 * (MMAX + 1) * sizeof(double), c->stream), "memset");
+    k_conv(lv, u0, lv->c0, lam_old(lv, 0));
+    for (int m = 0; m < lv->M; ++m) {
+        k_conv(lv, Um(lv, U, m), Um(lv, lv->CC, m), lam_old(lv, m + 1));
+        k_lap(lv, Um(lv, U, m), Um(lv, lv->LU, m), APPLY_LAP_F, Um(lv, lv->F, m), Um(lv, lv->CC, m));
+    }
+    copy_d2d(lv, lam_new(lv, 0), lam_old(lv, 0), 1);
+    lv->valid = true;
+    lv->cache_u0 = u0;
+    lv->cache_U = U;
+}
+
+void sweep(sisdc_level_s* lv, const double* u0, double* U, const double* G, double dt, int nsweeps) {
+    sisdc_ctx_s* c = lv->ctx;
+    if (!lv->valid || lv->cache_u0 != u0 || lv->cache_U != U) refresh(lv, u0, U);
+    const int stages = c->prob.si_stages;
+    const double nd = nu_d(c->prob);
+    for (int k = 0; k < nsweeps; ++k) {
+        check(c, launch_quad(lv->F, lv->Qb, lv->tab.wnn.data(), lv->M, dt, lv->NV, c->stream), "quad kernel");
+        c->launches++;
+        check(c, cudaMemsetAsync(lam_new(lv, 1), 0, lv->M * sizeof(double), c->stream), "memset");
+        for (int m = 0; m < lv->M; ++m) {
+            const double dtm = dt * lv->tab.dtau[m];
+            const double* uprev = m ? Um(lv, (const double*)U, m - 1) : u0;
+            double* um = Um(lv, U, m);
+            Terms base;
+            base.add(uprev, 1.0);
+            base.add(Um(lv, lv->Qb, m), 1.0);
+            if (G) base.add(Um(lv, G, m), 1.0);
+            if (dtm == 0.0) {
+                k_lin(lv, um, base);
+            } else {
+                // old term -H part: -dt_m nu_tilde(u^{k-1}_{m-1}) L u^{k-1}_m
+                base.add(Um(lv, lv->LU, m), -dtm * nd, -0.5 * dtm * dtm, lam_old(lv, m));
+                const Coef cimp = cimp_coef(lv, dtm, lam_new(lv, m));
+                Terms t1 = base;
+                if (m > 0) t1.add(lv->dC, dtm);     // c(u^k_{m-1}) - c(u^{k-1}_{m-1})
+                k_pcg(lv, um, t1, cimp);
+                if (stages == 2) {
+                    k_conv(lv, um, lv->tmpc, nullptr);
+                    Terms t2 = base;
+                    t2.add(lv->tmpc, dtm);                  // c(u^(1))
+                    t2.add(Um(lv, lv->CC, m), -dtm);        // c(u^{k-1}_m)
+                    k_pcg(lv, um, t2, cimp);
+                }
+            }
+            k_conv(lv, um, nullptr, lam_new(lv, m + 1), CONV_DELTA, Um(lv, lv->CC, m), lv->dC);
+            k_lap(lv, um, Um(lv, lv->LU, m), APPLY_LAP_F, Um(lv, lv->F, m), Um(lv, lv->CC, m));
+        }
+        copy_d2d(lv, lam_old(lv, 1), lam_new(lv, 1), lv->M);
+        if (lv->index < 8) c->sweeps[lv->index]++;
+    }
+    lv->valid = true;
+    lv->cache_u0 = u0;
+    lv->cache_U = U;
+}
+
+void predict(sisdc_level_s* lv, const double* u0, double* U, double dt) {
+    sisdc_ctx_s* c = lv->ctx;
+    const int stages = c->prob.si_stages;
+    check(c, cudaMemsetAsync(lv->lam, 0, 2 * (MMAX + 1) * sizeof(double), c->stream), "memset");
+    k_conv(lv, u0, lv->c0, lam_new(lv, 0));
+    for (int m = 0; m < lv->M; ++m) {
+        const double dtm = dt * lv->tab.dtau[m];
+        const double* uprev = m ? Um(lv, (const double*)U, m - 1) : u0;
+        const double* cprev = m ? Um(lv, (const double*)lv->CC, m - 1) : lv->c0;
+        double* um = Um(lv, U, m);
+        copy_d2d(lv, um, uprev, lv->NV);
+        if (dtm != 0.0) {
+            const Coef cimp = cimp_coef(lv, dtm, lam_new(lv, m));
+            Terms t;
+            t.add(uprev, 1.0);
+            t.add(cprev, dtm);
+            k_pcg(lv, um, t, cimp);
+            if (stages == 2) {
+                k_conv(lv, um, lv->tmpc, nullptr);
+                Terms t2;
+                t2.add(uprev, 1.0);
+                t2.add(lv->tmpc, dtm);
+                k_pcg(lv, um, t2, cimp);
+            }
+        }
+        k_conv(lv, um, Um(lv, lv->CC, m), lam_new(lv, m + 1));
+        k_lap(lv, um, Um(lv, lv->LU, m), APPLY_LAP_F, Um(lv, lv->F, m), Um(lv, lv->CC, m));
+    }
+    copy_d2d(lv, lam_old(lv, 0), lam_new(lv, 0), lv->M + 1);
+    if (lv->index < 8) c->sweeps[lv->index]++;
+    lv->valid = true;
+    lv->cache_u0 = u0;
+    lv->cache_U = U;
+}
+
+// r = G - F^nn(U) (G may be null); needs valid caches
+void residual(sisdc_level_s* lv, const double* u0, const double* U, const double* G, double dt, double* r) {
+    sisdc_ctx_s* c = lv->ctx;
+    if (!lv->valid || lv->cache_u0 != u0 || lv->cache_U != U) refresh(lv, u0, U);
+    check(c, launch_quad(lv->F, lv->Qb, lv->tab.wnn.data(), lv->M, dt, lv->NV, c->stream), "quad kernel");
+    check(c, launch_fnn(u0, U, lv->Qb, G, r, lv->M, lv->NV, 1, c->stream), "fnn kernel");
+    c->launches += 2;
+}
+
+struct LevelPtrs {
+    std::vector<const double*> u0;
+    std::vector<double*> U;
+};
+
+// Algorithm 2 on levels 0..top-1 (top-1 acts as the finest level, g = 0).
+void vcycle(sisdc_ctx_s* c, LevelPtrs& P, int top, double dt, int Nc) {
+    std::vector<sisdc_level_s*>& L = c->levels;
+    for (int l = top - 1; l >= 1; --l) {
+        sisdc_level_s* f = L[l];
+        sisdc_level_s* cl = L[l - 1];
+        const double* Gf = (l == top - 1) ? nullptr : f->G;
+        sweep(f, P.u0[l], P.U[l], Gf, dt, 1);                                  // pre-sweep
+        residual(f, P.u0[l], P.U[l], Gf, dt, f->R);                            // r_l = g_l - F_l(u_l)
+        k_transfer(f, T_PROJECT, P.U[l], P.U[l - 1], 0);                        // v_{l-1} = P u_l
+        copy_d2d(cl, cl->V, P.U[l - 1], (long long)cl->M * cl->NV);
+        refresh(cl, P.u0[l - 1], P.U[l - 1]);
+        check(c, launch_quad(cl->F, cl->Qb, cl->tab.wnn.data(), cl->M, dt, cl->NV, c->stream), "quad kernel");
+        check(c, launch_fnn(P.u0[l - 1], P.U[l - 1], cl->Qb, nullptr, cl->G, cl->M, cl->NV, 0, c->stream),
+              "fnn kernel");
+        c->launches += 2;
+        k_transfer(f, T_RESTRICT, f->R, cl->G, 1);                             // g_{l-1} += R r_l
+    }
+    sweep(L[0], P.u0[0], P.U[0], top > 1 ? L[0]->G : nullptr, dt, Nc);        // coarse solve
+    for (int l = 1; l < top; ++l) {
+        sisdc_level_s* f = L[l];
+        sisdc_level_s* cl = L[l - 1];
+        Terms d;
+        d.add(P.U[l - 1], 1.0);
+        d.add(cl->V, -1.0);
+        k_lin(cl, cl->R, d, (long long)cl->M * cl->NV);                         // u_{l-1} - v_{l-1}
+        k_transfer(f, T_INTERP, cl->R, P.U[l], 1);                              // u_l += I(...)
+        f->valid = false;
+        if (l < top - 1) sweep(f, P.u0[l], P.U[l], f->G, dt, 1);              // post-sweep
+    }
+}
+
+void start_strategy(sisdc_ctx_s* c, LevelPtrs& P, double dt, int start) {
+    std::vector<sisdc_level_s*>& L = c->levels;
+    const int nl = (int)L.size();
+    if (start == SISDC_START_CASCADE || start == SISDC_START_FMG1) {
+        predict(L[0], P.u0[0], P.U[0], dt);
+        sweep(L[0], P.u0[0], P.U[0], nullptr, dt, 1);
+        if (nl > 1) {
+            k_transfer(L[1], T_INTERP, P.U[0], P.U[1], 0);
+            L[1]->valid = false;
+        }
+        for (int l = 1; l < nl - 1; ++l) {
+            if (start == SISDC_START_FMG1) vcycle(c, P, l + 1, dt, c->prob.Nc);
+            else sweep(L[l], P.u0[l], P.U[l], nullptr, dt, 1);
+            k_transfer(L[l + 1], T_INTERP, P.U[l], P.U[l + 1], 0);
+            L[l + 1]->valid = false;
+        }
+    } else if (start == SISDC_START_PREDICTOR) {
+        for (int l = 0; l < nl; ++l) predict(L[l], P.u0[l], P.U[l], dt);
+    } else {
+        for (int l = 0; l < nl; ++l) {
+            for (int m = 0; m < L[l]->M; ++m) copy_d2d(L[l], Um(L[l], P.U[l], m), P.u0[l], L[l]->NV);
+            L[l]->valid = false;
+        }
+    }
+}
+
+void enqueue_step(sisdc_ctx_s* c, double* d_u, double dt, int ncycles, int start, int post) {
+    std::vector<sisdc_level_s*>& L = c->levels;
+    const int nl = (int)L.size();
+    sisdc_level_s* fine = L[nl - 1];
+    LevelPtrs P;
+    P.u0.resize(nl);
+    P.U.resize(nl);
+    copy_d2d(fine, fine->u0, d_u, fine->NV);
+    for (int l = 0; l < nl; ++l) {
+        P.u0[l] = L[l]->u0;
+        P.U[l] = L[l]->U;
+        L[l]->valid = false;
+    }
+    for (int l = nl - 1; l >= 1; --l) k_transfer(L[l], T_PROJECT_SPACE, L[l]->u0, L[l - 1]->u0, 0);
+    if (nl == 1) {
+        predict(fine, fine->u0, fine->U, dt);
+        sweep(fine, fine->u0, fine->U, nullptr, dt, ncycles);
+    } else {
+        start_strategy(c, P, dt, start);
+        for (int k = 0; k < ncycles; ++k) vcycle(c, P, nl, dt, c->prob.Nc);
+        if (post) sweep(fine, fine->u0, fine->U, nullptr, dt, 1);
+    }
+    copy_d2d(fine, d_u, Um(fine, fine->U, fine->M - 1), fine->NV);
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ctx* out) {
+    if (!prob || !out) return SISDC_E_ARG;
+    *out = nullptr;
+    const int nc_expect = prob->pde == SISDC_PDE_CONVDIFF ? 1 : prob->pde == SISDC_PDE_BURGERS ? 2
+                          : prob->pde == SISDC_PDE_EULER  ? 4 : -1;
+    if (nc_expect < 0 || prob->ncomp != nc_expect) return SISDC_E_ARG;
+    if (prob->si_stages != 1 && prob->si_stages != 2) return SISDC_E_ARG;
+    if (prob->precision != SISDC_FP64 && prob->precision != SISDC_MIXED) return SISDC_E_ARG;
+    if (!(prob->cg_rtol > 0.0) || prob->cg_maxit < 1 || prob->Nc < 0) return SISDC_E_ARG;
+    if (prob->pde == SISDC_PDE_EULER && !(prob->gamma > 1.0)) return SISDC_E_ARG;
+    if (prob->nu < 0.0) return SISDC_E_ARG;
+    sisdc_ctx_s* c = new sisdc_ctx_s();
+    c->prob = *prob;
+    c->stream = (cudaStream_t)cuda_stream;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && prob->use_graph && cuda_stream == nullptr) {
+        // the legacy stream cannot be captured; a blocking stream keeps the
+        // legacy stream's ordering with respect to other work
+        e = cudaStreamCreate(&c->own_stream);
+        c->stream = c->own_stream;
+    }
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->max_grid = 32 * (nsm > 0 ? nsm : 160);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, ST_N * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_part, 4 * (size_t)c->max_grid * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, ST_N * sizeof(long long));
+    if (e != cudaSuccess) {
+        sisdc_destroy(c);
+        return e == cudaErrorMemoryAllocation ? SISDC_E_OOM : SISDC_E_CUDA;
+    }
+    *out = c;
+    return SISDC_OK;
+}
+
+void sisdc_destroy(sisdc_ctx c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->d_iters);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    for (sisdc_level_s* lv : c->levels) {
+        cudaFree(lv->d_tab);
+        cudaFree(lv->d_mem);
+        delete lv;
+    }
+    cudaFree(c->d_bar);
+    cudaFree(c->d_err);
+    cudaFree(c->d_stats);
+    cudaFree(c->d_part);
+    delete c;
+}
+
+sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_level* out) {
+    if (!c || !d || !out) return SISDC_E_ARG;
+    *out = nullptr;
+    if (d->dim != 1 && d->dim != 2) return fail(c, SISDC_E_ARG, "dim must be 1 or 2");
+    if (d->dim == 1 && c->prob.pde != SISDC_PDE_CONVDIFF) return fail(c, SISDC_E_ARG, "1D supports convection-diffusion only");
+    if (d->P < 1 || d->P > 8) return fail(c, SISDC_E_ARG, "P must be in 1..8");
+    if (d->M < 1 || d->M > MMAX) return fail(c, SISDC_E_ARG, "M must be in 1..8");
+    if (d->nodes != SISDC_RADAU_RIGHT && d->nodes != SISDC_LOBATTO) return fail(c, SISDC_E_ARG, "bad node kind");
+    if (d->nodes == SISDC_LOBATTO && d->M < 2) return fail(c, SISDC_E_ARG, "Lobatto needs M >= 2");
+    const int ney = d->dim == 2 ? d->nel[1] : 1;
+    if (d->nel[0] < 1 || ney < 1) return fail(c, SISDC_E_ARG, "nel must be >= 1");
+    if (!(d->hi[0] > d->lo[0]) || (d->dim == 2 && !(d->hi[1] > d->lo[1]))) return fail(c, SISDC_E_ARG, "empty box");
+    if ((int)c->levels.size() >= 8) return fail(c, SISDC_E_ARG, "at most 8 levels");
+    if (!c->levels.empty()) {
+        const sisdc_level_desc& p = c->levels.back()->desc;
+        if (p.dim != d->dim || p.nel[0] != d->nel[0] || (d->dim == 2 && p.nel[1] != d->nel[1]) ||
+            p.nodes != d->nodes || p.lo[0] != d->lo[0] || p.hi[0] != d->hi[0] ||
+            (d->dim == 2 && (p.lo[1] != d->lo[1] || p.hi[1] != d->hi[1])))
+            return fail(c, SISDC_E_ARG, "levels must share dim, element grid, box and node kind");
+        if (p.P > d->P || p.M > d->M) return fail(c, SISDC_E_ARG, "levels must be added coarse to fine");
+    }
+    sisdc_level_s* lv = new sisdc_level_s();
+    lv->ctx = c;
+    lv->index = (int)c->levels.size();
+    lv->desc = *d;
+    if (d->dim == 1) { lv->desc.nel[1] = 1; lv->desc.lo[1] = 0.0; lv->desc.hi[1] = 1.0; }
+    if (!build_level_tables(d->P, d->M, d->nodes == SISDC_LOBATTO, &lv->tab)) {
+        delete lv;
+        return fail(c, SISDC_E_ARG, "table construction failed");
+    }
+    lv->nq = d->P + 1;
+    lv->nqy = d->dim == 2 ? lv->nq : 1;
+    lv->Q = lv->nq * lv->nqy;
+    lv->M = d->M;
+    lv->nel = d->nel[0] * ney;
+    lv->N = (long long)lv->nel * lv->Q;
+    lv->NV = lv->N * c->prob.ncomp;
+    const double hx = (d->hi[0] - d->lo[0]) / d->nel[0];
+    const double hy = d->dim == 2 ? (d->hi[1] - d->lo[1]) / ney : 1.0;
+    const int nq = lv->nq;
+    const double taux = 2.0 * nq * nq / hx, tauy = 2.0 * nq * nq / hy;
+    std::vector<double> htab(2 * nq * nq + 3 * nq);
+    for (int k = 0; k < nq * nq; ++k) { htab[k] = lv->tab.D[k]; htab[nq * nq + k] = lv->tab.K[k]; }
+    for (int i = 0; i < nq; ++i) {
+        htab[2 * nq * nq + i] = lv->tab.w[i];
+        double dx = (2.0 / hx) * lv->tab.Kdiag[i], dy = (2.0 / hy) * lv->tab.Kdiag[i];
+        if (i == nq - 1) { dx += -2.0 * lv->tab.DPP / hx + taux; dy += -2.0 * lv->tab.DPP / hy + tauy; }
+        if (i == 0) { dx += 2.0 * lv->tab.D00 / hx + taux; dy += 2.0 * lv->tab.D00 / hy + tauy; }
+        htab[2 * nq * nq + nq + i] = dx;
+        htab[2 * nq * nq + 2 * nq + i] = dy;
+    }
+    // transfers to the coarser level
+    std::vector<double> ttab;
+    size_t off_Ix = 0, off_Px = 0, off_Rx = 0, off_It = 0, off_Pt = 0, off_Rt = 0, off_one = 0;
+    if (lv->index > 0) {
+        sisdc_level_s* cl = c->levels.back();
+        const std::vector<double>& xf = lv->tab.gll;
+        const std::vector<double>& xc = cl->tab.gll;
+        std::vector<double> Ix = lagrange_matrix(xc, xf);   // (nqf x nqc)
+        std::vector<double> Px = lagrange_matrix(xf, xc);   // (nqc x nqf)
+        std::vector<double> Rx(cl->nq * nq);
+        for (int a = 0; a < cl->nq; ++a)
+            for (int b = 0; b < nq; ++b) Rx[a * nq + b] = Ix[b * cl->nq + a] * lv->tab.w[b] / cl->tab.w[a];
+        std::vector<double> It = lagrange_matrix(cl->tab.tau, lv->tab.tau);   // (Mf x Mc)
+        std::vector<double> Pt = lagrange_matrix(lv->tab.tau, cl->tab.tau);   // (Mc x Mf)
+        std::vector<double> Rt(cl->M * lv->M);
+        for (int a = 0; a < cl->M; ++a)
+            for (int b = 0; b < lv->M; ++b) Rt[a * lv->M + b] = It[b * cl->M + a];
+        auto push = [&](const std::vector<double>& v) { size_t o = ttab.size(); ttab.insert(ttab.end(), v.begin(), v.end()); return o; };
+        off_Ix = push(Ix); off_Px = push(Px); off_Rx = push(Rx);
+        off_It = push(It); off_Pt = push(Pt); off_Rt = push(Rt);
+        off_one = push(std::vector<double>{1.0});
+    }
+    const size_t ntab = htab.size() + ttab.size();
+    cudaError_t e = cudaMalloc(&lv->d_tab, ntab * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(lv->d_tab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ttab.empty())
+        e = cudaMemcpy(lv->d_tab + htab.size(), ttab.data(), ttab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    // work arrays
+    const long long NV = lv->NV, MV = (long long)lv->M * NV;
+    const long long ntr = (long long)c->prob.ncomp * lv->nel * 2 * d->dim * 2 * nq;
+    const long long total = 8 * MV + 2 * NV + 3 * NV + 3 * NV + 2 * ntr + 2 * (MMAX + 1);
+    if (e == cudaSuccess) e = cudaMalloc(&lv->d_mem, total * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(lv->d_tab);
+        cudaFree(lv->d_mem);
+        delete lv;
+        return fail(c, e == cudaErrorMemoryAllocation ? SISDC_E_OOM : SISDC_E_CUDA,
+                    std::string("level allocation: ") + cudaGetErrorString(e));
+    }
+    cudaMemset(lv->d_mem, 0, total * sizeof(double));
+    double* p = lv->d_mem;
+    auto take = [&](long long n) { double* q = p; p += n; return q; };
+    lv->U = take(MV); lv->F = take(MV); lv->CC = take(MV); lv->LU = take(MV);
+    lv->Qb = take(MV); lv->G = take(MV); lv->V = take(MV); lv->R = take(MV);
+    lv->u0 = take(NV); lv->c0 = take(NV);
+    lv->dC = take(NV); lv->tmpc = take(NV); lv->cg_r = take(NV);
+    lv->cg_p = take(NV); lv->cg_Ap = take(NV); take(NV);
+    lv->trx = take(ntr); lv->trp = take(ntr);
+    lv->lam = take(2 * (MMAX + 1));
+    if (lv->index > 0) {
+        double* t = lv->d_tab + htab.size();
+        lv->d_Ix = t + off_Ix; lv->d_Px = t + off_Px; lv->d_Rx = t + off_Rx;
+        lv->d_It = t + off_It; lv->d_Pt = t + off_Pt; lv->d_Rt = t + off_Rt; lv->d_one = t + off_one;
+    }
+    Geo& g = lv->geo;
+    g.dim = d->dim; g.nq = nq; g.nqy = lv->nqy; g.q = lv->Q;
+    g.nex = d->nel[0]; g.ney = ney; g.nel = lv->nel; g.ncomp = c->prob.ncomp;
+    g.N = lv->N; g.hx = hx; g.hy = hy; g.taux = taux; g.tauy = tauy;
+    g.D = lv->d_tab; g.K = lv->d_tab + nq * nq; g.w = lv->d_tab + 2 * nq * nq;
+    g.dline_x = g.w + nq; g.dline_y = g.w + 2 * nq;
+    lv->pcg_grid = pcg_grid(g, &lv->pcg_block);
+    if (lv->pcg_grid < 1 || lv->pcg_grid > c->max_grid) {
+        cudaFree(lv->d_tab);
+        cudaFree(lv->d_mem);
+        delete lv;
+        return fail(c, SISDC_E_CUDA, "cooperative PCG launch configuration unavailable");
+    }
+    c->levels.push_back(lv);
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    *out = lv;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_level_info(sisdc_level lv, int* ncomp, long long* nodes, int* M) {
+    if (!lv) return SISDC_E_ARG;
+    if (ncomp) *ncomp = lv->ctx->prob.ncomp;
+    if (nodes) *nodes = lv->N;
+    if (M) *M = lv->M;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_level_coords(sisdc_level lv, double* hx_out, double* hy_out) {
+    if (!lv || !hx_out) return SISDC_E_ARG;
+    const sisdc_level_desc& d = lv->desc;
+    const double hx = lv->geo.hx, hy = lv->geo.hy;
+    for (int e = 0; e < lv->nel; ++e) {
+        const int ex = e % d.nel[0], ey = e / d.nel[0];
+        for (int j = 0; j < lv->nqy; ++j)
+            for (int i = 0; i < lv->nq; ++i) {
+                const long long k = (long long)e * lv->Q + j * lv->nq + i;
+                hx_out[k] = d.lo[0] + (ex + (lv->tab.gll[i] + 1.0) / 2.0) * hx;
+                if (hy_out) hy_out[k] = d.dim == 2 ? d.lo[1] + (ey + (lv->tab.gll[j] + 1.0) / 2.0) * hy : 0.0;
+            }
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_level_tables(sisdc_level lv, double* tau, double* wnn, double* gll, double* w, double* D) {
+    if (!lv) return SISDC_E_ARG;
+    if (tau) std::memcpy(tau, lv->tab.tau.data(), lv->M * sizeof(double));
+    if (wnn) std::memcpy(wnn, lv->tab.wnn.data(), lv->M * lv->M * sizeof(double));
+    if (gll) std::memcpy(gll, lv->tab.gll.data(), lv->nq * sizeof(double));
+    if (w) std::memcpy(w, lv->tab.w.data(), lv->nq * sizeof(double));
+    if (D) std::memcpy(D, lv->tab.D.data(), lv->nq * lv->nq * sizeof(double));
+    return SISDC_OK;
+}
+
+#define SISDC_TRY(ctx, body)                                   \
+    try {                                                      \
+        body;                                                  \
+    } catch (const Fail& f_) {                                 \
+        return f_.st;                                          \
+    } catch (...) {                                            \
+        return fail(ctx, SISDC_E_CUDA, "unexpected host error"); \
+    }                                                          \
+    return SISDC_OK;
+
+sisdc_status sisdc_apply_conv(sisdc_level lv, const double* u, double* out) {
+    if (!lv || !u || !out) return SISDC_E_ARG;
+    SISDC_TRY(lv->ctx, k_conv(lv, u, out, nullptr));
+}
+
+sisdc_status sisdc_apply_lap(sisdc_level lv, const double* u, double* out) {
+    if (!lv || !u || !out) return SISDC_E_ARG;
+    SISDC_TRY(lv->ctx, k_lap(lv, u, out, APPLY_LAP));
+}
+
+sisdc_status sisdc_solve(sisdc_level lv, double cval, const double* rhs, double* x, int* iters) {
+    if (!lv || !rhs || !x || !(cval >= 0.0)) return SISDC_E_ARG;
+    sisdc_ctx_s* c = lv->ctx;
+    try {
+        long long before = 0;
+        if (iters) {
+            check(c, cudaStreamSynchronize(c->stream), "sync");
+            check(c, cudaMemcpy(&before, c->d_stats + ST_ITERS, sizeof(long long), cudaMemcpyDeviceToHost), "stats");
+        }
+        Terms t;
+        t.add(rhs, 1.0);
+        k_pcg(lv, x, t, Coef{cval, 0.0, nullptr});
+        if (iters) {
+            long long after = 0;
+            check(c, cudaStreamSynchronize(c->stream), "sync");
+            check(c, cudaMemcpy(&after, c->d_stats + ST_ITERS, sizeof(long long), cudaMemcpyDeviceToHost), "stats");
+            *iters = (int)(after - before);
+        }
+    } catch (const Fail& f) {
+        return f.st;
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_predict(sisdc_level lv, const double* u0, double* U, double dt) {
+    if (!lv || !u0 || !U || !(dt > 0.0)) return SISDC_E_ARG;
+    SISDC_TRY(lv->ctx, predict(lv, u0, U, dt));
+}
+
+sisdc_status sisdc_sweep(sisdc_level lv, const double* u0, double* U, const double* g, double dt, int nsweeps) {
+    if (!lv || !u0 || !U || !(dt > 0.0) || nsweeps < 0) return SISDC_E_ARG;
+    lv->valid = false;   // the caller may have changed U since the last call
+    SISDC_TRY(lv->ctx, sweep(lv, u0, U, g, dt, nsweeps));
+}
+
+sisdc_status sisdc_residual(sisdc_level lv, const double* u0, const double* U, const double* g, double dt,
+                            double* r) {
+    if (!lv || !u0 || !U || !r || !(dt > 0.0)) return SISDC_E_ARG;
+    lv->valid = false;
+    SISDC_TRY(lv->ctx, residual(lv, u0, U, g, dt, r));
+}
+
+sisdc_status sisdc_transfer(sisdc_level fine, sisdc_level coarse, int op, const double* in, double* out) {
+    if (!fine || !coarse || !in || !out || op < 0 || op > 3) return SISDC_E_ARG;
+    if (fine->ctx != coarse->ctx || fine->index != coarse->index + 1)
+        return fail(fine->ctx, SISDC_E_ARG, "transfer needs adjacent levels of one context");
+    SISDC_TRY(fine->ctx, k_transfer(fine, op, in, out, 0));
+}
+
+sisdc_status sisdc_vcycle(sisdc_ctx c, const double* u0, double* U, double dt, int Nc) {
+    if (!c || !u0 || !U || !(dt > 0.0) || Nc < 0) return SISDC_E_ARG;
+    if (c->levels.empty()) return fail(c, SISDC_E_STATE, "no level created");
+    try {
+        const int nl = (int)c->levels.size();
+        LevelPtrs P;
+        P.u0.resize(nl);
+        P.U.resize(nl);
+        for (int l = 0; l < nl; ++l) {
+            P.u0[l] = l == nl - 1 ? u0 : c->levels[l]->u0;
+            P.U[l] = l == nl - 1 ? U : c->levels[l]->U;
+            c->levels[l]->valid = false;
+        }
+        for (int l = nl - 1; l >= 1; --l) k_transfer(c->levels[l], T_PROJECT_SPACE, P.u0[l], c->levels[l - 1]->u0, 0);
+        vcycle(c, P, nl, dt, Nc);
+    } catch (const Fail& f) {
+        return f.st;
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_step(sisdc_ctx c, double* u, double t, double dt, int ncycles, int start, int post) {
+    (void)t;
+    if (!c || !u || !(dt > 0.0) || ncycles < 0 || start < 0 || start > 3) return SISDC_E_ARG;
+    if (c->levels.empty()) return fail(c, SISDC_E_STATE, "no level created");
+    try {
+        if (!c->prob.use_graph) {
+            enqueue_step(c, u, dt, ncycles, start, post);
+            return SISDC_OK;
+        }
+        if (!(c->gexec && c->g_u == u && c->g_dt == dt && c->g_ncycles == ncycles && c->g_start == start &&
+              c->g_post == post)) {
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            check(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            try {
+                enqueue_step(c, u, dt, ncycles, start, post);
+            } catch (...) {
+                cudaStreamEndCapture(c->stream, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            check(c, cudaStreamEndCapture(c->stream, &graph), "end capture");
+            cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            check(c, e, "graph instantiate");
+            c->g_u = u; c->g_dt = dt; c->g_ncycles = ncycles; c->g_start = start; c->g_post = post;
+        }
+        check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+    } catch (const Fail& f) {
+        return f.st;
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_sync(sisdc_ctx c) {
+    if (!c) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    int flag = 0;
+    e = cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("flag read: ") + cudaGetErrorString(e));
+    if (flag) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        if (flag & DEV_TIMEOUT) {
+            cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
+            return fail(c, SISDC_E_TIMEOUT, "a grid barrier wait timed out");
+        }
+        if (flag & DEV_NONFINITE) return fail(c, SISDC_E_NONFINITE, "non-finite value in an implicit solve");
+        if (flag & DEV_NOCONV) return fail(c, SISDC_E_NOCONV, "an implicit solve reached cg_maxit");
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_get_stats(sisdc_ctx c, sisdc_stats* out) {
+    if (!c || !out) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    long long s[ST_N] = {0};
+    if (e == cudaSuccess) e = cudaMemcpy(s, c->d_stats, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("stats: ") + cudaGetErrorString(e));
+    std::memset(out, 0, sizeof(*out));
+    out->cg_solves = s[ST_SOLVES];
+    out->cg_iters = s[ST_ITERS];
+    out->cg_max_iters = s[ST_MAXIT];
+    out->cg_noconv = s[ST_NOCONV];
+    out->ir_steps = s[ST_IR];
+    for (int l = 0; l < 8; ++l) out->sweeps[l] = c->sweeps[l];
+    out->launches = c->launches;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_reset_stats(sisdc_ctx c) {
+    if (!c) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, ST_N * sizeof(long long));
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("reset: ") + cudaGetErrorString(e));
+    for (int l = 0; l < 8; ++l) c->sweeps[l] = 0;
+    c->launches = 0;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_set_kernel_timing(sisdc_ctx c, int enable, int level) {
+    if (!c) return SISDC_E_ARG;
+    if (enable && c->prob.use_graph) return fail(c, SISDC_E_STATE, "kernel timing needs eager mode (use_graph = 0)");
+    c->timing = enable != 0;
+    c->timing_level = level;
+    c->ev_used = 0;
+    c->ev_level.clear();
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_get_kernel_timing(sisdc_ctx c, double* ms_total, long long* launches, long long* iters,
+                                     long long* nodes_x_iters) {
+    if (!c) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+    const size_t n = c->ev_used / 2;
+    std::vector<int> it(n);
+    if (n) {
+        e = cudaMemcpy(it.data(), c->d_iters, n * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("copy: ") + cudaGetErrorString(e));
+    }
+    double tot = 0.0;
+    long long its = 0, nxi = 0;
+    for (size_t k = 0; k < n; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]);
+        if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("elapsed: ") + cudaGetErrorString(e));
+        tot += ms;
+        its += it[k];
+        nxi += (long long)it[k] * c->levels[c->ev_level[k]]->NV;
+    }
+    if (ms_total) *ms_total = tot;
+    if (launches) *launches = (long long)n;
+    if (iters) *iters = its;
+    if (nodes_x_iters) *nodes_x_iters = nxi;
+    c->ev_used = 0;
+    c->ev_level.clear();
+    return SISDC_OK;
+}
+
+const char* sisdc_last_error(sisdc_ctx c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

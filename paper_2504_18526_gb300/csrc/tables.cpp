@@ -1,0 +1,198 @@
+// Host tables of one level, computed in long double and rounded to double.
+//
+// * GLL nodes/weights and the nodal differentiation matrix on [-1, 1]
+//   (DG-SEM basis, Sec. 6).
+// * Collocation nodes on [0, 1] (Sec. 3.1): Radau-Right = roots of
+//   P_{M-1}(x) - P_M(x) mapped by (x+1)/2; Lobatto = GLL with M points.
+// * Node-to-node weights w^nn_{m,i} = int_{tau_{m-1}}^{tau_m} l_i (Sec. 3.2),
+//   by M-point Gauss-Legendre quadrature per subinterval (exact).
+// * Lagrange evaluation matrices for the embedded transfers (Sec. 4.2).
+#include "tables.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace sisdc {
+
+typedef long double ld;
+
+// P_n(x) and P_n'(x) by the three-term recurrence.
+static void legendre(int n, ld x, ld* p, ld* dp) {
+    ld p0 = 1.0L, p1 = x;
+    if (n == 0) { *p = 1.0L; *dp = 0.0L; return; }
+    for (int k = 2; k <= n; ++k) {
+        const ld pk = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+    }
+    *p = p1;
+    // derivative from n (x P_n - P_{n-1}) / (x^2 - 1), endpoints n(n+1)/2 (+-)
+    if (fabsl(fabsl(x) - 1.0L) < 1e-30L) {
+        *dp = (x > 0 ? 1.0L : ((n % 2) ? 1.0L : -1.0L)) * n * (n + 1) / 2.0L;
+    } else {
+        *dp = n * (x * p1 - p0) / (x * x - 1.0L);
+    }
+}
+
+static std::vector<ld> gauss_legendre(int n, std::vector<ld>* w) {
+    std::vector<ld> x(n);
+    w->assign(n, 0.0L);
+    const ld pi = 3.14159265358979323846264338327950288L;
+    for (int k = 0; k < n; ++k) {
+        ld t = cosl(pi * (k + 0.75L) / (n + 0.5L));
+        for (int it = 0; it < 100; ++it) {
+            ld p, dp;
+            legendre(n, t, &p, &dp);
+            const ld d = p / dp;
+            t -= d;
+            if (fabsl(d) < 1e-19L) break;
+        }
+        ld p, dp;
+        legendre(n, t, &p, &dp);
+        x[k] = t;
+        (*w)[k] = 2.0L / ((1.0L - t * t) * dp * dp);
+    }
+    std::vector<size_t> ord(n);
+    for (int k = 0; k < n; ++k) ord[k] = k;
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return x[a] < x[b]; });
+    std::vector<ld> xs(n), ws(n);
+    for (int k = 0; k < n; ++k) { xs[k] = x[ord[k]]; ws[k] = (*w)[ord[k]]; }
+    *w = ws;
+    return xs;
+}
+
+static void gll_ld(int P, std::vector<ld>* x, std::vector<ld>* w) {
+    x->assign(P + 1, 0.0L);
+    w->assign(P + 1, 0.0L);
+    const ld pi = 3.14159265358979323846264338327950288L;
+    (*x)[0] = -1.0L;
+    (*x)[P] = 1.0L;
+    for (int k = 1; k < P; ++k) {
+        // roots of P_P'(x); P_P'' from the Legendre equation
+        ld t = -cosl(pi * k / P);
+        for (int it = 0; it < 100; ++it) {
+            ld p, dp;
+            legendre(P, t, &p, &dp);
+            const ld d2 = (2.0L * t * dp - P * (P + 1) * p) / (1.0L - t * t);
+            const ld d = dp / d2;
+            t -= d;
+            if (fabsl(d) < 1e-19L) break;
+        }
+        (*x)[k] = t;
+    }
+    for (int k = 0; k <= P; ++k) {
+        ld p, dp;
+        legendre(P, (*x)[k], &p, &dp);
+        (*w)[k] = 2.0L / (P * (P + 1) * p * p);
+    }
+}
+
+static std::vector<ld> radau_right_ld(int M) {
+    // roots of r(x) = P_{M-1}(x) - P_M(x) on [-1, 1]; x = 1 is one of them
+    std::vector<ld> x(M);
+    const ld pi = 3.14159265358979323846264338327950288L;
+    for (int k = 0; k < M; ++k) {
+        ld t = cosl(2.0L * pi * k / (2 * M - 1));
+        if (k == 0) { x[k] = 1.0L; continue; }
+        for (int it = 0; it < 200; ++it) {
+            ld a, da, b, db;
+            legendre(M - 1, t, &a, &da);
+            legendre(M, t, &b, &db);
+            const ld d = (a - b) / (da - db);
+            t -= d;
+            if (fabsl(d) < 1e-19L) break;
+        }
+        x[k] = t;
+    }
+    std::sort(x.begin(), x.end());
+    x[M - 1] = 1.0L;
+    for (int k = 0; k < M; ++k) x[k] = (x[k] + 1.0L) / 2.0L;
+    return x;
+}
+
+static ld lagrange(const std::vector<ld>& nodes, int j, ld t) {
+    ld v = 1.0L;
+    for (size_t k = 0; k < nodes.size(); ++k)
+        if ((int)k != j) v *= (t - nodes[k]) / (nodes[j] - nodes[k]);
+    return v;
+}
+
+std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& pts) {
+    std::vector<ld> nl(nodes.begin(), nodes.end());
+    std::vector<double> E(pts.size() * nodes.size());
+    for (size_t p = 0; p < pts.size(); ++p)
+        for (size_t j = 0; j < nodes.size(); ++j)
+            E[p * nodes.size() + j] = (double)lagrange(nl, (int)j, (ld)pts[p]);
+    return E;
+}
+
+bool build_level_tables(int P, int M, int lobatto, LevelTables* t) {
+    if (P < 1 || P > 8 || M < 1 || M > 8 || (lobatto && M < 2)) return false;
+    const int nq = P + 1;
+    std::vector<ld> x, w;
+    gll_ld(P, &x, &w);
+    t->gll.assign(x.begin(), x.end());
+    t->w.assign(w.begin(), w.end());
+    // barycentric differentiation matrix
+    std::vector<ld> lam(nq, 1.0L);
+    for (int j = 0; j < nq; ++j)
+        for (int k = 0; k < nq; ++k)
+            if (k != j) lam[j] /= (x[j] - x[k]);
+    t->D.assign(nq * nq, 0.0);
+    std::vector<ld> Dl(nq * nq, 0.0L);
+    for (int i = 0; i < nq; ++i) {
+        ld diag = 0.0L;
+        for (int j = 0; j < nq; ++j) {
+            if (i == j) continue;
+            Dl[i * nq + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+            diag -= Dl[i * nq + j];
+        }
+        Dl[i * nq + i] = diag;
+    }
+    for (int k = 0; k < nq * nq; ++k) t->D[k] = (double)Dl[k];
+    // K = D^T W D
+    t->K.assign(nq * nq, 0.0);
+    for (int i = 0; i < nq; ++i)
+        for (int k = 0; k < nq; ++k) {
+            ld s = 0.0L;
+            for (int q = 0; q < nq; ++q) s += Dl[q * nq + i] * w[q] * Dl[q * nq + k];
+            t->K[i * nq + k] = (double)s;
+        }
+    // diagonal of the 1D SIPG line operator on the reference scaling:
+    // dline(h)[i] = (2/h) K_ii + face terms; stored as the h-independent
+    // pieces, combined in level_geometry.
+    t->Kdiag.resize(nq);
+    for (int i = 0; i < nq; ++i) t->Kdiag[i] = t->K[i * nq + i];
+    t->D00 = (double)Dl[0];
+    t->DPP = (double)Dl[nq * nq - 1];
+    // collocation nodes
+    std::vector<ld> tau;
+    if (lobatto) {
+        std::vector<ld> xl, wl;
+        gll_ld(M - 1, &xl, &wl);
+        tau.resize(M);
+        for (int k = 0; k < M; ++k) tau[k] = (xl[k] + 1.0L) / 2.0L;
+        tau[0] = 0.0L;
+        tau[M - 1] = 1.0L;
+    } else {
+        tau = radau_right_ld(M);
+    }
+    t->tau.assign(tau.begin(), tau.end());
+    t->dtau.resize(M);
+    for (int m = 0; m < M; ++m) t->dtau[m] = (double)(tau[m] - (m ? tau[m - 1] : 0.0L));
+    // w^nn by Gauss-Legendre per subinterval
+    std::vector<ld> gw;
+    std::vector<ld> gx = gauss_legendre(M, &gw);
+    t->wnn.assign(M * M, 0.0);
+    for (int m = 0; m < M; ++m) {
+        const ld a = m ? tau[m - 1] : 0.0L, b = tau[m];
+        for (int i = 0; i < M; ++i) {
+            ld s = 0.0L;
+            for (int q = 0; q < M; ++q) s += gw[q] * lagrange(tau, i, a + (b - a) * (gx[q] + 1.0L) / 2.0L);
+            t->wnn[m * M + i] = (double)((b - a) / 2.0L * s);
+        }
+    }
+    return true;
+}
+
+}  // namespace sisdc

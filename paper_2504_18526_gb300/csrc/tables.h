@@ -1,0 +1,18 @@
+// Host tables of one level (long double construction, double storage).
+#pragma once
+#include <vector>
+
+namespace sisdc {
+
+struct LevelTables {
+    std::vector<double> gll, w, D, K, Kdiag;   // GLL nodes/weights, D, D^T W D
+    double D00 = 0.0, DPP = 0.0;
+    std::vector<double> tau, dtau, wnn;        // collocation nodes, substeps, w^nn
+};
+
+bool build_level_tables(int P, int M, int lobatto, LevelTables* t);
+
+// E[p][j] = l_j(pts[p]) for the Lagrange basis on `nodes`.
+std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& pts);
+
+}  // namespace sisdc

@@ -1,0 +1,291 @@
+"""Thin Python binding of the C ABI in include/sisdc.h (argument marshalling only).
+
+Every entry point has the C name.  Device arrays are passed as torch CUDA
+float64 tensors (or raw integer addresses); all arithmetic runs in the CUDA
+library.  A missing library raises instead of falling back to anything.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsisdc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sisdc.h")
+
+c_int, c_double, c_ll, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
+
+SISDC_OK, SISDC_E_ARG, SISDC_E_CUDA, SISDC_E_NOCONV = 0, -1, -2, -3
+SISDC_E_TIMEOUT, SISDC_E_NONFINITE, SISDC_E_OOM, SISDC_E_STATE = -4, -5, -6, -7
+STATUS_NAMES = {0: "SISDC_OK", -1: "SISDC_E_ARG", -2: "SISDC_E_CUDA", -3: "SISDC_E_NOCONV",
+                -4: "SISDC_E_TIMEOUT", -5: "SISDC_E_NONFINITE", -6: "SISDC_E_OOM", -7: "SISDC_E_STATE"}
+SISDC_RADAU_RIGHT, SISDC_LOBATTO = 0, 1
+SISDC_PDE_CONVDIFF, SISDC_PDE_BURGERS, SISDC_PDE_EULER = 0, 1, 2
+SISDC_FP64, SISDC_MIXED = 0, 1
+SISDC_START_SPREAD, SISDC_START_PREDICTOR, SISDC_START_CASCADE, SISDC_START_FMG1 = 0, 1, 2, 3
+T_INTERP, T_PROJECT, T_RESTRICT, T_PROJECT_SPACE = 0, 1, 2, 3
+
+
+class sisdc_level_desc(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("nel", c_int * 2), ("P", c_int), ("M", c_int), ("nodes", c_int),
+                ("lo", c_double * 2), ("hi", c_double * 2)]
+
+
+class sisdc_problem(ctypes.Structure):
+    _fields_ = [("pde", c_int), ("ncomp", c_int), ("nu", c_double), ("gamma", c_double),
+                ("adv", c_double * 2), ("precision", c_int), ("si_stages", c_int),
+                ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("use_graph", c_int)]
+
+
+class sisdc_stats(ctypes.Structure):
+    _fields_ = [("cg_solves", c_ll), ("cg_iters", c_ll), ("cg_max_iters", c_ll), ("cg_noconv", c_ll),
+                ("ir_steps", c_ll), ("sweeps", c_ll * 8), ("launches", c_ll)]
+
+
+class SisdcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def header_symbols():
+    """Entry points declared in include/sisdc.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:sisdc_status|void|const char\*)\s+(sisdc_\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsisdc.so is not built (run __graft_entry__.build()); "
+                           "there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "sisdc_create": (c_int, [P(sisdc_problem), c_void_p, P(c_void_p)]),
+        "sisdc_destroy": (None, [c_void_p]),
+        "sisdc_create_level": (c_int, [c_void_p, P(sisdc_level_desc), P(c_void_p)]),
+        "sisdc_level_info": (c_int, [c_void_p, P(c_int), P(c_ll), P(c_int)]),
+        "sisdc_level_coords": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "sisdc_level_tables": (c_int, [c_void_p] + [c_void_p] * 5),
+        "sisdc_apply_conv": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "sisdc_apply_lap": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "sisdc_solve": (c_int, [c_void_p, c_double, c_void_p, c_void_p, P(c_int)]),
+        "sisdc_predict": (c_int, [c_void_p, c_void_p, c_void_p, c_double]),
+        "sisdc_sweep": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int]),
+        "sisdc_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_void_p]),
+        "sisdc_transfer": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+        "sisdc_vcycle": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int]),
+        "sisdc_step": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_int, c_int]),
+        "sisdc_sync": (c_int, [c_void_p]),
+        "sisdc_get_stats": (c_int, [c_void_p, P(sisdc_stats)]),
+        "sisdc_reset_stats": (c_int, [c_void_p]),
+        "sisdc_last_error": (ctypes.c_char_p, [c_void_p]),
+        "sisdc_set_kernel_timing": (c_int, [c_void_p, c_int, c_int]),
+        "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device address of a torch tensor (float64, contiguous) or an int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if x.dtype.is_floating_point and x.element_size() != 8:
+        raise TypeError("expected float64 storage")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _hptr(a):
+    """Host address of a numpy float64 array."""
+    if a is None:
+        return None
+    return a.ctypes.data
+
+
+_LEVEL_CTX = {}
+
+
+def _check(st, ctx=None, lv=None):
+    if st != SISDC_OK:
+        ctx = ctx if ctx else _LEVEL_CTX.get(lv)
+        msg = load().sisdc_last_error(ctx).decode() if ctx else ""
+        raise SisdcError(st, msg)
+
+
+# ---- entry points (same names as the C ABI) ------------------------------------
+def sisdc_create(prob, stream=0):
+    out = c_void_p()
+    _check(load().sisdc_create(ctypes.byref(prob), c_void_p(stream), ctypes.byref(out)))
+    return out.value
+
+
+def sisdc_destroy(ctx):
+    load().sisdc_destroy(ctx)
+
+
+def sisdc_create_level(ctx, desc):
+    out = c_void_p()
+    _check(load().sisdc_create_level(ctx, ctypes.byref(desc), ctypes.byref(out)), ctx)
+    _LEVEL_CTX[out.value] = ctx
+    return out.value
+
+
+def sisdc_level_info(lv):
+    nc, n, m = c_int(), c_ll(), c_int()
+    _check(load().sisdc_level_info(lv, ctypes.byref(nc), ctypes.byref(n), ctypes.byref(m)))
+    return nc.value, n.value, m.value
+
+
+def sisdc_level_coords(lv, hx, hy=None):
+    _check(load().sisdc_level_coords(lv, _hptr(hx), _hptr(hy)))
+
+
+def sisdc_level_tables(lv, tau=None, wnn=None, gll=None, w=None, D=None):
+    _check(load().sisdc_level_tables(lv, _hptr(tau), _hptr(wnn), _hptr(gll), _hptr(w), _hptr(D)))
+
+
+def sisdc_apply_conv(lv, u, c):
+    _check(load().sisdc_apply_conv(lv, _ptr(u), _ptr(c)), lv=lv)
+
+
+def sisdc_apply_lap(lv, u, Lu):
+    _check(load().sisdc_apply_lap(lv, _ptr(u), _ptr(Lu)), lv=lv)
+
+
+def sisdc_solve(lv, c, rhs, x, want_iters=False):
+    it = c_int()
+    _check(load().sisdc_solve(lv, c, _ptr(rhs), _ptr(x), ctypes.byref(it) if want_iters else None),
+           lv=lv)
+    return it.value if want_iters else None
+
+
+def sisdc_predict(lv, u0, U, dt):
+    _check(load().sisdc_predict(lv, _ptr(u0), _ptr(U), dt), lv=lv)
+
+
+def sisdc_sweep(lv, u0, U, g, dt, nsweeps):
+    _check(load().sisdc_sweep(lv, _ptr(u0), _ptr(U), _ptr(g), dt, nsweeps), lv=lv)
+
+
+def sisdc_residual(lv, u0, U, g, dt, r):
+    _check(load().sisdc_residual(lv, _ptr(u0), _ptr(U), _ptr(g), dt, _ptr(r)), lv=lv)
+
+
+def sisdc_transfer(fine, coarse, op, src, dst):
+    _check(load().sisdc_transfer(fine, coarse, op, _ptr(src), _ptr(dst)), lv=fine)
+
+
+def sisdc_vcycle(ctx, u0, U, dt, Nc):
+    _check(load().sisdc_vcycle(ctx, _ptr(u0), _ptr(U), dt, Nc), ctx)
+
+
+def sisdc_step(ctx, u, t, dt, ncycles, start, post_sweep):
+    _check(load().sisdc_step(ctx, _ptr(u), t, dt, ncycles, start, 1 if post_sweep else 0), ctx)
+
+
+def sisdc_sync(ctx):
+    _check(load().sisdc_sync(ctx), ctx)
+
+
+def sisdc_get_stats(ctx):
+    s = sisdc_stats()
+    _check(load().sisdc_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {"cg_solves": s.cg_solves, "cg_iters": s.cg_iters, "cg_max_iters": s.cg_max_iters,
+            "cg_noconv": s.cg_noconv, "ir_steps": s.ir_steps, "sweeps": list(s.sweeps),
+            "launches": s.launches}
+
+
+def sisdc_reset_stats(ctx):
+    _check(load().sisdc_reset_stats(ctx), ctx)
+
+
+def sisdc_set_kernel_timing(ctx, enable, level=-1):
+    _check(load().sisdc_set_kernel_timing(ctx, 1 if enable else 0, level), ctx)
+
+
+def sisdc_get_kernel_timing(ctx):
+    ms, n, it, nxi = c_double(), c_ll(), c_ll(), c_ll()
+    _check(load().sisdc_get_kernel_timing(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(it),
+                                          ctypes.byref(nxi)), ctx)
+    return {"ms": ms.value, "launches": n.value, "iters": it.value, "nodes_x_iters": nxi.value}
+
+
+def sisdc_last_error(ctx):
+    return load().sisdc_last_error(ctx).decode()
+
+
+# ---- construction from a workload description (marshalling) -------------------
+PDE_IDS = {"convdiff": SISDC_PDE_CONVDIFF, "burgers": SISDC_PDE_BURGERS, "euler": SISDC_PDE_EULER}
+NODE_IDS = {"radau_right": SISDC_RADAU_RIGHT, "lobatto": SISDC_LOBATTO}
+START_IDS = {"spread": SISDC_START_SPREAD, "predictor": SISDC_START_PREDICTOR,
+             "cascade": SISDC_START_CASCADE, "fmg1": SISDC_START_FMG1}
+
+
+def make_problem(w, precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12, cg_maxit=1000, Nc=2,
+                 use_graph=0):
+    p = sisdc_problem()
+    p.pde = PDE_IDS[w["pde"]]
+    p.ncomp = w["ncomp"]
+    p.nu = w.get("nu", 0.0)
+    p.gamma = w.get("gamma", 1.4)
+    adv = w.get("adv", (0.0, 0.0))
+    p.adv[0], p.adv[1] = adv[0], adv[1]
+    p.precision = precision
+    p.si_stages = si_stages
+    p.cg_rtol = cg_rtol
+    p.cg_maxit = cg_maxit
+    p.Nc = Nc
+    p.use_graph = use_graph
+    return p
+
+
+def make_level_desc(w, lvl):
+    d = sisdc_level_desc()
+    d.dim = w["dim"]
+    d.nel[0] = lvl["nel"][0]
+    d.nel[1] = lvl["nel"][1] if w["dim"] == 2 else 1
+    d.P = lvl["P"]
+    d.M = lvl["M"]
+    d.nodes = NODE_IDS[w["nodes"]]
+    d.lo[0], d.lo[1] = w["lo"][0], w["lo"][1]
+    d.hi[0], d.hi[1] = w["hi"][0], w["hi"][1]
+    return d
+
+
+class Context:
+    """Owns one sisdc context and its levels (coarse to fine)."""
+
+    def __init__(self, w, stream=0, **kw):
+        self.w = w
+        self.ctx = sisdc_create(make_problem(w, **kw), stream)
+        self.levels = [sisdc_create_level(self.ctx, make_level_desc(w, lv)) for lv in w["levels"]]
+
+    def info(self, l=-1):
+        return sisdc_level_info(self.levels[l])
+
+    def close(self):
+        if self.ctx:
+            sisdc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

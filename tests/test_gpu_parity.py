@@ -1,0 +1,295 @@
+"""FP64 parity of the CUDA library (through the C ABI) against the CPU oracle.
+
+Every test feeds the same seeded inputs to both sides and compares element
+by element; the bar is relative L2 <= 1e-12 (FP64 path), with the implicit
+solves of both sides run to rtol 1e-14.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2504_18526_gb300 import inputs, sisdc as S   # noqa: E402
+from oracle import sdc as OS                              # noqa: E402
+from oracle.mlsdc import Transfer                         # noqa: E402
+from oracle.tables import collocation_nodes, wnn, gll, diff_matrix   # noqa: E402
+from tests.helpers import oracle_ml, oracle_space, rel_l2, random_state   # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    S.load()
+    return torch.device("cuda:0")
+
+
+def T(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def wl(name, **over):
+    w = inputs.scaled(name)
+    w.update(over)
+    return w
+
+
+CASES = {
+    "cd1d": dict(pde="convdiff", dim=1, ncomp=1, adv=(1.0, 0.0), nu=0.01, lo=(0.0, 0.0),
+                 hi=(2 * math.pi, 0.0), nodes="lobatto",
+                 levels=[dict(nel=(7, 1), P=2, M=3), dict(nel=(7, 1), P=4, M=5)]),
+    "cd2d": dict(pde="convdiff", dim=2, ncomp=1, adv=(0.7, -1.3), nu=0.02, lo=(0.0, 0.0),
+                 hi=(1.0, 2.0), nodes="radau_right",
+                 levels=[dict(nel=(5, 3), P=2, M=2), dict(nel=(5, 3), P=3, M=3)]),
+    "burgers": dict(pde="burgers", dim=2, ncomp=2, nu=5e-3, lo=(0.0, 0.0), hi=(1.0, 1.0),
+                    nodes="radau_right",
+                    levels=[dict(nel=(6, 5), P=3, M=3), dict(nel=(6, 5), P=7, M=5)]),
+    "euler": dict(pde="euler", dim=2, ncomp=4, gamma=1.4, lo=(-10.0, -10.0), hi=(10.0, 10.0),
+                  nodes="lobatto",
+                  levels=[dict(nel=(4, 6), P=3, M=2), dict(nel=(4, 6), P=5, M=3),
+                          dict(nel=(4, 6), P=7, M=5)]),
+}
+
+
+def make_ctx(w, stages=2, rtol=1e-14, maxit=10000, **kw):
+    return S.Context(w, cg_rtol=rtol, cg_maxit=maxit, si_stages=stages, **kw)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["radau_right", "lobatto"])
+def test_tables_match_oracle(dev, kind):
+    for P in range(1, 9):
+        for M in range(2, 9):
+            w = dict(pde="convdiff", dim=2, ncomp=1, adv=(1.0, 0.0), nu=0.0, lo=(0, 0), hi=(1, 1),
+                     nodes=kind, levels=[dict(nel=(1, 1), P=P, M=M)])
+            ctx = make_ctx(w)
+            tau, W = np.zeros(M), np.zeros(M * M)
+            x, wt, D = np.zeros(P + 1), np.zeros(P + 1), np.zeros((P + 1) ** 2)
+            S.sisdc_level_tables(ctx.levels[0], tau, W, x, wt, D)
+            ot = collocation_nodes(kind, M)
+            ox, ow = gll(P)
+            assert np.max(np.abs(tau - ot)) < 1e-15
+            assert np.max(np.abs(W.reshape(M, M) - wnn(ot))) < 2e-15
+            assert np.max(np.abs(x - ox)) < 1e-15 and np.max(np.abs(wt - ow)) < 1e-15
+            assert np.max(np.abs(D.reshape(P + 1, P + 1) - diff_matrix(ox))) < 1e-12 * P * P
+            ctx.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_conv_and_lap_parity(dev, case):
+    w = CASES[case]
+    ctx = make_ctx(w)
+    for li, lvl in enumerate(w["levels"]):
+        sp = oracle_space(w, lvl)
+        u = random_state(w, sp.shape, li)
+        du = T(u, dev)
+        out = torch.empty_like(du)
+        S.sisdc_apply_conv(ctx.levels[li], du, out)
+        assert rel_l2(N(out), sp.conv(u)) < 1e-13
+        if w["pde"] != "euler":
+            S.sisdc_apply_lap(ctx.levels[li], du, out)
+            assert rel_l2(N(out), sp.lap(u)) < 1e-13
+    # coordinates of the library's nodes
+    nc, n, M = ctx.info(-1)
+    hx, hy = np.zeros(n), np.zeros(n)
+    S.sisdc_level_coords(ctx.levels[-1], hx, hy)
+    X, Y = oracle_space(w, w["levels"][-1]).coords()
+    assert np.max(np.abs(hx - X.ravel())) < 1e-13 and np.max(np.abs(hy - Y.ravel())) < 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("P", range(1, 9))
+def test_lap_parity_all_degrees(dev, P):
+    w = dict(pde="convdiff", dim=2, ncomp=1, adv=(1.0, 0.5), nu=0.01, lo=(0, 0), hi=(1.0, 0.7),
+             nodes="radau_right", levels=[dict(nel=(3, 4), P=P, M=2)])
+    ctx = make_ctx(w)
+    sp = oracle_space(w, w["levels"][0])
+    u = random_state(w, sp.shape, P)
+    du = T(u, dev)
+    out = torch.empty_like(du)
+    S.sisdc_apply_lap(ctx.levels[0], du, out)
+    assert rel_l2(N(out), sp.lap(u)) < 1e-13
+    S.sisdc_apply_conv(ctx.levels[0], du, out)
+    assert rel_l2(N(out), sp.conv(u)) < 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["cd1d", "cd2d", "burgers", "euler"])
+def test_solve_parity(dev, case):
+    w = CASES[case]
+    ctx = make_ctx(w)
+    lvl = w["levels"][-1]
+    sp = oracle_space(w, lvl)
+    rhs = random_state(w, sp.shape, 7)
+    x0 = random_state(w, sp.shape, 8)
+    for cval in (1e-4, 0.05):
+        ref = sp.solve(cval, rhs, x0)
+        dx = T(x0, dev)
+        it = S.sisdc_solve(ctx.levels[-1], cval, T(rhs, dev), dx, want_iters=True)
+        assert rel_l2(N(dx), ref) < TOL
+        assert abs(it - sp.last_cg_iters[-1]) <= 1
+    S.sisdc_sync(ctx.ctx)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["cd1d", "cd2d", "burgers", "euler"])
+@pytest.mark.parametrize("stages", [1, 2])
+def test_predict_sweep_residual_parity(dev, case, stages):
+    w = CASES[case]
+    ctx = make_ctx(w, stages=stages)
+    om = oracle_ml(w, stages=stages)
+    lv = om.levels[-1]
+    sp = lv.space
+    u0 = random_state(w, sp.shape, 11) if w["pde"] != "euler" else random_state(w, sp.shape, 11)
+    dt = 0.02 if w["pde"] != "euler" else 0.01
+    U = OS.predictor(lv, u0, dt, stages)
+    dU = torch.empty((lv.M,) + sp.shape, dtype=torch.float64, device=dev)
+    du0 = T(u0, dev)
+    S.sisdc_predict(ctx.levels[-1], du0, dU, dt)
+    assert rel_l2(N(dU), U) < TOL
+    g = 1e-3 * np.random.default_rng(5).standard_normal(U.shape)
+    if w["pde"] == "euler":
+        g *= 0.1
+    U2 = OS.corrector(lv, u0, U, g, dt, stages, 2)
+    dg = T(g, dev)
+    S.sisdc_sweep(ctx.levels[-1], du0, dU, dg, dt, 2)
+    assert rel_l2(N(dU), U2) < TOL
+    r = g - OS.Fnn(lv, u0, U2, dt)
+    dr = torch.empty_like(dU)
+    S.sisdc_residual(ctx.levels[-1], du0, dU, dg, dt, dr)
+    # r is a small difference of O(|U|) terms: measure its error on their scale
+    assert np.linalg.norm((N(dr) - r).ravel()) < TOL * np.linalg.norm(U2.ravel())
+    S.sisdc_sync(ctx.ctx)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["cd1d", "burgers", "euler"])
+def test_transfer_parity(dev, case):
+    w = CASES[case]
+    ctx = make_ctx(w)
+    om = oracle_ml(w)
+    for l in range(1, len(om.levels)):
+        Tr = Transfer(om.levels[l], om.levels[l - 1])
+        fs, cs = om.levels[l].space, om.levels[l - 1].space
+        Mf, Mc = om.levels[l].M, om.levels[l - 1].M
+        rng = np.random.default_rng(l)
+        Uf = rng.standard_normal((Mf,) + fs.shape)
+        Uc = rng.standard_normal((Mc,) + cs.shape)
+        fine, coarse = ctx.levels[l], ctx.levels[l - 1]
+        out_f = torch.empty((Mf,) + fs.shape, dtype=torch.float64, device=dev)
+        out_c = torch.empty((Mc,) + cs.shape, dtype=torch.float64, device=dev)
+        S.sisdc_transfer(fine, coarse, S.T_INTERP, T(Uc, dev), out_f)
+        assert rel_l2(N(out_f), Tr.interp(Uc)) < 1e-14
+        S.sisdc_transfer(fine, coarse, S.T_PROJECT, T(Uf, dev), out_c)
+        assert rel_l2(N(out_c), Tr.project(Uf)) < 1e-14
+        S.sisdc_transfer(fine, coarse, S.T_RESTRICT, T(Uf, dev), out_c)
+        assert rel_l2(N(out_c), Tr.restrict(Uf)) < 1e-14
+        oc = torch.empty(cs.shape, dtype=torch.float64, device=dev)
+        S.sisdc_transfer(fine, coarse, S.T_PROJECT_SPACE, T(Uf[0], dev), oc)
+        assert rel_l2(N(oc), Tr.project_space(Uf[0])) < 1e-14
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["cd1d", "burgers", "euler"])
+def test_vcycle_parity(dev, case):
+    w = CASES[case]
+    ctx = make_ctx(w)
+    om = oracle_ml(w)
+    fine = om.levels[-1]
+    sp = fine.space
+    X, Y = sp.coords()
+    if w["pde"] == "euler":
+        u0 = inputs.isentropic_vortex(X, Y)
+        dt = 0.05
+    elif w["pde"] == "burgers":
+        u0 = inputs.burgers2d_initial(X, Y)
+        dt = 2e-3
+    else:
+        u0 = np.sin(X)[None] + 0.5 * np.sin(3 * X)[None]
+        dt = 0.05
+    u0s = om.initial_values(u0)
+    Us = om.start(u0s, dt, "fmg1" if len(om.levels) > 2 else "cascade")
+    dU = T(Us[-1], dev)
+    om.vcycle(u0s, Us, dt)
+    S.sisdc_vcycle(ctx.ctx, T(u0, dev), dU, dt, 2)
+    S.sisdc_sync(ctx.ctx)
+    assert rel_l2(N(dU), Us[-1]) < TOL
+    ctx.close()
+
+
+def _step_parity(w, u0, dt, nsteps, ncycles, start, dev, use_graph=0):
+    ctx = make_ctx(w, use_graph=use_graph)
+    om = oracle_ml(w)
+    u = u0.copy()
+    du = T(u0, dev)
+    worst = 0.0
+    for n in range(nsteps):
+        u = om.step(u, dt, ncycles, start=start)
+        S.sisdc_step(ctx.ctx, du, n * dt, dt, ncycles, S.START_IDS[start], 1)
+        worst = max(worst, rel_l2(N(du), u))
+    S.sisdc_sync(ctx.ctx)
+    ctx.close()
+    return worst, u
+
+
+def test_step_parity_convdiff1d_full(dev):
+    """The full 1D convection-diffusion workload: 40 steps to t = 2, every
+    step within 1e-12 of the oracle, and close to the exact solution."""
+    w = inputs.WORKLOADS["convdiff1d"]
+    sp = oracle_space(w, w["levels"][-1])
+    X, _ = sp.coords()
+    u0 = inputs.convdiff1d_exact(X, 0.0)
+    worst, u = _step_parity(w, u0, w["dt"], w["nsteps"], w["ncycles"], w["start"], dev)
+    assert worst < TOL
+    assert sp.l2(u - inputs.convdiff1d_exact(X, 2.0)) < 2e-4
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_step_parity_burgers_small(dev, use_graph):
+    w = inputs.scaled("burgers2d", nel=(6, 6))
+    sp = oracle_space(w, w["levels"][-1])
+    X, Y = sp.coords()
+    u0 = inputs.burgers2d_initial(X, Y)
+    dt = inputs.cfl_dt(0.5, 1.0 / 6, 7, inputs.max_wave_speed("burgers", u0))
+    worst, _ = _step_parity(w, u0, dt, 3, 3, "cascade", dev, use_graph)
+    assert worst < TOL
+
+
+def test_step_parity_euler_small(dev):
+    w = inputs.scaled("euler_vortex", nel=(5, 5))
+    sp = oracle_space(w, w["levels"][-1])
+    X, Y = sp.coords()
+    u0 = inputs.isentropic_vortex(X, Y)
+    dt = inputs.cfl_dt(0.5, 20.0 / 5, 7, inputs.max_wave_speed("euler", u0))
+    worst, _ = _step_parity(w, u0, dt, 2, 2, "fmg1", dev)
+    assert worst < TOL
+
+
+def test_device_error_flags(dev):
+    w = CASES["burgers"]
+    ctx = make_ctx(w, rtol=1e-30, maxit=2)
+    sp = oracle_space(w, w["levels"][-1])
+    rhs = T(random_state(w, sp.shape, 3), dev)
+    x = torch.zeros_like(rhs)
+    S.sisdc_solve(ctx.levels[-1], 0.05, rhs, x)
+    with pytest.raises(S.SisdcError) as ei:
+        S.sisdc_sync(ctx.ctx)
+    assert ei.value.status == S.SISDC_E_NOCONV
+    S.sisdc_sync(ctx.ctx)          # flag cleared
+    bad = rhs.clone()
+    bad[0, 0, 0, 0, 0] = float("nan")
+    S.sisdc_solve(ctx.levels[-1], 0.05, bad, x)
+    with pytest.raises(S.SisdcError) as ei:
+        S.sisdc_sync(ctx.ctx)
+    assert ei.value.status == S.SISDC_E_NONFINITE
+    ctx.close()
