@@ -164,6 +164,35 @@ sisdc_status sisdc_apply_lap(sisdc_level lv, const double* d_u, double* d_Lu);
  * h_iters is not NULL. */
 sisdc_status sisdc_solve(sisdc_level lv, double c, const double* d_rhs, double* d_x, int* h_iters);
 
+/* No-allocation solve (the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory when they need a solve -- for
+ * instance code that must stay inside a fixed memory budget owned by another
+ * framework's caching allocator, or a time-critical loop that cannot afford
+ * cudaMalloc's implicit device synchronisation).  It solves the same system
+ * as sisdc_solve, (I - c L) x = rhs on the uniform periodic mesh described
+ * by *desc (its M and nodes fields are ignored) with ncomp components, by
+ * the same Jacobi-PCG kernel, but needs no context and no level: every
+ * piece of scratch lives in one static device array of
+ * SISDC_NOALLOC_SCRATCH_BYTES (16 MiB) that each GPU loading the library
+ * holds until the process exits.  It calls no cudaMalloc/cudaFree.
+ *   - Fits when 5 * NV doubles (NV = ncomp * nodes) plus face traces and
+ *     tables fit in the array (e.g. 2 x 32x32 elements of P = 7); larger
+ *     problems are rejected with SISDC_E_ARG and a message in h_err.
+ *   - d_x holds the initial guess on entry and the solution on exit
+ *     (device pointers); the call is synchronous on cuda_stream and writes
+ *     the CG iteration count to *h_iters (may be NULL).  h_err (may be
+ *     NULL) receives a message of at most h_err_len bytes.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the
+ *     caller.  Each call clears the parts that must start at zero. */
+#define SISDC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+sisdc_status sisdc_solve_noalloc(const sisdc_level_desc* desc, int ncomp, double c, const double* d_rhs,
+                                 double* d_x, double rtol, int maxit, void* cuda_stream, int* h_iters,
+                                 char* h_err, int h_err_len);
+
 /* --- the method ------------------------------------------------------------ */
 
 /* SI(1)/SI(2) predictor sweep (Sec. 3.3, eqs. sdc:incremental_predictor_si1

@@ -196,3 +196,56 @@ bool build_level_tables(int P, int M, int lobatto, LevelTables* t) {
 }
 
 }  // namespace sisdc
+
+namespace sisdc {
+
+bool gll_tables_fixed(int P, double* xo, double* wo, double* Do, double* Ko) {
+    if (P < 1 || P > 8) return false;
+    const int nq = P + 1;
+    const ld pi = 3.14159265358979323846264338327950288L;
+    ld x[9], w[9], lam[9], Dl[81];
+    x[0] = -1.0L;
+    x[P] = 1.0L;
+    for (int k = 1; k < P; ++k) {
+        ld t = -cosl(pi * k / P);
+        for (int it = 0; it < 100; ++it) {
+            ld p, dp;
+            legendre(P, t, &p, &dp);
+            const ld d = dp / ((2.0L * t * dp - P * (P + 1) * p) / (1.0L - t * t));
+            t -= d;
+            if (fabsl(d) < 1e-19L) break;
+        }
+        x[k] = t;
+    }
+    for (int k = 0; k < nq; ++k) {
+        ld p, dp;
+        legendre(P, x[k], &p, &dp);
+        w[k] = 2.0L / (P * (P + 1) * p * p);
+        lam[k] = 1.0L;
+    }
+    for (int j = 0; j < nq; ++j)
+        for (int k = 0; k < nq; ++k)
+            if (k != j) lam[j] /= (x[j] - x[k]);
+    for (int i = 0; i < nq; ++i) {
+        ld diag = 0.0L;
+        for (int j = 0; j < nq; ++j) {
+            if (i == j) continue;
+            Dl[i * nq + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+            diag -= Dl[i * nq + j];
+        }
+        Dl[i * nq + i] = diag;
+    }
+    for (int i = 0; i < nq; ++i) {
+        xo[i] = (double)x[i];
+        wo[i] = (double)w[i];
+        for (int k = 0; k < nq; ++k) {
+            Do[i * nq + k] = (double)Dl[i * nq + k];
+            ld s = 0.0L;
+            for (int q = 0; q < nq; ++q) s += Dl[q * nq + i] * w[q] * Dl[q * nq + k];
+            Ko[i * nq + k] = (double)s;
+        }
+    }
+    return true;
+}
+
+}  // namespace sisdc

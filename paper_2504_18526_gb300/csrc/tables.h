@@ -16,3 +16,9 @@ bool build_level_tables(int P, int M, int lobatto, LevelTables* t);
 std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& pts);
 
 }  // namespace sisdc
+
+namespace sisdc {
+// GLL nodes x, weights w, differentiation matrix D and K = D^T W D for degree
+// P (1..8) into caller arrays of at least 9, 9, 81, 81 doubles; no heap use.
+bool gll_tables_fixed(int P, double* x, double* w, double* D, double* K);
+}  // namespace sisdc

@@ -88,6 +88,8 @@ def load():
         "sisdc_reset_stats": (c_int, [c_void_p]),
         "sisdc_last_error": (ctypes.c_char_p, [c_void_p]),
         "sisdc_set_kernel_timing": (c_int, [c_void_p, c_int, c_int]),
+        "sisdc_solve_noalloc": (c_int, [P(sisdc_level_desc), c_int, c_double, c_void_p, c_void_p, c_double,
+                                        c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
         "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll)]),
     }
     for name, (res, args) in sig.items():
@@ -173,6 +175,17 @@ def sisdc_solve(lv, c, rhs, x, want_iters=False):
     _check(load().sisdc_solve(lv, c, _ptr(rhs), _ptr(x), ctypes.byref(it) if want_iters else None),
            lv=lv)
     return it.value if want_iters else None
+
+
+def sisdc_solve_noalloc(desc, ncomp, c, rhs, x, rtol, maxit, stream=0):
+    """Solve without any allocation (static scratch); returns the iteration count."""
+    it = c_int()
+    buf = ctypes.create_string_buffer(256)
+    st = load().sisdc_solve_noalloc(ctypes.byref(desc), ncomp, c, _ptr(rhs), _ptr(x), rtol, maxit,
+                                    c_void_p(stream), ctypes.byref(it), buf, 256)
+    if st != SISDC_OK:
+        raise SisdcError(st, buf.value.decode())
+    return it.value
 
 
 def sisdc_predict(lv, u0, U, dt):
