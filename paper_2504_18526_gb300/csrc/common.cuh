@@ -42,6 +42,11 @@ struct Geo {
     const double* w;              // [nq] GLL weights (device)
     const double* dline_x;        // [nq] diagonal of the 1D SIPG line operator (x)
     const double* dline_y;        // [nq] (y)
+    // host-computed factors (no divisions in the kernels' inner loops)
+    double sx, sy;                // 2/h_x, 2/h_y
+    double ihx, ihy;              // 1/h_x, 1/h_y
+    double liftLx, liftRx;        // (2/h_x)/w_0, (2/h_x)/w_P: Rusanov flux lifting
+    double liftLy, liftRy;
 };
 
 // Deterministic block reduction (fixed shuffle tree, fixed warp order).

@@ -92,6 +92,7 @@ extern "C" sisdc_status sisdc_solve_noalloc(const sisdc_level_desc* d, int ncomp
     g.dim = d->dim; g.nq = nq; g.nqy = d->dim == 2 ? nq : 1; g.q = Q;
     g.nex = d->nel[0]; g.ney = ney; g.nel = (int)nel; g.ncomp = ncomp; g.N = nel * Q;
     g.hx = hx; g.hy = hy; g.taux = 2.0 * nq * nq / hx; g.tauy = 2.0 * nq * nq / hy;
+    g.sx = 2.0 / hx; g.sy = 2.0 / hy; g.ihx = 1.0 / hx; g.ihy = 1.0 / hy;
     int block = 0;
     const int grid = pcg_grid(g, &block);
     if (grid < 1) {

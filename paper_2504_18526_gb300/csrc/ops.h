@@ -65,6 +65,41 @@ struct ConvArgs {
 };
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s);
 
+// ---- persistent sweep kernel (sweep.cuh, sweep_*.cu) ------------------------
+enum SweepMode : int { SW_REFRESH = 0, SW_PREDICT = 1, SW_CORRECT = 2 };
+
+struct SweepArgs {
+    Geo g;
+    int pde;
+    double gamma, ax, ay;   // flux parameters
+    double nu;              // physical diffusion in f
+    double nu_d;            // nu_d of nu_tilde = nu_d + dt_m/2 lam_max^2
+    int mode, nsweeps, stages, M;
+    double dt;
+    double dtau[MMAX];
+    double W[MMAX * MMAX];  // w^nn, row m
+    const double* u0;
+    double* U;              // [M][NV]
+    const double* G;        // FAS right-hand side [M][NV] or null
+    double *F, *CC, *LU, *Qb;   // caches [M][NV] and quadrature
+    double *c0, *dC, *tmpc; // [NV]
+    double *r, *p, *p2, *Ap;   // CG vectors [NV] (p double-buffered)
+    double* lam;            // [2][MMAX+1] spectral radius slots (old, new)
+    double* part;           // 8 * grid partial sums
+    double* partmax;        // (MMAX+1) * grid partial maxima
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* err;
+    long long* stats;
+    double rtol;
+    int maxit;
+    int epb;
+    cudaStream_t stream;
+};
+// returns the cooperative grid (0 if unavailable); epb = elements per block
+int sweep_config(const Geo& g, int pde, int* epb, int* block);
+cudaError_t launch_sweep(const SweepArgs& a, int grid, int block);
+
 // ---- elementwise and transfer kernels (ops_misc.cu) -------------------------
 struct LinArgs {          // out[idx] = sum_t coef_t * in_t[idx], idx < n
     long long n;

@@ -10,86 +10,9 @@
 // convective spectral radius of u (for nu_tilde) and can update the cache of
 // c from the previous sweep in place (delta = c_new - c_old).
 #include "ops.h"
+#include "pde.cuh"
 
 namespace sisdc {
-
-template <int PDE>
-struct Pde;
-
-template <>
-struct Pde<0> {   // scalar convection-diffusion, F = a u
-    static constexpr int NC = 1;
-    __device__ static void fx(const ConvArgs& a, const double* u, double* f) { f[0] = a.ax * u[0]; }
-    __device__ static void fy(const ConvArgs& a, const double* u, double* f) { f[0] = a.ay * u[0]; }
-    __device__ static double rx(const ConvArgs& a, const double*) { return fabs(a.ax); }
-    __device__ static double ry(const ConvArgs& a, const double*) { return fabs(a.ay); }
-};
-
-template <>
-struct Pde<1> {   // two-component Burgers, F = u (x) u
-    static constexpr int NC = 2;
-    __device__ static void fx(const ConvArgs&, const double* u, double* f) {
-        f[0] = u[0] * u[0];
-        f[1] = u[0] * u[1];
-    }
-    __device__ static void fy(const ConvArgs&, const double* u, double* f) {
-        f[0] = u[0] * u[1];
-        f[1] = u[1] * u[1];
-    }
-    __device__ static double rx(const ConvArgs&, const double* u) { return 2.0 * fabs(u[0]); }
-    __device__ static double ry(const ConvArgs&, const double* u) { return 2.0 * fabs(u[1]); }
-};
-
-template <>
-struct Pde<2> {   // 2D compressible Euler, perfect gas
-    static constexpr int NC = 4;
-    __device__ static double pres(const ConvArgs& a, const double* u) {
-        return (a.gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]);
-    }
-    __device__ static void fx(const ConvArgs& a, const double* u, double* f) {
-        const double p = pres(a, u), vx = u[1] / u[0];
-        f[0] = u[1];
-        f[1] = u[1] * vx + p;
-        f[2] = u[2] * vx;
-        f[3] = (u[3] + p) * vx;
-    }
-    __device__ static void fy(const ConvArgs& a, const double* u, double* f) {
-        const double p = pres(a, u), vy = u[2] / u[0];
-        f[0] = u[2];
-        f[1] = u[1] * vy;
-        f[2] = u[2] * vy + p;
-        f[3] = (u[3] + p) * vy;
-    }
-    __device__ static double rx(const ConvArgs& a, const double* u) {
-        return fabs(u[1] / u[0]) + sqrt(a.gamma * pres(a, u) / u[0]);
-    }
-    __device__ static double ry(const ConvArgs& a, const double* u) {
-        return fabs(u[2] / u[0]) + sqrt(a.gamma * pres(a, u) / u[0]);
-    }
-};
-
-// Rusanov flux between a left/lower state uL and right/upper state uR.
-template <int PDE, bool XDIR>
-__device__ __forceinline__ void rusanov(const ConvArgs& a, const double* uL, const double* uR,
-                                        double* Fs) {
-    using P = Pde<PDE>;
-    double FL[P::NC], FR[P::NC];
-    double lL, lR;
-    if (XDIR) {
-        P::fx(a, uL, FL);
-        P::fx(a, uR, FR);
-        lL = P::rx(a, uL);
-        lR = P::rx(a, uR);
-    } else {
-        P::fy(a, uL, FL);
-        P::fy(a, uR, FR);
-        lL = P::ry(a, uL);
-        lR = P::ry(a, uR);
-    }
-    const double lam = fmax(lL, lR);
-#pragma unroll
-    for (int c = 0; c < P::NC; ++c) Fs[c] = 0.5 * (FL[c] + FR[c]) - 0.5 * lam * (uR[c] - uL[c]);
-}
 
 template <int NQ, int DIM, int PDE>
 __global__ void k_conv(const ConvArgs a) {
@@ -105,6 +28,7 @@ __global__ void k_conv(const ConvArgs a) {
     const Geo& g = a.g;
     for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) sD[t] = g.D[t];
     for (int t = threadIdx.x; t < NQ; t += blockDim.x) sw[t] = g.w[t];
+    const PdeParams pp{a.gamma, a.ax, a.ay};
 
     const int epb = blockDim.x / Q;
     const int le = threadIdx.x / Q, node = threadIdx.x - le * Q;
@@ -120,13 +44,13 @@ __global__ void k_conv(const ConvArgs a) {
     if (act) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) u[c] = a.u[c * N + e * Q + node];
-        P::fx(a, u, Fx);
-        lmax = P::rx(a, u);
+        P::fx(pp, u, Fx);
+        lmax = P::rx(pp, u);
 #pragma unroll
         for (int c = 0; c < NC; ++c) sFx[c * Q + node] = Fx[c];
         if (DIM == 2) {
-            P::fy(a, u, Fy);
-            lmax = fmax(lmax, P::ry(a, u));
+            P::fy(pp, u, Fy);
+            lmax = fmax(lmax, P::ry(pp, u));
 #pragma unroll
             for (int c = 0; c < NC; ++c) sFy[c * Q + node] = Fy[c];
         }
@@ -163,7 +87,7 @@ __global__ void k_conv(const ConvArgs a) {
         const long long en = (long long)ey * g.nex + (ex + 1) % g.nex;
 #pragma unroll
         for (int c = 0; c < NC; ++c) un[c] = a.u[c * N + en * Q + j * NQ];
-        rusanov<PDE, true>(a, u, un, Fs);
+        rusanov<PDE, true>(pp, u, un, Fs);
         const double s = sx / sw[NQ - 1];
 #pragma unroll
         for (int c = 0; c < NC; ++c) cv[c] -= s * (Fs[c] - Fx[c]);
@@ -172,7 +96,7 @@ __global__ void k_conv(const ConvArgs a) {
         const long long en = (long long)ey * g.nex + (ex + g.nex - 1) % g.nex;
 #pragma unroll
         for (int c = 0; c < NC; ++c) un[c] = a.u[c * N + en * Q + j * NQ + NQ - 1];
-        rusanov<PDE, true>(a, un, u, Fs);
+        rusanov<PDE, true>(pp, un, u, Fs);
         const double s = sx / sw[0];
 #pragma unroll
         for (int c = 0; c < NC; ++c) cv[c] += s * (Fs[c] - Fx[c]);
@@ -183,7 +107,7 @@ __global__ void k_conv(const ConvArgs a) {
             const long long en = (long long)((ey + 1) % g.ney) * g.nex + ex;
 #pragma unroll
             for (int c = 0; c < NC; ++c) un[c] = a.u[c * N + en * Q + i];
-            rusanov<PDE, false>(a, u, un, Fs);
+            rusanov<PDE, false>(pp, u, un, Fs);
             const double s = sy / sw[NQ - 1];
 #pragma unroll
             for (int c = 0; c < NC; ++c) cv[c] -= s * (Fs[c] - Fy[c]);
@@ -192,7 +116,7 @@ __global__ void k_conv(const ConvArgs a) {
             const long long en = (long long)((ey + g.ney - 1) % g.ney) * g.nex + ex;
 #pragma unroll
             for (int c = 0; c < NC; ++c) un[c] = a.u[c * N + en * Q + (NQ - 1) * NQ + i];
-            rusanov<PDE, false>(a, un, u, Fs);
+            rusanov<PDE, false>(pp, un, u, Fs);
             const double s = sy / sw[0];
 #pragma unroll
             for (int c = 0; c < NC; ++c) cv[c] += s * (Fs[c] - Fy[c]);

@@ -20,7 +20,7 @@ static inline unsigned ew_grid(long long n, int bs) {
 
 __global__ void k_lincomb(const __grid_constant__ LinArgs a) {
     __shared__ double sc[MAXTERMS];
-    if (threadIdx.x < MAXTERMS) sc[threadIdx.x] = threadIdx.x < a.nterms ? coef_value(a.coef[threadIdx.x]) : 0.0;
+    for (int t = threadIdx.x; t < MAXTERMS; t += blockDim.x) sc[t] = t < a.nterms ? coef_value(a.coef[t]) : 0.0;
     __syncthreads();
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n;
          idx += (long long)gridDim.x * blockDim.x) {

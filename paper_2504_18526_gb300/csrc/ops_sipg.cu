@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs
     double* sf = su + epb * S::Q;
     const Geo& g = a.g;
     load_tables<NQ>(g, sD, sK, sw, sdx, sdy);
-    if (threadIdx.x < MAXTERMS) scoef[threadIdx.x] = threadIdx.x < a.nterms ? coef_value(a.coef[threadIdx.x]) : 0.0;
+    for (int t = threadIdx.x; t < MAXTERMS; t += blockDim.x) scoef[t] = t < a.nterms ? coef_value(a.coef[t]) : 0.0;
     __syncthreads();
 
     const long long nec = (long long)g.ncomp * g.nel;

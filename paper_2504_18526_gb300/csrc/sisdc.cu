@@ -40,6 +40,8 @@ struct sisdc_level_s {
     double *F = nullptr, *CC = nullptr, *LU = nullptr, *Qb = nullptr, *G = nullptr, *V = nullptr, *R = nullptr;
     double *c0 = nullptr, *dC = nullptr, *tmpc = nullptr;
     double *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *trx = nullptr, *trp = nullptr;
+    double* cg_p2 = nullptr;    // second search-direction buffer of the sweep kernel
+    int sw_grid = 0, sw_epb = 0, sw_block = 0;
     double* lam = nullptr;      // [2][MMAX+1]: old, new spectral radius slots
     int pcg_grid = 0, pcg_block = 0;
     bool valid = false;         // caches match (u0, U)
@@ -99,11 +101,7 @@ sisdc_status fail(sisdc_ctx_s* c, sisdc_status st, const std::string& msg) {
 double nu_d(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER ? 0.0 : p.nu; }
 double nu_phys(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER ? 0.0 : p.nu; }
 
-double* lam_old(sisdc_level_s* lv, int slot) { return lv->lam + slot; }
-double* lam_new(sisdc_level_s* lv, int slot) { return lv->lam + (MMAX + 1) + slot; }
-
 double* Um(sisdc_level_s* lv, double* U, int m) { return U + (long long)m * lv->NV; }
-const double* Um(sisdc_level_s* lv, const double* U, int m) { return U + (long long)m * lv->NV; }
 
 // ---- kernel wrappers ---------------------------------------------------------
 void k_conv(sisdc_level_s* lv, const double* u, double* out, double* lam, int mode = CONV_OUT,
@@ -264,101 +262,68 @@ void k_transfer(sisdc_level_s* fine, int op, const double* in, double* out, int 
     fine->ctx->launches++;
 }
 
-Coef cimp_coef(sisdc_level_s* lv, double dtm, const double* lam) {
-    return Coef{dtm * nu_d(lv->ctx->prob), 0.5 * dtm * dtm, lam};
-}
 
 // ---- method building blocks ----------------------------------------------------
+// One cooperative launch of the persistent sweep kernel (sweep.cuh).
+void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, const double* G, double dt,
+                      int nsweeps) {
+    sisdc_ctx_s* c = lv->ctx;
+    SweepArgs a{};
+    a.g = lv->geo;
+    a.pde = c->prob.pde;
+    a.gamma = c->prob.gamma;
+    a.ax = c->prob.adv[0];
+    a.ay = c->prob.adv[1];
+    a.nu = nu_phys(c->prob);
+    a.nu_d = nu_d(c->prob);
+    a.mode = mode;
+    a.nsweeps = nsweeps;
+    a.stages = c->prob.si_stages;
+    a.M = lv->M;
+    a.dt = dt;
+    for (int m = 0; m < lv->M; ++m) a.dtau[m] = lv->tab.dtau[m];
+    for (int k = 0; k < lv->M * lv->M; ++k) a.W[k] = lv->tab.wnn[k];
+    a.u0 = u0;
+    a.U = U;
+    a.G = G;
+    a.F = lv->F; a.CC = lv->CC; a.LU = lv->LU; a.Qb = lv->Qb;
+    a.c0 = lv->c0; a.dC = lv->dC; a.tmpc = lv->tmpc;
+    a.r = lv->cg_r; a.p = lv->cg_p; a.p2 = lv->cg_p2; a.Ap = lv->cg_Ap;
+    a.lam = lv->lam;
+    a.part = c->d_part;
+    a.partmax = c->d_part + 8 * (size_t)c->max_grid;
+    a.bar_count = c->d_bar;
+    a.bar_gen = c->d_bar + 1;
+    a.err = c->d_err;
+    a.stats = c->d_stats;
+    a.rtol = c->prob.cg_rtol;
+    a.maxit = c->prob.cg_maxit;
+    a.epb = lv->sw_epb;
+    a.stream = c->stream;
+    check(c, launch_sweep(a, lv->sw_grid, lv->sw_block), "sweep kernel");
+    c->launches++;
+}
+
 // Caches f(U_m), c(U_m), L U_m, c(u0) and the spectral-radius slots of (u0, U).
 void refresh(sisdc_level_s* lv, const double* u0, const double* U) {
-    sisdc_ctx_s* c = lv->ctx;
-    check(c, cudaMemsetAsync(lv->lam, 0, 2 * (MMAX + 1) * sizeof(double), c->stream), "memset");
-    k_conv(lv, u0, lv->c0, lam_old(lv, 0));
-    for (int m = 0; m < lv->M; ++m) {
-        k_conv(lv, Um(lv, U, m), Um(lv, lv->CC, m), lam_old(lv, m + 1));
-        k_lap(lv, Um(lv, U, m), Um(lv, lv->LU, m), APPLY_LAP_F, Um(lv, lv->F, m), Um(lv, lv->CC, m));
-    }
-    copy_d2d(lv, lam_new(lv, 0), lam_old(lv, 0), 1);
+    run_sweep_kernel(lv, SW_REFRESH, u0, const_cast<double*>(U), nullptr, 1.0, 0);
     lv->valid = true;
     lv->cache_u0 = u0;
     lv->cache_U = U;
 }
 
 void sweep(sisdc_level_s* lv, const double* u0, double* U, const double* G, double dt, int nsweeps) {
-    sisdc_ctx_s* c = lv->ctx;
     if (!lv->valid || lv->cache_u0 != u0 || lv->cache_U != U) refresh(lv, u0, U);
-    const int stages = c->prob.si_stages;
-    const double nd = nu_d(c->prob);
-    for (int k = 0; k < nsweeps; ++k) {
-        check(c, launch_quad(lv->F, lv->Qb, lv->tab.wnn.data(), lv->M, dt, lv->NV, c->stream), "quad kernel");
-        c->launches++;
-        check(c, cudaMemsetAsync(lam_new(lv, 1), 0, lv->M * sizeof(double), c->stream), "memset");
-        for (int m = 0; m < lv->M; ++m) {
-            const double dtm = dt * lv->tab.dtau[m];
-            const double* uprev = m ? Um(lv, (const double*)U, m - 1) : u0;
-            double* um = Um(lv, U, m);
-            Terms base;
-            base.add(uprev, 1.0);
-            base.add(Um(lv, lv->Qb, m), 1.0);
-            if (G) base.add(Um(lv, G, m), 1.0);
-            if (dtm == 0.0) {
-                k_lin(lv, um, base);
-            } else {
-                // old term -H part: -dt_m nu_tilde(u^{k-1}_{m-1}) L u^{k-1}_m
-                base.add(Um(lv, lv->LU, m), -dtm * nd, -0.5 * dtm * dtm, lam_old(lv, m));
-                const Coef cimp = cimp_coef(lv, dtm, lam_new(lv, m));
-                Terms t1 = base;
-                if (m > 0) t1.add(lv->dC, dtm);     // c(u^k_{m-1}) - c(u^{k-1}_{m-1})
-                k_pcg(lv, um, t1, cimp);
-                if (stages == 2) {
-                    k_conv(lv, um, lv->tmpc, nullptr);
-                    Terms t2 = base;
-                    t2.add(lv->tmpc, dtm);                  // c(u^(1))
-                    t2.add(Um(lv, lv->CC, m), -dtm);        // c(u^{k-1}_m)
-                    k_pcg(lv, um, t2, cimp);
-                }
-            }
-            k_conv(lv, um, nullptr, lam_new(lv, m + 1), CONV_DELTA, Um(lv, lv->CC, m), lv->dC);
-            k_lap(lv, um, Um(lv, lv->LU, m), APPLY_LAP_F, Um(lv, lv->F, m), Um(lv, lv->CC, m));
-        }
-        copy_d2d(lv, lam_old(lv, 1), lam_new(lv, 1), lv->M);
-        if (lv->index < 8) c->sweeps[lv->index]++;
-    }
+    if (nsweeps > 0) run_sweep_kernel(lv, SW_CORRECT, u0, U, G, dt, nsweeps);
+    if (lv->index < 8) lv->ctx->sweeps[lv->index] += nsweeps;
     lv->valid = true;
     lv->cache_u0 = u0;
     lv->cache_U = U;
 }
 
 void predict(sisdc_level_s* lv, const double* u0, double* U, double dt) {
-    sisdc_ctx_s* c = lv->ctx;
-    const int stages = c->prob.si_stages;
-    check(c, cudaMemsetAsync(lv->lam, 0, 2 * (MMAX + 1) * sizeof(double), c->stream), "memset");
-    k_conv(lv, u0, lv->c0, lam_new(lv, 0));
-    for (int m = 0; m < lv->M; ++m) {
-        const double dtm = dt * lv->tab.dtau[m];
-        const double* uprev = m ? Um(lv, (const double*)U, m - 1) : u0;
-        const double* cprev = m ? Um(lv, (const double*)lv->CC, m - 1) : lv->c0;
-        double* um = Um(lv, U, m);
-        copy_d2d(lv, um, uprev, lv->NV);
-        if (dtm != 0.0) {
-            const Coef cimp = cimp_coef(lv, dtm, lam_new(lv, m));
-            Terms t;
-            t.add(uprev, 1.0);
-            t.add(cprev, dtm);
-            k_pcg(lv, um, t, cimp);
-            if (stages == 2) {
-                k_conv(lv, um, lv->tmpc, nullptr);
-                Terms t2;
-                t2.add(uprev, 1.0);
-                t2.add(lv->tmpc, dtm);
-                k_pcg(lv, um, t2, cimp);
-            }
-        }
-        k_conv(lv, um, Um(lv, lv->CC, m), lam_new(lv, m + 1));
-        k_lap(lv, um, Um(lv, lv->LU, m), APPLY_LAP_F, Um(lv, lv->F, m), Um(lv, lv->CC, m));
-    }
-    copy_d2d(lv, lam_old(lv, 0), lam_new(lv, 0), lv->M + 1);
-    if (lv->index < 8) c->sweeps[lv->index]++;
+    run_sweep_kernel(lv, SW_PREDICT, u0, U, nullptr, dt, 0);
+    if (lv->index < 8) lv->ctx->sweeps[lv->index]++;
     lv->valid = true;
     lv->cache_u0 = u0;
     lv->cache_U = U;
@@ -495,7 +460,7 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (e == cudaSuccess) e = cudaMalloc(&c->d_bar, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, ST_N * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_part, 4 * (size_t)c->max_grid * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_part, (8 + MMAX + 1) * (size_t)c->max_grid * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, ST_N * sizeof(long long));
@@ -624,7 +589,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     lv->Qb = take(MV); lv->G = take(MV); lv->V = take(MV); lv->R = take(MV);
     lv->u0 = take(NV); lv->c0 = take(NV);
     lv->dC = take(NV); lv->tmpc = take(NV); lv->cg_r = take(NV);
-    lv->cg_p = take(NV); lv->cg_Ap = take(NV); take(NV);
+    lv->cg_p = take(NV); lv->cg_Ap = take(NV); lv->cg_p2 = take(NV);
     lv->trx = take(ntr); lv->trp = take(ntr);
     lv->lam = take(2 * (MMAX + 1));
     if (lv->index > 0) {
@@ -638,8 +603,12 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     g.N = lv->N; g.hx = hx; g.hy = hy; g.taux = taux; g.tauy = tauy;
     g.D = lv->d_tab; g.K = lv->d_tab + nq * nq; g.w = lv->d_tab + 2 * nq * nq;
     g.dline_x = g.w + nq; g.dline_y = g.w + 2 * nq;
+    g.sx = 2.0 / hx; g.sy = 2.0 / hy; g.ihx = 1.0 / hx; g.ihy = 1.0 / hy;
+    g.liftLx = g.sx / lv->tab.w[0]; g.liftRx = g.sx / lv->tab.w[nq - 1];
+    g.liftLy = g.sy / lv->tab.w[0]; g.liftRy = g.sy / lv->tab.w[nq - 1];
     lv->pcg_grid = pcg_grid(g, &lv->pcg_block);
-    if (lv->pcg_grid < 1 || lv->pcg_grid > c->max_grid) {
+    lv->sw_grid = sweep_config(g, c->prob.pde, &lv->sw_epb, &lv->sw_block);
+    if (lv->pcg_grid < 1 || lv->pcg_grid > c->max_grid || lv->sw_grid < 1 || lv->sw_grid > c->max_grid) {
         cudaFree(lv->d_tab);
         cudaFree(lv->d_mem);
         delete lv;
