@@ -81,9 +81,14 @@ struct SweepArgs {
     const double* u0;
     double* U;              // [M][NV]
     const double* G;        // FAS right-hand side [M][NV] or null
-    double *F, *CC, *LU, *Qb;   // caches [M][NV] and quadrature
-    double *c0, *dC, *tmpc; // [NV]
-    double *r, *p, *p2, *Ap;   // CG vectors [NV] (p double-buffered)
+    int mix;                // 1: mixed precision (caches and inner CG in FP32)
+    double* F;              // cached f [M][NV] (FP64)
+    void *CC, *LU;          // cached c and L u [M][NV] (FP64, or FP32 when mix)
+    double* Qb;             // S.F quadrature [M][NV] (FP64)
+    void *c0, *dC, *tmpc;   // [NV] (FP64, or FP32 when mix)
+    double* r;              // CG residual, or M b of the refinement (FP64) [NV]
+    void *p, *p2, *Ap;      // CG vectors (FP64, or FP32 when mix) [NV]
+    void* rf;               // inner FP32 residual of the refinement (mix) [NV]
     double* lam;            // [2][MMAX+1] spectral radius slots (old, new)
     double* part;           // 8 * grid partial sums
     double* partmax;        // (MMAX+1) * grid partial maxima
@@ -97,7 +102,7 @@ struct SweepArgs {
     cudaStream_t stream;
 };
 // returns the cooperative grid (0 if unavailable); epb = elements per block
-int sweep_config(const Geo& g, int pde, int* epb, int* block);
+int sweep_config(const Geo& g, int pde, int mix, int* epb, int* block);
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int block);
 
 // ---- elementwise and transfer kernels (ops_misc.cu) -------------------------
@@ -110,8 +115,9 @@ struct LinArgs {          // out[idx] = sum_t coef_t * in_t[idx], idx < n
 };
 cudaError_t launch_lincomb(const LinArgs& a, cudaStream_t s);
 
-// Q[m] = dt * sum_i W[m][i] F[i] for m < M (arrays of n values)
-cudaError_t launch_quad(const double* F, double* Q, const double* W, int M, double dt,
+// Q[m] = dt * sum_i W[m][i] F[i] for m < M (arrays of n values; F in FP32
+// when f32, accumulation in FP64 either way)
+cudaError_t launch_quad(const void* F, int f32, double* Q, const double* W, int M, double dt,
                         long long n, cudaStream_t s);
 
 // r[m] = (g ? g[m] : 0) - (U[m] - U[m-1] - Q[m]),  U[-1] = u0   (sign = +1)

@@ -36,7 +36,8 @@ cudaError_t launch_lincomb(const LinArgs& a, cudaStream_t s) {
 }
 
 struct QuadArgs {
-    const double* F;
+    const void* F;
+    int f32;
     double* Q;
     double W[MMAX * MMAX];
     int M;
@@ -48,7 +49,9 @@ __global__ void k_quad(const __grid_constant__ QuadArgs a) {
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n;
          idx += (long long)gridDim.x * blockDim.x) {
         double f[MMAX];
-        for (int i = 0; i < a.M; ++i) f[i] = a.F[i * a.n + idx];
+        for (int i = 0; i < a.M; ++i)
+            f[i] = a.f32 ? (double)static_cast<const float*>(a.F)[i * a.n + idx]
+                         : static_cast<const double*>(a.F)[i * a.n + idx];
         for (int m = 0; m < a.M; ++m) {
             double s = 0.0;
             for (int i = 0; i < a.M; ++i) s += a.W[m * a.M + i] * f[i];
@@ -57,10 +60,11 @@ __global__ void k_quad(const __grid_constant__ QuadArgs a) {
     }
 }
 
-cudaError_t launch_quad(const double* F, double* Q, const double* W, int M, double dt, long long n,
+cudaError_t launch_quad(const void* F, int f32, double* Q, const double* W, int M, double dt, long long n,
                         cudaStream_t s) {
     QuadArgs a;
     a.F = F;
+    a.f32 = f32;
     a.Q = Q;
     for (int t = 0; t < M * M; ++t) a.W[t] = W[t];
     a.M = M;

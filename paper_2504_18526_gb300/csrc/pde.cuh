@@ -1,4 +1,7 @@
 // PDE flux definitions shared by the convective-operator kernels (Sec. 2).
+// Templated on the arithmetic type T (double for the FP64 path, float for
+// the operator evaluations of the mixed-precision path); every constant is
+// cast to T so that the float versions stay in FP32.
 #pragma once
 #include "common.cuh"
 
@@ -16,62 +19,61 @@ struct Pde;
 template <>
 struct Pde<0> {   // scalar convection-diffusion, F = a u
     static constexpr int NC = 1;
-    __device__ static void fx(const PdeParams& a, const double* u, double* f) { f[0] = a.ax * u[0]; }
-    __device__ static void fy(const PdeParams& a, const double* u, double* f) { f[0] = a.ay * u[0]; }
-    __device__ static double rx(const PdeParams& a, const double*) { return fabs(a.ax); }
-    __device__ static double ry(const PdeParams& a, const double*) { return fabs(a.ay); }
+    template <class T> __device__ static void fx(const PdeParams& a, const T* u, T* f) { f[0] = T(a.ax) * u[0]; }
+    template <class T> __device__ static void fy(const PdeParams& a, const T* u, T* f) { f[0] = T(a.ay) * u[0]; }
+    template <class T> __device__ static T rx(const PdeParams& a, const T*) { return fabs(T(a.ax)); }
+    template <class T> __device__ static T ry(const PdeParams& a, const T*) { return fabs(T(a.ay)); }
 };
 
 template <>
 struct Pde<1> {   // two-component Burgers, F = u (x) u
     static constexpr int NC = 2;
-    __device__ static void fx(const PdeParams&, const double* u, double* f) {
+    template <class T> __device__ static void fx(const PdeParams&, const T* u, T* f) {
         f[0] = u[0] * u[0];
         f[1] = u[0] * u[1];
     }
-    __device__ static void fy(const PdeParams&, const double* u, double* f) {
+    template <class T> __device__ static void fy(const PdeParams&, const T* u, T* f) {
         f[0] = u[0] * u[1];
         f[1] = u[1] * u[1];
     }
-    __device__ static double rx(const PdeParams&, const double* u) { return 2.0 * fabs(u[0]); }
-    __device__ static double ry(const PdeParams&, const double* u) { return 2.0 * fabs(u[1]); }
+    template <class T> __device__ static T rx(const PdeParams&, const T* u) { return T(2) * fabs(u[0]); }
+    template <class T> __device__ static T ry(const PdeParams&, const T* u) { return T(2) * fabs(u[1]); }
 };
 
 template <>
 struct Pde<2> {   // 2D compressible Euler, perfect gas
     static constexpr int NC = 4;
-    __device__ static double pres(const PdeParams& a, const double* u) {
-        return (a.gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+    template <class T> __device__ static T pres(const PdeParams& a, const T* u) {
+        return (T(a.gamma) - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
     }
-    __device__ static void fx(const PdeParams& a, const double* u, double* f) {
-        const double p = pres(a, u), vx = u[1] / u[0];
+    template <class T> __device__ static void fx(const PdeParams& a, const T* u, T* f) {
+        const T p = pres(a, u), vx = u[1] / u[0];
         f[0] = u[1];
         f[1] = u[1] * vx + p;
         f[2] = u[2] * vx;
         f[3] = (u[3] + p) * vx;
     }
-    __device__ static void fy(const PdeParams& a, const double* u, double* f) {
-        const double p = pres(a, u), vy = u[2] / u[0];
+    template <class T> __device__ static void fy(const PdeParams& a, const T* u, T* f) {
+        const T p = pres(a, u), vy = u[2] / u[0];
         f[0] = u[2];
         f[1] = u[1] * vy;
         f[2] = u[2] * vy + p;
         f[3] = (u[3] + p) * vy;
     }
-    __device__ static double rx(const PdeParams& a, const double* u) {
-        return fabs(u[1] / u[0]) + sqrt(a.gamma * pres(a, u) / u[0]);
+    template <class T> __device__ static T rx(const PdeParams& a, const T* u) {
+        return fabs(u[1] / u[0]) + sqrt(T(a.gamma) * pres(a, u) / u[0]);
     }
-    __device__ static double ry(const PdeParams& a, const double* u) {
-        return fabs(u[2] / u[0]) + sqrt(a.gamma * pres(a, u) / u[0]);
+    template <class T> __device__ static T ry(const PdeParams& a, const T* u) {
+        return fabs(u[2] / u[0]) + sqrt(T(a.gamma) * pres(a, u) / u[0]);
     }
 };
 
 // Rusanov flux between a left/lower state uL and right/upper state uR.
-template <int PDE, bool XDIR>
-__device__ __forceinline__ void rusanov(const PdeParams& a, const double* uL, const double* uR,
-                                        double* Fs) {
+template <int PDE, bool XDIR, class T>
+__device__ __forceinline__ void rusanov(const PdeParams& a, const T* uL, const T* uR, T* Fs) {
     using P = Pde<PDE>;
-    double FL[P::NC], FR[P::NC];
-    double lL, lR;
+    T FL[P::NC], FR[P::NC];
+    T lL, lR;
     if (XDIR) {
         P::fx(a, uL, FL);
         P::fx(a, uR, FR);
@@ -83,9 +85,9 @@ __device__ __forceinline__ void rusanov(const PdeParams& a, const double* uL, co
         lL = P::ry(a, uL);
         lR = P::ry(a, uR);
     }
-    const double lam = fmax(lL, lR);
+    const T lam = fmax(lL, lR);
 #pragma unroll
-    for (int c = 0; c < P::NC; ++c) Fs[c] = 0.5 * (FL[c] + FR[c]) - 0.5 * lam * (uR[c] - uL[c]);
+    for (int c = 0; c < P::NC; ++c) Fs[c] = T(0.5) * (FL[c] + FR[c]) - T(0.5) * lam * (uR[c] - uL[c]);
 }
 
 }  // namespace sisdc

@@ -41,6 +41,7 @@ struct sisdc_level_s {
     double *c0 = nullptr, *dC = nullptr, *tmpc = nullptr;
     double *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *trx = nullptr, *trp = nullptr;
     double* cg_p2 = nullptr;    // second search-direction buffer of the sweep kernel
+    double* cg_rf = nullptr;    // FP32 inner residual of the mixed-precision refinement
     int sw_grid = 0, sw_epb = 0, sw_block = 0;
     double* lam = nullptr;      // [2][MMAX+1]: old, new spectral radius slots
     int pcg_grid = 0, pcg_block = 0;
@@ -286,9 +287,10 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.u0 = u0;
     a.U = U;
     a.G = G;
+    a.mix = c->prob.precision == SISDC_MIXED ? 1 : 0;
     a.F = lv->F; a.CC = lv->CC; a.LU = lv->LU; a.Qb = lv->Qb;
     a.c0 = lv->c0; a.dC = lv->dC; a.tmpc = lv->tmpc;
-    a.r = lv->cg_r; a.p = lv->cg_p; a.p2 = lv->cg_p2; a.Ap = lv->cg_Ap;
+    a.r = lv->cg_r; a.p = lv->cg_p; a.p2 = lv->cg_p2; a.Ap = lv->cg_Ap; a.rf = lv->cg_rf;
     a.lam = lv->lam;
     a.part = c->d_part;
     a.partmax = c->d_part + 8 * (size_t)c->max_grid;
@@ -333,7 +335,7 @@ void predict(sisdc_level_s* lv, const double* u0, double* U, double dt) {
 void residual(sisdc_level_s* lv, const double* u0, const double* U, const double* G, double dt, double* r) {
     sisdc_ctx_s* c = lv->ctx;
     if (!lv->valid || lv->cache_u0 != u0 || lv->cache_U != U) refresh(lv, u0, U);
-    check(c, launch_quad(lv->F, lv->Qb, lv->tab.wnn.data(), lv->M, dt, lv->NV, c->stream), "quad kernel");
+    check(c, launch_quad(lv->F, 0, lv->Qb, lv->tab.wnn.data(), lv->M, dt, lv->NV, c->stream), "quad kernel");
     check(c, launch_fnn(u0, U, lv->Qb, G, r, lv->M, lv->NV, 1, c->stream), "fnn kernel");
     c->launches += 2;
 }
@@ -355,7 +357,7 @@ void vcycle(sisdc_ctx_s* c, LevelPtrs& P, int top, double dt, int Nc) {
         k_transfer(f, T_PROJECT, P.U[l], P.U[l - 1], 0);                        // v_{l-1} = P u_l
         copy_d2d(cl, cl->V, P.U[l - 1], (long long)cl->M * cl->NV);
         refresh(cl, P.u0[l - 1], P.U[l - 1]);
-        check(c, launch_quad(cl->F, cl->Qb, cl->tab.wnn.data(), cl->M, dt, cl->NV, c->stream), "quad kernel");
+        check(c, launch_quad(cl->F, 0, cl->Qb, cl->tab.wnn.data(), cl->M, dt, cl->NV, c->stream), "quad kernel");
         check(c, launch_fnn(P.u0[l - 1], P.U[l - 1], cl->Qb, nullptr, cl->G, cl->M, cl->NV, 0, c->stream),
               "fnn kernel");
         c->launches += 2;
@@ -505,6 +507,8 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     if (d->nel[0] < 1 || ney < 1) return fail(c, SISDC_E_ARG, "nel must be >= 1");
     if (!(d->hi[0] > d->lo[0]) || (d->dim == 2 && !(d->hi[1] > d->lo[1]))) return fail(c, SISDC_E_ARG, "empty box");
     if ((int)c->levels.size() >= 8) return fail(c, SISDC_E_ARG, "at most 8 levels");
+    if (c->prob.precision == SISDC_MIXED && (d->dim != 2 || d->P < 3))
+        return fail(c, SISDC_E_ARG, "mixed precision supports 2D levels with P >= 3");
     if (!c->levels.empty()) {
         const sisdc_level_desc& p = c->levels.back()->desc;
         if (p.dim != d->dim || p.nel[0] != d->nel[0] || (d->dim == 2 && p.nel[1] != d->nel[1]) ||
@@ -573,7 +577,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     // work arrays
     const long long NV = lv->NV, MV = (long long)lv->M * NV;
     const long long ntr = (long long)c->prob.ncomp * lv->nel * 2 * d->dim * 2 * nq;
-    const long long total = 8 * MV + 2 * NV + 3 * NV + 3 * NV + 2 * ntr + 2 * (MMAX + 1);
+    const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1);
     if (e == cudaSuccess) e = cudaMalloc(&lv->d_mem, total * sizeof(double));
     if (e != cudaSuccess) {
         cudaFree(lv->d_tab);
@@ -589,7 +593,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     lv->Qb = take(MV); lv->G = take(MV); lv->V = take(MV); lv->R = take(MV);
     lv->u0 = take(NV); lv->c0 = take(NV);
     lv->dC = take(NV); lv->tmpc = take(NV); lv->cg_r = take(NV);
-    lv->cg_p = take(NV); lv->cg_Ap = take(NV); lv->cg_p2 = take(NV);
+    lv->cg_p = take(NV); lv->cg_Ap = take(NV); lv->cg_p2 = take(NV); lv->cg_rf = take(NV);
     lv->trx = take(ntr); lv->trp = take(ntr);
     lv->lam = take(2 * (MMAX + 1));
     if (lv->index > 0) {
@@ -607,7 +611,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     g.liftLx = g.sx / lv->tab.w[0]; g.liftRx = g.sx / lv->tab.w[nq - 1];
     g.liftLy = g.sy / lv->tab.w[0]; g.liftRy = g.sy / lv->tab.w[nq - 1];
     lv->pcg_grid = pcg_grid(g, &lv->pcg_block);
-    lv->sw_grid = sweep_config(g, c->prob.pde, &lv->sw_epb, &lv->sw_block);
+    lv->sw_grid = sweep_config(g, c->prob.pde, c->prob.precision == SISDC_MIXED, &lv->sw_epb, &lv->sw_block);
     if (lv->pcg_grid < 1 || lv->pcg_grid > c->max_grid || lv->sw_grid < 1 || lv->sw_grid > c->max_grid) {
         cudaFree(lv->d_tab);
         cudaFree(lv->d_mem);

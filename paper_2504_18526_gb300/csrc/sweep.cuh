@@ -7,7 +7,7 @@
 // set of elements (all components) for the whole launch, so elementwise work
 // (right-hand sides, the S.F quadrature, CG vector updates, f updates) needs
 // no synchronisation; only neighbour coupling (face values of c(u), SIPG face
-// traces) and global reductions (CG inner products, the largest spectral
+// lines) and global reductions (CG inner products, the largest spectral
 // radius entering nu_tilde) go through the bounded grid barrier.  Data other
 // blocks write during the launch is read through L2 (__ldcg).
 //
@@ -17,40 +17,69 @@
 // p_old (p is double-buffered), with the same inline arithmetic the owner
 // uses, so both sides of every face see bitwise-identical values and p never
 // has to be published before it is used.
+//
+// MIX = true (mixed precision): the implicit solves run as an iterative
+// refinement whose residual, right-hand side, inner products and solution
+// update are FP64 while the inner CG (its matvecs and vectors) is FP32.  The
+// explicit operator evaluations (c(u), L u) and all cached quantities stay
+// FP64: evaluated in FP32 they perturb every sweep by eps_32 * dt_m * |c|,
+// which the few sweeps of a step do not iterate away.
+//
+// The first residual of a solve whose initial guess is the previous iterate
+// x0 = u^{k-1}_m reuses the cached L x0:  (M + c A) x0 = M x0 - c M L x0.
 #pragma once
+#include <type_traits>
+
 #include "ops.h"
 #include "pde.cuh"
 
 namespace sisdc {
 
-template <int NQ, int DIM, int PDE>
+template <int NQ, int DIM, int PDE, bool MIX>
 struct Sweeper {
     using PD = Pde<PDE>;
+    using RT = typename std::conditional<MIX, float, double>::type;   // operator arithmetic
+    using CT = double;                                                 // cache storage (FP64)
     static constexpr int NC = PD::NC;
     static constexpr int NQY = DIM == 2 ? NQ : 1;
     static constexpr int Q = NQ * NQY;
     static constexpr int NF = 2 * DIM;
     static constexpr int TRS = NF * 2 * NQ;
 
+    static size_t smem_bytes(int epb) {
+        const size_t d = 2 * NQ * NQ + 3 * NQ + 32 + 2 * (MMAX + 1) + Q      // tables, scratch, lam, dinv
+                         + (size_t)epb * NC * Q + (size_t)epb * NC * TRS;    // FP64 tile + faces
+        const size_t d2 = d + (size_t)epb * 2 * NC * Q;                     // FP64 fluxes
+        size_t r = MIX ? (2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q + (size_t)epb * NC * TRS +
+                          (size_t)epb * 2 * NC * Q)                            // RT tables, tile, faces, fluxes
+                       : 0;
+        return d2 * sizeof(double) + r * sizeof(RT) + 16;
+    }
+
     const SweepArgs& a;
     const Geo& g;
     PdeParams pp;
-    double *sD, *sK, *sw, *sdx, *sdy, *scratch, *su, *sf, *sF, *slam_old, *slam_new, *sdinv;
+    double *sD, *sK, *sw, *sdx, *sdy, *scratch, *slam_old, *slam_new, *sdinv, *su, *sf, *sF64;
+    RT *rD, *rK, *rw, *rdx, *rdy, *rdinv, *ru, *rf, *sFR;
     int epb, le, node, i, j, G;
-    long long ntiles, N;
+    long long ntiles, N, NV;
     double mass, diagA;
     int solve_parity;
 
     struct Terms {
         int n;
-        const double* in[6];
+        const void* in[6];
         double cf[6];
-        __device__ void add(const double* p, double c) {
-            in[n] = p;
-            cf[n] = c;
-            ++n;
+        bool f32[6];
+        __device__ void add(const double* p, double c) { in[n] = p; cf[n] = c; f32[n] = false; ++n; }
+        __device__ void add(const float* p, double c) { in[n] = p; cf[n] = c; f32[n] = true; ++n; }
+        __device__ double at(int q, long long id) const {
+            return f32[q] ? (double)__ldcg((const float*)in[q] + id) : __ldcg((const double*)in[q] + id);
         }
     };
+
+    __device__ CT* C(void* p) const { return static_cast<CT*>(p); }
+    __device__ const CT* C(const void* p) const { return static_cast<const CT*>(p); }
 
     __device__ Sweeper(const SweepArgs& args) : a(args), g(args.g) {
         extern __shared__ double sm[];
@@ -64,18 +93,49 @@ struct Sweeper {
         scratch = sdy + NQ;
         slam_old = scratch + 32;
         slam_new = slam_old + MMAX + 1;
-        sdinv = slam_new + MMAX + 1;          // [Q] Jacobi factors of the current solve
-        su = sdinv + Q;                       // [epb][NC][Q]
-        sf = su + epb * NC * Q;               // [epb][NC][NF][2][NQ]
-        sF = sf + epb * NC * TRS;             // [epb][2][NC][Q]
+        sdinv = slam_new + MMAX + 1;
+        su = sdinv + Q;                       // [epb][NC][Q] FP64 tile
+        sf = su + epb * NC * Q;               // [epb][NC][NF][2][NQ] FP64 faces
+        sF64 = sf + epb * NC * TRS;           // [epb][2][NC][Q] FP64 fluxes
+        RT* rbase = reinterpret_cast<RT*>(sF64 + epb * 2 * NC * Q);
+        if (MIX) {
+            rD = rbase;
+            rK = rD + NQ * NQ;
+            rw = rK + NQ * NQ;
+            rdx = rw + NQ;
+            rdy = rdx + NQ;
+            rdinv = rdy + NQ;
+            ru = rdinv + Q;
+            rf = ru + epb * NC * Q;
+            sFR = rf + epb * NC * TRS;
+        } else {
+            rD = reinterpret_cast<RT*>(sD);
+            rK = reinterpret_cast<RT*>(sK);
+            rw = reinterpret_cast<RT*>(sw);
+            rdx = reinterpret_cast<RT*>(sdx);
+            rdy = reinterpret_cast<RT*>(sdy);
+            rdinv = reinterpret_cast<RT*>(sdinv);
+            ru = reinterpret_cast<RT*>(su);
+            rf = reinterpret_cast<RT*>(sf);
+            sFR = reinterpret_cast<RT*>(sF64);
+        }
         for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) {
             sD[t] = g.D[t];
             sK[t] = g.K[t];
+            if (MIX) {
+                rD[t] = (RT)g.D[t];
+                rK[t] = (RT)g.K[t];
+            }
         }
         for (int t = threadIdx.x; t < NQ; t += blockDim.x) {
             sw[t] = g.w[t];
             sdx[t] = g.dline_x[t];
             sdy[t] = g.dline_y[t];
+            if (MIX) {
+                rw[t] = (RT)g.w[t];
+                rdx[t] = (RT)g.dline_x[t];
+                rdy[t] = (RT)g.dline_y[t];
+            }
         }
         for (int t = threadIdx.x; t <= MMAX; t += blockDim.x) {
             slam_old[t] = __ldcg(a.lam + t);
@@ -88,6 +148,7 @@ struct Sweeper {
         G = gridDim.x;
         ntiles = (g.nel + epb - 1) / epb;
         N = g.N;
+        NV = (long long)NC * N;
         solve_parity = 0;
         __syncthreads();
         mass_diag(i, j, mass, diagA);
@@ -130,7 +191,15 @@ struct Sweeper {
         return r;
     }
 
-    // ---- tile helpers -------------------------------------------------------
+    // run f(e0, nle) over the block's element tiles
+    template <class F>
+    __device__ void tiles(F f) {
+        for (long long t = blockIdx.x; t < ntiles; t += G) {
+            const long long e0 = t * epb;
+            f(e0, (int)min((long long)epb, (long long)g.nel - e0));
+        }
+    }
+
     __device__ long long vidx(int c, long long e) const { return c * N + e * Q + node; }
 
     __device__ long long neighbour(long long e, int f) const {
@@ -144,20 +213,21 @@ struct Sweeper {
     // node of the line normal to face f through face row k, position q
     __device__ static int line_node(int f, int k, int q) { return f < 2 ? k * NQ + q : q * NQ + k; }
 
-    // value and physical normal derivative at the face end of a line
-    __device__ void face_line(const double* v, int f, double& val, double& der) const {
+    // ---- SIPG face terms and operator, in arithmetic V ------------------------
+    template <class V>
+    __device__ void face_line(const V* v, int f, const V* Dt, V& val, V& der) const {
         const int end = (f & 1) ? NQ - 1 : 0;
         val = v[end];
-        double s = 0.0;
+        V s = V(0);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) s += sD[end * NQ + q] * v[q];
-        der = s * (f < 2 ? g.sx : g.sy);
+        for (int q = 0; q < NQ; ++q) s += Dt[end * NQ + q] * v[q];
+        der = s * (f < 2 ? V(g.sx) : V(g.sy));
     }
 
     // jumps [u] and averages {u'} on the faces of the tile's elements: own
-    // lines from the tile in su, neighbour lines from getv(c, e, node).
-    template <class GetV>
-    __device__ void faces(int nle, long long e0, GetV getv) {
+    // lines from the tile tu, neighbour lines from getv(c, e, node).
+    template <class V, class GetV>
+    __device__ void faces(int nle, long long e0, const V* tu, V* tf, const V* Dt, GetV getv) {
         const int per = NC * NF * NQ;
         for (int t = threadIdx.x; t < nle * per; t += blockDim.x) {
             const int l = t / per;
@@ -167,81 +237,94 @@ struct Sweeper {
             const int f = rem / NQ, k = rem - f * NQ;
             if (f < 2 && k >= NQY) continue;
             const long long en = neighbour(e0 + l, f);
-            const double* u = su + (l * NC + c) * Q;
-            double vo[NQ], vn[NQ];
+            const V* u = tu + (l * NC + c) * Q;
+            V vo[NQ], vn[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 vo[q] = u[line_node(f, k, q)];
                 vn[q] = getv(c, en, line_node(f ^ 1, k, q));
             }
-            double ov, od, nv, nd;
-            face_line(vo, f, ov, od);
-            face_line(vn, f ^ 1, nv, nd);
-            double jump, avg;
+            V ov, od, nv, nd;
+            face_line(vo, f, Dt, ov, od);
+            face_line(vn, f ^ 1, Dt, nv, nd);
+            V jump, avg;
             if ((f & 1) == 0) {
                 jump = nv - ov;
-                avg = 0.5 * (nd + od);
+                avg = V(0.5) * (nd + od);
             } else {
                 jump = ov - nv;
-                avg = 0.5 * (od + nd);
+                avg = V(0.5) * (od + nd);
             }
-            double* o = sf + ((l * NC + c) * NF + f) * 2 * NQ;
+            V* o = tf + ((l * NC + c) * NF + f) * 2 * NQ;
             o[k] = jump;
             o[NQ + k] = avg;
         }
     }
 
-    // new search direction at one node (shared by owner and neighbours)
-    __device__ static double pnew(double r, double dinv, double beta, double pold) {
-        const double z = r * dinv;
-        return beta == 0.0 ? z : z + beta * pold;
-    }
-
-    // (A u)(i, j) for component c of local element l (tile in su, faces in sf)
-    __device__ double opA(int l, int c) const {
-        const double* u = su + (l * NC + c) * Q;
-        const double* f = sf + (l * NC + c) * TRS;
-        double ax = 0.0;
+    // (A u)(i, j) for component c of local element l
+    template <class V>
+    __device__ V opA(int l, int c, const V* tu, const V* tf, const V* Dt, const V* Kt, const V* wt) const {
+        const V* u = tu + (l * NC + c) * Q;
+        const V* f = tf + (l * NC + c) * TRS;
+        V ax = V(0);
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) ax += sK[i * NQ + k] * u[j * NQ + k];
-        ax *= g.sx;
-        ax -= g.ihx * (sD[(NQ - 1) * NQ + i] * f[2 * NQ + j] + sD[i] * f[j]);
-        if (i == NQ - 1) ax += -f[3 * NQ + j] + g.taux * f[2 * NQ + j];
-        if (i == 0) ax += f[NQ + j] - g.taux * f[j];
+        for (int k = 0; k < NQ; ++k) ax += Kt[i * NQ + k] * u[j * NQ + k];
+        ax *= V(g.sx);
+        ax -= V(g.ihx) * (Dt[(NQ - 1) * NQ + i] * f[2 * NQ + j] + Dt[i] * f[j]);
+        if (i == NQ - 1) ax += -f[3 * NQ + j] + V(g.taux) * f[2 * NQ + j];
+        if (i == 0) ax += f[NQ + j] - V(g.taux) * f[j];
         if (DIM == 1) return ax;
-        double ay = 0.0;
+        V ay = V(0);
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) ay += sK[j * NQ + k] * u[k * NQ + i];
-        ay *= g.sy;
-        ay -= g.ihy * (sD[(NQ - 1) * NQ + j] * f[6 * NQ + i] + sD[j] * f[4 * NQ + i]);
-        if (j == NQ - 1) ay += -f[7 * NQ + i] + g.tauy * f[6 * NQ + i];
-        if (j == 0) ay += f[5 * NQ + i] - g.tauy * f[4 * NQ + i];
-        return (0.5 * g.hy * sw[j]) * ax + (0.5 * g.hx * sw[i]) * ay;
+        for (int k = 0; k < NQ; ++k) ay += Kt[j * NQ + k] * u[k * NQ + i];
+        ay *= V(g.sy);
+        ay -= V(g.ihy) * (Dt[(NQ - 1) * NQ + j] * f[6 * NQ + i] + Dt[j] * f[4 * NQ + i]);
+        if (j == NQ - 1) ay += -f[7 * NQ + i] + V(g.tauy) * f[6 * NQ + i];
+        if (j == 0) ay += f[5 * NQ + i] - V(g.tauy) * f[4 * NQ + i];
+        return (V(0.5) * V(g.hy) * wt[j]) * ax + (V(0.5) * V(g.hx) * wt[i]) * ay;
+    }
+    __device__ double opA64(int l, int c) const { return opA<double>(l, c, su, sf, sD, sK, sw); }
+    __device__ RT opAR(int l, int c) const { return opA<RT>(l, c, ru, rf, rD, rK, rw); }
+
+    // new search direction at one node (shared by owner and neighbours)
+    template <class V>
+    __device__ static V pnew(V r, V dinv, V beta, V pold) {
+        const V z = r * dinv;
+        return beta == V(0) ? z : z + beta * pold;
     }
 
-    // run f(e0, nle) over the block's element tiles
-    template <class F>
-    __device__ void tiles(F f) {
-        for (long long t = blockIdx.x; t < ntiles; t += G) {
-            const long long e0 = t * epb;
-            f(e0, (int)min((long long)epb, (long long)g.nel - e0));
-        }
-    }
-
-    // ---- implicit solve -------------------------------------------------------
-    // (M + c A) x = M b, b = sum_t cf_t in_t.  The initial guess is xsrc (x
-    // itself when xsrc == x); neighbours' xsrc must be final on entry.
-    __device__ bool solve(double* x, const double* xsrc, const Terms& tm, double c) {
-        double* part = a.part + (size_t)(solve_parity ? 4 : 0) * G;
-        solve_parity ^= 1;
+    __device__ void set_dinv(double c) {
         __syncthreads();
         for (int t = threadIdx.x; t < Q; t += blockDim.x) {
-            const int ii = t % NQ, jj = t / NQ;
             double ms, dg;
-            mass_diag(ii, jj, ms, dg);
+            mass_diag(t % NQ, t / NQ, ms, dg);
             sdinv[t] = 1.0 / (ms + c * dg);
+            if (MIX) rdinv[t] = (RT)sdinv[t];
         }
         __syncthreads();
+    }
+
+    __device__ void stat_solve(int it, bool fin, bool conv_ok) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicAdd((unsigned long long*)&a.stats[ST_SOLVES], 1ull);
+            atomicAdd((unsigned long long*)&a.stats[ST_ITERS], (unsigned long long)it);
+            atomicMax((unsigned long long*)&a.stats[ST_MAXIT], (unsigned long long)it);
+            if (!fin) {
+                atomicOr(a.err, DEV_NONFINITE);
+            } else if (!conv_ok) {
+                atomicOr(a.err, DEV_NOCONV);
+                atomicAdd((unsigned long long*)&a.stats[ST_NOCONV], 1ull);
+            }
+        }
+    }
+
+    // ---- implicit solve (FP64) ---------------------------------------------------
+    // (M + c A) x = M b, b = sum_t cf_t in_t.  The initial guess is xsrc (x
+    // itself when xsrc == x); neighbours' xsrc must be final on entry.
+    __device__ bool solve64(double* x, const double* xsrc, const Terms& tm, double c, const double* Lx0) {
+        double* part = a.part + (size_t)(solve_parity ? 8 : 0) * G;
+        solve_parity ^= 1;
+        set_dinv(c);
         const double dinv = sdinv[node];
         double acc_bb = 0.0, acc = 0.0;
         tiles([&](const long long e0, const int nle) {
@@ -257,7 +340,8 @@ struct Sweeper {
                 }
             }
             __syncthreads();
-            faces(nle, e0, [&](int cc, long long en, int nd) { return __ldcg(xsrc + cc * N + en * Q + nd); });
+            if (!Lx0)
+                faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) { return __ldcg(xsrc + cc * N + en * Q + nd); });
             __syncthreads();
             if (act) {
 #pragma unroll
@@ -266,10 +350,11 @@ struct Sweeper {
                     double b = 0.0;
 #pragma unroll
                     for (int q = 0; q < 6; ++q)
-                        if (q < tm.n) b += tm.cf[q] * __ldcg(tm.in[q] + id);
+                        if (q < tm.n) b += tm.cf[q] * tm.at(q, id);
                     const double mb = mass * b;
                     const double xv = su[(le * NC + cc) * Q + node];
-                    const double rr = mb - (mass * xv + c * opA(le, cc));
+                    const double Ax = Lx0 ? -mass * __ldcg(Lx0 + id) : opA64(le, cc);
+                    const double rr = mb - (mass * xv + c * Ax);
                     a.r[id] = rr;
                     acc_bb += mb * mb * dinv;
                     acc += rr * (rr * dinv);
@@ -286,9 +371,12 @@ struct Sweeper {
         bool fin = isfinite(rz) && isfinite(bb);
         int it = 0, par = 0;
         double beta = 0.0;
+        double* P0 = static_cast<double*>(a.p);
+        double* P1 = static_cast<double*>(a.p2);
+        double* AP = static_cast<double*>(a.Ap);
         while (fin && rz > tol2 && it < a.maxit) {
-            const double* pold = par ? a.p2 : a.p;
-            double* pcur = par ? a.p : a.p2;
+            const double* pold = par ? P1 : P0;
+            double* pcur = par ? P0 : P1;
             acc = 0.0;
             tiles([&](const long long e0, const int nle) {
                 const bool act = le < nle;
@@ -298,22 +386,22 @@ struct Sweeper {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
                         const long long id = vidx(cc, e);
-                        pn[cc] = pnew(__ldcg(a.r + id), dinv, beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
+                        pn[cc] = pnew<double>(__ldcg(a.r + id), dinv, beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
                         pcur[id] = pn[cc];
                         su[(le * NC + cc) * Q + node] = pn[cc];
                     }
                 }
                 __syncthreads();
-                faces(nle, e0, [&](int cc, long long en, int nd) {
+                faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) {
                     const long long id = cc * N + en * Q + nd;
-                    return pnew(__ldcg(a.r + id), sdinv[nd], beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
+                    return pnew<double>(__ldcg(a.r + id), sdinv[nd], beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
                 });
                 __syncthreads();
                 if (act) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        const double Apv = mass * pn[cc] + c * opA(le, cc);
-                        a.Ap[vidx(cc, e)] = Apv;
+                        const double Apv = mass * pn[cc] + c * opA64(le, cc);
+                        AP[vidx(cc, e)] = Apv;
                         acc += pn[cc] * Apv;
                     }
                 }
@@ -330,7 +418,7 @@ struct Sweeper {
                     for (int cc = 0; cc < NC; ++cc) {
                         const long long id = vidx(cc, e);
                         x[id] = __ldcg(x + id) + alpha * __ldcg(pcur + id);
-                        const double rr = __ldcg(a.r + id) - alpha * __ldcg(a.Ap + id);
+                        const double rr = __ldcg(a.r + id) - alpha * __ldcg(AP + id);
                         a.r[id] = rr;
                         acc += rr * (rr * dinv);
                     }
@@ -345,109 +433,260 @@ struct Sweeper {
             par ^= 1;
             fin = isfinite(rz);
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            atomicAdd((unsigned long long*)&a.stats[ST_SOLVES], 1ull);
-            atomicAdd((unsigned long long*)&a.stats[ST_ITERS], (unsigned long long)it);
-            atomicMax((unsigned long long*)&a.stats[ST_MAXIT], (unsigned long long)it);
-            if (!fin) {
-                atomicOr(a.err, DEV_NONFINITE);
-            } else if (rz > tol2) {
-                atomicOr(a.err, DEV_NOCONV);
-                atomicAdd((unsigned long long*)&a.stats[ST_NOCONV], 1ull);
-            }
-        }
+        stat_solve(it, fin, !(rz > tol2));
         return true;
     }
 
-    // ---- convective operator phase -------------------------------------------
-    // c(X) for the block's elements; out by mode; optional spectral-radius
-    // partial into lamslot; optional traces of X into trout.
-    __device__ void conv(const double* X, int mode, double* out, double* lamslot) {
+    // ---- implicit solve (mixed: FP64 refinement residual, FP32 inner PCG) --------
+    // Outer iterative refinement in FP64: r = M b - (M + c A) x with the FP64
+    // operator; inner Jacobi-PCG in FP32 on (M + c A) d = r from d = 0 with
+    // FP64-accumulated inner products; x += d accumulated in FP64.  Stops when
+    // the FP64 residual meets the same criterion as the FP64 solve.
+    __device__ bool solve_mix(double* x, const double* xsrc, const Terms& tm, double c, const double* Lx0) {
+        double* part = a.part + (size_t)(solve_parity ? 8 : 0) * G;
+        solve_parity ^= 1;
+        set_dinv(c);
+        const double dinv = sdinv[node];
+        const RT dinvr = rdinv[node];
+        const RT cr = (RT)c, massr = (RT)mass;
+        RT* RF = static_cast<RT*>(a.rf);
+        RT* P0 = static_cast<RT*>(a.p);
+        RT* P1 = static_cast<RT*>(a.p2);
+        RT* AP = static_cast<RT*>(a.Ap);
+        double bb = 0.0, tol2 = 0.0;
+        bool fin = true, done = false;
+        int its = 0, ir = 0;
+        const int max_ir = 30;
+        for (; ir < max_ir; ++ir) {
+            // FP64 refinement residual (first pass also forms M b and copies xsrc)
+            const double* xs = ir == 0 ? xsrc : x;
+            double acc_bb = 0.0, acc64 = 0.0, acc32 = 0.0;
+            tiles([&](const long long e0, const int nle) {
+                const bool act = le < nle;
+                const long long e = e0 + le;
+                if (act) {
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) {
+                        const long long id = vidx(cc, e);
+                        const double xv = __ldcg(xs + id);
+                        su[(le * NC + cc) * Q + node] = xv;
+                        if (ir == 0 && xsrc != x) x[id] = xv;
+                    }
+                }
+                __syncthreads();
+                if (!(ir == 0 && Lx0))
+                    faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) { return __ldcg(xs + cc * N + en * Q + nd); });
+                __syncthreads();
+                if (act) {
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) {
+                        const long long id = vidx(cc, e);
+                        double mb;
+                        if (ir == 0) {
+                            double b = 0.0;
+#pragma unroll
+                            for (int q = 0; q < 6; ++q)
+                                if (q < tm.n) b += tm.cf[q] * tm.at(q, id);
+                            mb = mass * b;
+                            a.r[id] = mb;
+                            acc_bb += mb * mb * dinv;
+                        } else {
+                            mb = __ldcg(a.r + id);
+                        }
+                        const double xv = su[(le * NC + cc) * Q + node];
+                        const double Ax = (ir == 0 && Lx0) ? -mass * __ldcg(Lx0 + id) : opA64(le, cc);
+                        const double r64 = mb - (mass * xv + c * Ax);
+                        acc64 += r64 * (r64 * dinv);
+                        const RT r32 = (RT)r64;
+                        RF[id] = r32;
+                        acc32 += (double)r32 * (double)(r32 * dinvr);
+                    }
+                }
+                __syncthreads();
+            });
+            if (ir == 0) put_partial(part, acc_bb);
+            put_partial(part + G, acc64);
+            put_partial(part + 2 * G, acc32);
+            if (!bar()) return false;
+            if (ir == 0) {
+                bb = total(part);
+                tol2 = fmax(a.rtol * a.rtol * bb, 1e-300);
+            }
+            const double rz64 = total(part + G);
+            double rz = total(part + 2 * G);
+            fin = isfinite(rz64) && isfinite(bb);
+            if (!fin || !(rz64 > tol2)) {
+                done = fin;
+                break;
+            }
+            // inner FP32 PCG from d = 0 (x += alpha p applied to x directly)
+            const double tol_in = fmax(1e-10 * rz, 0.25 * tol2);
+            int par = 0;
+            double beta = 0.0;
+            while (rz > tol_in && its < a.maxit) {
+                const RT* pold = par ? P1 : P0;
+                RT* pcur = par ? P0 : P1;
+                const RT betar = (RT)beta;
+                double acc = 0.0;
+                tiles([&](const long long e0, const int nle) {
+                    const bool act = le < nle;
+                    const long long e = e0 + le;
+                    RT pn[NC];
+                    if (act) {
+#pragma unroll
+                        for (int cc = 0; cc < NC; ++cc) {
+                            const long long id = vidx(cc, e);
+                            pn[cc] = pnew<RT>(__ldcg(RF + id), dinvr, betar, betar == RT(0) ? RT(0) : __ldcg(pold + id));
+                            pcur[id] = pn[cc];
+                            ru[(le * NC + cc) * Q + node] = pn[cc];
+                        }
+                    }
+                    __syncthreads();
+                    faces<RT>(nle, e0, ru, rf, rD, [&](int cc, long long en, int nd) {
+                        const long long id = cc * N + en * Q + nd;
+                        return pnew<RT>(__ldcg(RF + id), rdinv[nd], betar, betar == RT(0) ? RT(0) : __ldcg(pold + id));
+                    });
+                    __syncthreads();
+                    if (act) {
+#pragma unroll
+                        for (int cc = 0; cc < NC; ++cc) {
+                            const RT Apv = massr * pn[cc] + cr * opAR(le, cc);
+                            AP[vidx(cc, e)] = Apv;
+                            acc += (double)pn[cc] * (double)Apv;
+                        }
+                    }
+                    __syncthreads();
+                });
+                put_partial(part + 3 * G, acc);
+                if (!bar()) return false;
+                const double alpha = rz / total(part + 3 * G);
+                const RT alphar = (RT)alpha;
+                acc = 0.0;
+                tiles([&](const long long e0, const int nle) {
+                    if (le < nle) {
+                        const long long e = e0 + le;
+#pragma unroll
+                        for (int cc = 0; cc < NC; ++cc) {
+                            const long long id = vidx(cc, e);
+                            x[id] = __ldcg(x + id) + alpha * (double)__ldcg(pcur + id);
+                            const RT rr = __ldcg(RF + id) - alphar * __ldcg(AP + id);
+                            RF[id] = rr;
+                            acc += (double)rr * (double)(rr * dinvr);
+                        }
+                    }
+                });
+                put_partial(part + 4 * G, acc);
+                if (!bar()) return false;
+                const double rzn = total(part + 4 * G);
+                beta = rzn / rz;
+                rz = rzn;
+                ++its;
+                par ^= 1;
+                if (!isfinite(rz)) break;
+            }
+            if (its >= a.maxit) break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            atomicAdd((unsigned long long*)&a.stats[ST_IR], (unsigned long long)(ir + 1));
+        stat_solve(its, fin, done);
+        return true;
+    }
+
+    // Lx0 (nullable): cached L xsrc, which replaces the first matvec
+    __device__ bool solve(double* x, const double* xsrc, const Terms& tm, double c, const double* Lx0 = nullptr) {
+        if (MIX) return solve_mix(x, xsrc, tm, c, Lx0);
+        return solve64(x, xsrc, tm, c, Lx0);
+    }
+
+    // ---- convective operator phase (arithmetic V) ------------------------------
+    // c(X) for the block's elements into out (CT); mode CONV_DELTA also
+    // writes dC = c - out_old; f64 (optional) receives c in FP64 (the start of
+    // the cached f); optional spectral-radius partial into lamslot.
+    template <class V>
+    __device__ void conv(const double* X, int mode, CT* out, double* f64, double* lamslot) {
+        V* sFv = std::is_same<V, double>::value ? reinterpret_cast<V*>(sF64) : reinterpret_cast<V*>(sFR);
+        const V* Dv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sD) : reinterpret_cast<const V*>(rD);
         double lmax = 0.0;
         tiles([&](const long long e0, const int nle) {
             const bool act = le < nle;
             const long long e = e0 + le;
-            double u[NC], Fx[NC], Fy[NC];
-            double* sFx = sF + (size_t)le * 2 * NC * Q;
-            double* sFy = sFx + NC * Q;
+            V u[NC], Fx[NC], Fy[NC];
+            V* sFx = sFv + (size_t)le * 2 * NC * Q;
+            V* sFy = sFx + NC * Q;
             if (act) {
 #pragma unroll
-                for (int cc = 0; cc < NC; ++cc) {
-                    u[cc] = __ldcg(X + vidx(cc, e));
-                    su[(le * NC + cc) * Q + node] = u[cc];
-                }
+                for (int cc = 0; cc < NC; ++cc) u[cc] = (V)__ldcg(X + vidx(cc, e));
                 PD::fx(pp, u, Fx);
-                lmax = fmax(lmax, PD::rx(pp, u));
+                lmax = fmax(lmax, (double)PD::rx(pp, u));
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) sFx[cc * Q + node] = Fx[cc];
                 if (DIM == 2) {
                     PD::fy(pp, u, Fy);
-                    lmax = fmax(lmax, PD::ry(pp, u));
+                    lmax = fmax(lmax, (double)PD::ry(pp, u));
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) sFy[cc * Q + node] = Fy[cc];
                 }
             }
             __syncthreads();
             if (act) {
-                double cv[NC];
+                V cv[NC];
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
-                    double s = 0.0;
+                    V s = V(0);
 #pragma unroll
-                    for (int k = 0; k < NQ; ++k) s += sD[i * NQ + k] * sFx[cc * Q + j * NQ + k];
-                    cv[cc] = -g.sx * s;
+                    for (int k = 0; k < NQ; ++k) s += Dv[i * NQ + k] * sFx[cc * Q + j * NQ + k];
+                    cv[cc] = -V(g.sx) * s;
                 }
                 if (DIM == 2) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        double s = 0.0;
+                        V s = V(0);
 #pragma unroll
-                        for (int k = 0; k < NQ; ++k) s += sD[j * NQ + k] * sFy[cc * Q + k * NQ + i];
-                        cv[cc] -= g.sy * s;
+                        for (int k = 0; k < NQ; ++k) s += Dv[j * NQ + k] * sFy[cc * Q + k * NQ + i];
+                        cv[cc] -= V(g.sy) * s;
                     }
                 }
-                double un[NC], Fs[NC];
+                V un[NC], Fs[NC];
                 if (i == NQ - 1) {
                     const long long en = neighbour(e, 1);
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) un[cc] = __ldcg(X + cc * N + en * Q + j * NQ);
+                    for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + j * NQ);
                     rusanov<PDE, true>(pp, u, un, Fs);
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) cv[cc] -= g.liftRx * (Fs[cc] - Fx[cc]);
+                    for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(g.liftRx) * (Fs[cc] - Fx[cc]);
                 }
                 if (i == 0) {
                     const long long en = neighbour(e, 0);
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) un[cc] = __ldcg(X + cc * N + en * Q + j * NQ + NQ - 1);
+                    for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + j * NQ + NQ - 1);
                     rusanov<PDE, true>(pp, un, u, Fs);
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) cv[cc] += g.liftLx * (Fs[cc] - Fx[cc]);
+                    for (int cc = 0; cc < NC; ++cc) cv[cc] += V(g.liftLx) * (Fs[cc] - Fx[cc]);
                 }
                 if (DIM == 2) {
                     if (j == NQ - 1) {
                         const long long en = neighbour(e, 3);
 #pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) un[cc] = __ldcg(X + cc * N + en * Q + i);
+                        for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + i);
                         rusanov<PDE, false>(pp, u, un, Fs);
 #pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) cv[cc] -= g.liftRy * (Fs[cc] - Fy[cc]);
+                        for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(g.liftRy) * (Fs[cc] - Fy[cc]);
                     }
                     if (j == 0) {
                         const long long en = neighbour(e, 2);
 #pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) un[cc] = __ldcg(X + cc * N + en * Q + (NQ - 1) * NQ + i);
+                        for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + (NQ - 1) * NQ + i);
                         rusanov<PDE, false>(pp, un, u, Fs);
 #pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) cv[cc] += g.liftLy * (Fs[cc] - Fy[cc]);
+                        for (int cc = 0; cc < NC; ++cc) cv[cc] += V(g.liftLy) * (Fs[cc] - Fy[cc]);
                     }
                 }
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
                     const long long id = vidx(cc, e);
-                    if (mode == CONV_DELTA) {
-                        a.dC[id] = cv[cc] - __ldcg(out + id);
-                    }
-                    out[id] = cv[cc];
+                    if (mode == CONV_DELTA) C(a.dC)[id] = (CT)((double)cv[cc] - (double)__ldcg(out + id));
+                    out[id] = (CT)cv[cc];
+                    if (f64) f64[id] = (double)cv[cc];
                 }
             }
             __syncthreads();
@@ -455,32 +694,40 @@ struct Sweeper {
         if (lamslot) put_partial_max(lamslot, lmax);
     }
 
-    // LU = L X, F = CC + nu LU (neighbours' X must be final)
-    __device__ void lap(const double* X, double* LUm, double* Fm, const double* CCm) {
+    // LU = L X (arithmetic V, stored CT); F += nu LU in FP64, F holding c(X)
+    // from the conv phase of the same block (neighbours' X must be final)
+    template <class V>
+    __device__ void lap(const double* X, CT* LUm, double* Fm) {
+        V* tu = std::is_same<V, double>::value ? reinterpret_cast<V*>(su) : reinterpret_cast<V*>(ru);
+        V* tf = std::is_same<V, double>::value ? reinterpret_cast<V*>(sf) : reinterpret_cast<V*>(rf);
+        const V* Dv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sD) : reinterpret_cast<const V*>(rD);
+        const V* Kv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sK) : reinterpret_cast<const V*>(rK);
+        const V* wv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sw) : reinterpret_cast<const V*>(rw);
+        const V massv = (V)mass;
         tiles([&](const long long e0, const int nle) {
             const bool act = le < nle;
             const long long e = e0 + le;
             if (act) {
 #pragma unroll
-                for (int cc = 0; cc < NC; ++cc) su[(le * NC + cc) * Q + node] = __ldcg(X + vidx(cc, e));
+                for (int cc = 0; cc < NC; ++cc) tu[(le * NC + cc) * Q + node] = (V)__ldcg(X + vidx(cc, e));
             }
             __syncthreads();
-            faces(nle, e0, [&](int cc, long long en, int nd) { return __ldcg(X + cc * N + en * Q + nd); });
+            faces<V>(nle, e0, tu, tf, Dv, [&](int cc, long long en, int nd) { return (V)__ldcg(X + cc * N + en * Q + nd); });
             __syncthreads();
             if (act) {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
                     const long long id = vidx(cc, e);
-                    const double lu = -opA(le, cc) / mass;
-                    LUm[id] = lu;
-                    Fm[id] = __ldcg(CCm + id) + a.nu * lu;
+                    const V lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) / massv;
+                    LUm[id] = (CT)lu;
+                    Fm[id] = __ldcg(Fm + id) + a.nu * (double)lu;
                 }
             }
             __syncthreads();
         });
     }
 
-    // elementwise: out = sum_t cf_t in_t over the block's nodes
+    // elementwise: out = sum_t cf_t in_t over the block's nodes (FP64)
     __device__ void lin(double* out, const Terms& tm) {
         tiles([&](const long long e0, const int nle) {
             if (le < nle) {
@@ -491,7 +738,7 @@ struct Sweeper {
                     double v = 0.0;
 #pragma unroll
                     for (int q = 0; q < 6; ++q)
-                        if (q < tm.n) v += tm.cf[q] * __ldcg(tm.in[q] + id);
+                        if (q < tm.n) v += tm.cf[q] * tm.at(q, id);
                     out[id] = v;
                 }
             }
@@ -500,6 +747,7 @@ struct Sweeper {
 
     // elementwise S.F quadrature Q_m = dt sum_i W[m][i] F_i (FP64 accumulation)
     __device__ void quad() {
+        const double* F = a.F;
         tiles([&](const long long e0, const int nle) {
             if (le < nle) {
                 const long long e = e0 + le;
@@ -508,7 +756,7 @@ struct Sweeper {
                     const long long id = vidx(cc, e);
                     double f[MMAX];
 #pragma unroll
-                    for (int q = 0; q < MMAX; ++q) f[q] = q < a.M ? __ldcg(a.F + q * (NC * N) + id) : 0.0;
+                    for (int q = 0; q < MMAX; ++q) f[q] = q < a.M ? (double)__ldcg(F + q * NV + id) : 0.0;
 #pragma unroll
                     for (int m = 0; m < MMAX; ++m) {
                         if (m >= a.M) break;
@@ -516,7 +764,7 @@ struct Sweeper {
 #pragma unroll
                         for (int q = 0; q < MMAX; ++q)
                             if (q < a.M) s += a.W[m * a.M + q] * f[q];
-                        a.Qb[m * (NC * N) + id] = a.dt * s;
+                        a.Qb[m * NV + id] = a.dt * s;
                     }
                 }
             }
@@ -524,15 +772,16 @@ struct Sweeper {
     }
 
     __device__ double nut(double dtm, double lam) const { return a.nu_d + 0.5 * dtm * lam * lam; }
-    __device__ double* Um(double* U, int m) const { return U + (long long)m * NC * N; }
-    __device__ const double* Um(const double* U, int m) const { return U + (long long)m * NC * N; }
+    __device__ double* Um(double* U, int m) const { return U + (long long)m * NV; }
+    __device__ const double* Um(const double* U, int m) const { return U + (long long)m * NV; }
+    __device__ CT* Cm(void* A, int m) const { return C(A) + (long long)m * NV; }
 
     // ---- the three modes ------------------------------------------------------
     __device__ bool refresh() {
-        conv(a.u0, CONV_OUT, a.c0, a.partmax);
+        conv<double>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
         for (int m = 0; m < a.M; ++m) {
-            conv(Um(a.U, m), CONV_OUT, Um(a.CC, m), a.partmax + (size_t)(m + 1) * G);
-            lap(Um(a.U, m), Um(a.LU, m), Um(a.F, m), Um(a.CC, m));
+            conv<double>(Um(a.U, m), CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+            lap<double>(Um(a.U, m), Cm(a.LU, m), Um(a.F, m));
         }
         if (!bar()) return false;
         for (int m = 0; m <= a.M; ++m) {
@@ -545,26 +794,26 @@ struct Sweeper {
     }
 
     __device__ bool predict() {
-        conv(a.u0, CONV_OUT, a.c0, a.partmax);
+        conv<double>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
         if (!bar()) return false;
         double lam = total_max(a.partmax);
         if (threadIdx.x == 0) slam_new[0] = lam;
         for (int m = 0; m < a.M; ++m) {
             const double dtm = a.dt * a.dtau[m];
             const double* up = m ? Um((const double*)a.U, m - 1) : a.u0;
-            const double* cp = m ? Um((const double*)a.CC, m - 1) : a.c0;
+            const CT* cp = m ? Cm(a.CC, m - 1) : C((const void*)a.c0);
             double* um = Um(a.U, m);
             if (dtm != 0.0) {
                 const double cimp = dtm * nut(dtm, lam);
                 Terms t1{};
                 t1.add(up, 1.0);
                 t1.add(cp, dtm);
-                if (!solve(um, up, t1, cimp)) return false;     // warm start u_{m-1}
+                if (!solve(um, up, t1, cimp, m ? Cm(a.LU, m - 1) : nullptr)) return false;   // warm start u_{m-1}
                 if (a.stages == 2) {
-                    conv(um, CONV_OUT, a.tmpc, nullptr);
+                    conv<double>(um, CONV_OUT, C(a.tmpc), nullptr, nullptr);
                     Terms t2{};
                     t2.add(up, 1.0);
-                    t2.add(a.tmpc, dtm);
+                    t2.add((const CT*)C(a.tmpc), dtm);
                     if (!solve(um, um, t2, cimp)) return false;
                 }
             } else {
@@ -573,8 +822,8 @@ struct Sweeper {
                 lin(um, t0);                               // Lobatto t_1 = t_0
                 if (!bar()) return false;
             }
-            conv(um, CONV_OUT, Um(a.CC, m), a.partmax + (size_t)(m + 1) * G);
-            lap(um, Um(a.LU, m), Um(a.F, m), Um(a.CC, m));
+            conv<double>(um, CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+            lap<double>(um, Cm(a.LU, m), Um(a.F, m));
             if (!bar()) return false;
             lam = total_max(a.partmax + (size_t)(m + 1) * G);
             if (threadIdx.x == 0) slam_new[m + 1] = lam;
@@ -606,19 +855,19 @@ struct Sweeper {
                     t1.add(up, 1.0);
                     t1.add(Um((const double*)a.Qb, m), 1.0);
                     if (a.G) t1.add(Um(a.G, m), 1.0);
-                    t1.add(Um((const double*)a.LU, m), -dtm * nu_old);
+                    t1.add((const CT*)Cm(a.LU, m), -dtm * nu_old);
                     Terms t2 = t1;
-                    if (m > 0) t1.add(a.dC, dtm);          // c(u^k_{m-1}) - c(u^{k-1}_{m-1})
-                    if (!solve(um, um, t1, dtm * nu_new)) return false;
+                    if (m > 0) t1.add((const CT*)C(a.dC), dtm);          // c(u^k_{m-1}) - c(u^{k-1}_{m-1})
+                    if (!solve(um, um, t1, dtm * nu_new, Cm(a.LU, m))) return false;
                     if (a.stages == 2) {
-                        conv(um, CONV_OUT, a.tmpc, nullptr);
-                        t2.add(a.tmpc, dtm);               // c(u^(1))
-                        t2.add(Um((const double*)a.CC, m), -dtm);   // c(u^{k-1}_m)
+                        conv<double>(um, CONV_OUT, C(a.tmpc), nullptr, nullptr);
+                        t2.add((const CT*)C(a.tmpc), dtm);               // c(u^(1))
+                        t2.add((const CT*)Cm(a.CC, m), -dtm);            // c(u^{k-1}_m)
                         if (!solve(um, um, t2, dtm * nu_new)) return false;
                     }
                 }
-                conv(um, CONV_DELTA, Um(a.CC, m), a.partmax + (size_t)(m + 1) * G);
-                lap(um, Um(a.LU, m), Um(a.F, m), Um(a.CC, m));
+                conv<double>(um, CONV_DELTA, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+                lap<double>(um, Cm(a.LU, m), Um(a.F, m));
                 if (!bar()) return false;
                 lam = total_max(a.partmax + (size_t)(m + 1) * G);
                 if (threadIdx.x == 0) slam_new[m + 1] = lam;
@@ -641,9 +890,9 @@ struct Sweeper {
     }
 };
 
-template <int NQ, int DIM, int PDE>
+template <int NQ, int DIM, int PDE, bool MIX>
 __global__ void __launch_bounds__(512, 1) k_sweep(const __grid_constant__ SweepArgs a) {
-    Sweeper<NQ, DIM, PDE> s(a);
+    Sweeper<NQ, DIM, PDE, MIX> s(a);
     bool ok;
     if (a.mode == SW_REFRESH) ok = s.refresh();
     else if (a.mode == SW_PREDICT) ok = s.predict();
@@ -651,16 +900,14 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const __grid_constant__ SweepA
     if (ok) s.finish();
 }
 
-template <int NQ, int DIM, int PDE>
+template <int NQ, int DIM, int PDE, bool MIX>
 size_t sweep_smem(int epb) {
-    using S = Sweeper<NQ, DIM, PDE>;
-    return (2 * NQ * NQ + 3 * NQ + 32 + 2 * (MMAX + 1) + S::Q + (size_t)epb * S::NC * S::Q +
-            (size_t)epb * S::NC * S::TRS + (size_t)epb * 2 * S::NC * S::Q) * sizeof(double);
+    return Sweeper<NQ, DIM, PDE, MIX>::smem_bytes(epb);
 }
 
-template <int NQ, int DIM, int PDE>
+template <int NQ, int DIM, int PDE, bool MIX>
 int sweep_config_impl(const Geo& g, int* epb_out, int* block_out) {
-    using S = Sweeper<NQ, DIM, PDE>;
+    using S = Sweeper<NQ, DIM, PDE, MIX>;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -670,10 +917,11 @@ int sweep_config_impl(const Geo& g, int* epb_out, int* block_out) {
     const int minepb = (32 + S::Q - 1) / S::Q;     // at least one warp per block
     if (epb < minepb) epb = minepb > maxepb ? maxepb : minepb;
     const int bs = epb * S::Q;
-    const size_t sh = sweep_smem<NQ, DIM, PDE>(epb);
-    cudaFuncSetAttribute(k_sweep<NQ, DIM, PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    const size_t sh = sweep_smem<NQ, DIM, PDE, MIX>(epb);
+    cudaFuncSetAttribute(k_sweep<NQ, DIM, PDE, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<NQ, DIM, PDE>, bs, sh) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<NQ, DIM, PDE, MIX>, bs, sh) != cudaSuccess ||
+        per < 1)
         return 0;
     const long long ntiles = (g.nel + epb - 1) / epb;
     long long grid = (long long)per * nsm;
@@ -683,19 +931,19 @@ int sweep_config_impl(const Geo& g, int* epb_out, int* block_out) {
     return (int)grid;
 }
 
-template <int NQ, int DIM, int PDE>
+template <int NQ, int DIM, int PDE, bool MIX>
 cudaError_t sweep_launch_impl(const SweepArgs& a, int grid, int block) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = sweep_smem<NQ, DIM, PDE>(a.epb);
+    cfg.dynamicSmemBytes = sweep_smem<NQ, DIM, PDE, MIX>(a.epb);
     cfg.stream = a.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sweep<NQ, DIM, PDE>, a);
+    return cudaLaunchKernelEx(&cfg, k_sweep<NQ, DIM, PDE, MIX>, a);
 }
 
 }  // namespace sisdc

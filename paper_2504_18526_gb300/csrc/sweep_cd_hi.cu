@@ -1,32 +1,32 @@
-// Instantiations of the persistent sweep kernel (PDE 0, NQ 6..9).
+// Instantiations of the persistent sweep kernel (PDE 0, NQ 6..9, FP64).
 #include "sweep.cuh"
 
 namespace sisdc {
 
-int sweep_config_pde0_hi(const Geo& g, int* epb, int* block) {
+int sweep_config_pde0_hi_0(const Geo& g, int* epb, int* block) {
     switch (g.nq * 10 + g.dim) {
-        case 61: return sweep_config_impl<6, 1, 0>(g, epb, block);
-        case 62: return sweep_config_impl<6, 2, 0>(g, epb, block);
-        case 71: return sweep_config_impl<7, 1, 0>(g, epb, block);
-        case 72: return sweep_config_impl<7, 2, 0>(g, epb, block);
-        case 81: return sweep_config_impl<8, 1, 0>(g, epb, block);
-        case 82: return sweep_config_impl<8, 2, 0>(g, epb, block);
-        case 91: return sweep_config_impl<9, 1, 0>(g, epb, block);
-        case 92: return sweep_config_impl<9, 2, 0>(g, epb, block);
+        case 61: return sweep_config_impl<6, 1, 0, false>(g, epb, block);
+        case 62: return sweep_config_impl<6, 2, 0, false>(g, epb, block);
+        case 71: return sweep_config_impl<7, 1, 0, false>(g, epb, block);
+        case 72: return sweep_config_impl<7, 2, 0, false>(g, epb, block);
+        case 81: return sweep_config_impl<8, 1, 0, false>(g, epb, block);
+        case 82: return sweep_config_impl<8, 2, 0, false>(g, epb, block);
+        case 91: return sweep_config_impl<9, 1, 0, false>(g, epb, block);
+        case 92: return sweep_config_impl<9, 2, 0, false>(g, epb, block);
         default: return 0;
     }
 }
 
-cudaError_t sweep_launch_pde0_hi(const SweepArgs& a, int grid, int block) {
+cudaError_t sweep_launch_pde0_hi_0(const SweepArgs& a, int grid, int block) {
     switch (a.g.nq * 10 + a.g.dim) {
-        case 61: return sweep_launch_impl<6, 1, 0>(a, grid, block);
-        case 62: return sweep_launch_impl<6, 2, 0>(a, grid, block);
-        case 71: return sweep_launch_impl<7, 1, 0>(a, grid, block);
-        case 72: return sweep_launch_impl<7, 2, 0>(a, grid, block);
-        case 81: return sweep_launch_impl<8, 1, 0>(a, grid, block);
-        case 82: return sweep_launch_impl<8, 2, 0>(a, grid, block);
-        case 91: return sweep_launch_impl<9, 1, 0>(a, grid, block);
-        case 92: return sweep_launch_impl<9, 2, 0>(a, grid, block);
+        case 61: return sweep_launch_impl<6, 1, 0, false>(a, grid, block);
+        case 62: return sweep_launch_impl<6, 2, 0, false>(a, grid, block);
+        case 71: return sweep_launch_impl<7, 1, 0, false>(a, grid, block);
+        case 72: return sweep_launch_impl<7, 2, 0, false>(a, grid, block);
+        case 81: return sweep_launch_impl<8, 1, 0, false>(a, grid, block);
+        case 82: return sweep_launch_impl<8, 2, 0, false>(a, grid, block);
+        case 91: return sweep_launch_impl<9, 1, 0, false>(a, grid, block);
+        case 92: return sweep_launch_impl<9, 2, 0, false>(a, grid, block);
         default: return cudaErrorInvalidValue;
     }
 }

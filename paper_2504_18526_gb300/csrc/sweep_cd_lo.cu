@@ -1,32 +1,32 @@
-// Instantiations of the persistent sweep kernel (PDE 0, NQ 2..5).
+// Instantiations of the persistent sweep kernel (PDE 0, NQ 2..5, FP64).
 #include "sweep.cuh"
 
 namespace sisdc {
 
-int sweep_config_pde0_lo(const Geo& g, int* epb, int* block) {
+int sweep_config_pde0_lo_0(const Geo& g, int* epb, int* block) {
     switch (g.nq * 10 + g.dim) {
-        case 21: return sweep_config_impl<2, 1, 0>(g, epb, block);
-        case 22: return sweep_config_impl<2, 2, 0>(g, epb, block);
-        case 31: return sweep_config_impl<3, 1, 0>(g, epb, block);
-        case 32: return sweep_config_impl<3, 2, 0>(g, epb, block);
-        case 41: return sweep_config_impl<4, 1, 0>(g, epb, block);
-        case 42: return sweep_config_impl<4, 2, 0>(g, epb, block);
-        case 51: return sweep_config_impl<5, 1, 0>(g, epb, block);
-        case 52: return sweep_config_impl<5, 2, 0>(g, epb, block);
+        case 21: return sweep_config_impl<2, 1, 0, false>(g, epb, block);
+        case 22: return sweep_config_impl<2, 2, 0, false>(g, epb, block);
+        case 31: return sweep_config_impl<3, 1, 0, false>(g, epb, block);
+        case 32: return sweep_config_impl<3, 2, 0, false>(g, epb, block);
+        case 41: return sweep_config_impl<4, 1, 0, false>(g, epb, block);
+        case 42: return sweep_config_impl<4, 2, 0, false>(g, epb, block);
+        case 51: return sweep_config_impl<5, 1, 0, false>(g, epb, block);
+        case 52: return sweep_config_impl<5, 2, 0, false>(g, epb, block);
         default: return 0;
     }
 }
 
-cudaError_t sweep_launch_pde0_lo(const SweepArgs& a, int grid, int block) {
+cudaError_t sweep_launch_pde0_lo_0(const SweepArgs& a, int grid, int block) {
     switch (a.g.nq * 10 + a.g.dim) {
-        case 21: return sweep_launch_impl<2, 1, 0>(a, grid, block);
-        case 22: return sweep_launch_impl<2, 2, 0>(a, grid, block);
-        case 31: return sweep_launch_impl<3, 1, 0>(a, grid, block);
-        case 32: return sweep_launch_impl<3, 2, 0>(a, grid, block);
-        case 41: return sweep_launch_impl<4, 1, 0>(a, grid, block);
-        case 42: return sweep_launch_impl<4, 2, 0>(a, grid, block);
-        case 51: return sweep_launch_impl<5, 1, 0>(a, grid, block);
-        case 52: return sweep_launch_impl<5, 2, 0>(a, grid, block);
+        case 21: return sweep_launch_impl<2, 1, 0, false>(a, grid, block);
+        case 22: return sweep_launch_impl<2, 2, 0, false>(a, grid, block);
+        case 31: return sweep_launch_impl<3, 1, 0, false>(a, grid, block);
+        case 32: return sweep_launch_impl<3, 2, 0, false>(a, grid, block);
+        case 41: return sweep_launch_impl<4, 1, 0, false>(a, grid, block);
+        case 42: return sweep_launch_impl<4, 2, 0, false>(a, grid, block);
+        case 51: return sweep_launch_impl<5, 1, 0, false>(a, grid, block);
+        case 52: return sweep_launch_impl<5, 2, 0, false>(a, grid, block);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,39 +1,55 @@
-// Dispatch of the persistent sweep kernel by PDE and degree.
+// Dispatch of the persistent sweep kernel by PDE, degree and precision.
 #include "ops.h"
 
 namespace sisdc {
 
-int sweep_config_pde0_lo(const Geo& g, int* epb, int* block);
-cudaError_t sweep_launch_pde0_lo(const SweepArgs& a, int grid, int block);
-int sweep_config_pde0_hi(const Geo& g, int* epb, int* block);
-cudaError_t sweep_launch_pde0_hi(const SweepArgs& a, int grid, int block);
-int sweep_config_pde1_lo(const Geo& g, int* epb, int* block);
-cudaError_t sweep_launch_pde1_lo(const SweepArgs& a, int grid, int block);
-int sweep_config_pde1_hi(const Geo& g, int* epb, int* block);
-cudaError_t sweep_launch_pde1_hi(const SweepArgs& a, int grid, int block);
-int sweep_config_pde2_lo(const Geo& g, int* epb, int* block);
-cudaError_t sweep_launch_pde2_lo(const SweepArgs& a, int grid, int block);
-int sweep_config_pde2_hi(const Geo& g, int* epb, int* block);
-cudaError_t sweep_launch_pde2_hi(const SweepArgs& a, int grid, int block);
+int sweep_config_pde0_lo_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde0_lo_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde0_hi_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde0_hi_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde0_lo_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde0_lo_1(const SweepArgs& a, int grid, int block);
+int sweep_config_pde0_hi_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde0_hi_1(const SweepArgs& a, int grid, int block);
+int sweep_config_pde1_lo_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde1_lo_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde1_hi_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde1_hi_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde1_lo_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde1_lo_1(const SweepArgs& a, int grid, int block);
+int sweep_config_pde1_hi_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde1_hi_1(const SweepArgs& a, int grid, int block);
+int sweep_config_pde2_lo_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde2_lo_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde2_hi_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde2_hi_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde2_lo_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde2_lo_1(const SweepArgs& a, int grid, int block);
+int sweep_config_pde2_hi_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde2_hi_1(const SweepArgs& a, int grid, int block);
 
-int sweep_config(const Geo& g, int pde, int* epb, int* block) {
+int sweep_config(const Geo& g, int pde, int mix, int* epb, int* block) {
     const bool lo = g.nq < 6;
-    switch (pde) {
-        case 0: return lo ? sweep_config_pde0_lo(g, epb, block) : sweep_config_pde0_hi(g, epb, block);
-        case 1: return lo ? sweep_config_pde1_lo(g, epb, block) : sweep_config_pde1_hi(g, epb, block);
-        case 2: return lo ? sweep_config_pde2_lo(g, epb, block) : sweep_config_pde2_hi(g, epb, block);
-        default: return 0;
-    }
+    mix = mix ? 1 : 0;
+    if (pde == 0 && mix == 0) return lo ? sweep_config_pde0_lo_0(g, epb, block) : sweep_config_pde0_hi_0(g, epb, block);
+    if (pde == 0 && mix == 1) return lo ? sweep_config_pde0_lo_1(g, epb, block) : sweep_config_pde0_hi_1(g, epb, block);
+    if (pde == 1 && mix == 0) return lo ? sweep_config_pde1_lo_0(g, epb, block) : sweep_config_pde1_hi_0(g, epb, block);
+    if (pde == 1 && mix == 1) return lo ? sweep_config_pde1_lo_1(g, epb, block) : sweep_config_pde1_hi_1(g, epb, block);
+    if (pde == 2 && mix == 0) return lo ? sweep_config_pde2_lo_0(g, epb, block) : sweep_config_pde2_hi_0(g, epb, block);
+    if (pde == 2 && mix == 1) return lo ? sweep_config_pde2_lo_1(g, epb, block) : sweep_config_pde2_hi_1(g, epb, block);
+    return 0;
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int block) {
     const bool lo = a.g.nq < 6;
-    switch (a.pde) {
-        case 0: return lo ? sweep_launch_pde0_lo(a, grid, block) : sweep_launch_pde0_hi(a, grid, block);
-        case 1: return lo ? sweep_launch_pde1_lo(a, grid, block) : sweep_launch_pde1_hi(a, grid, block);
-        case 2: return lo ? sweep_launch_pde2_lo(a, grid, block) : sweep_launch_pde2_hi(a, grid, block);
-        default: return cudaErrorInvalidValue;
-    }
+    const int mix = a.mix ? 1 : 0;
+    if (a.pde == 0 && mix == 0) return lo ? sweep_launch_pde0_lo_0(a, grid, block) : sweep_launch_pde0_hi_0(a, grid, block);
+    if (a.pde == 0 && mix == 1) return lo ? sweep_launch_pde0_lo_1(a, grid, block) : sweep_launch_pde0_hi_1(a, grid, block);
+    if (a.pde == 1 && mix == 0) return lo ? sweep_launch_pde1_lo_0(a, grid, block) : sweep_launch_pde1_hi_0(a, grid, block);
+    if (a.pde == 1 && mix == 1) return lo ? sweep_launch_pde1_lo_1(a, grid, block) : sweep_launch_pde1_hi_1(a, grid, block);
+    if (a.pde == 2 && mix == 0) return lo ? sweep_launch_pde2_lo_0(a, grid, block) : sweep_launch_pde2_hi_0(a, grid, block);
+    if (a.pde == 2 && mix == 1) return lo ? sweep_launch_pde2_lo_1(a, grid, block) : sweep_launch_pde2_hi_1(a, grid, block);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace sisdc
