@@ -213,32 +213,32 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel):
-    """dram bytes per launch from a committed ncu summary, if it matches the
-    current kernel source (hash line)."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel)
-    src = os.path.join(ROOT, "paper_2504_18526_gb300", "csrc", "ops_sipg.cu")
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        kv = {}
-        for ln in open(path):
-            if ":" in ln:
-                k, v = ln.split(":", 1)
-                kv[k.strip()] = v.strip()
-        if kv.get("source_sha256_16") != h:
-            return None, None
-        return float(kv["dram_bytes_per_node_iter"]), float(kv.get("dram_bytes_per_launch_fixed_per_node", 0))
-    except Exception:
-        return None, None
+# Algorithmic work of one correction-sweep launch (per fine DOF), from the
+# per-unit operation counts of the path: an SIPG operator application costs
+# 8(P+1) + 20 flop, a convective-operator application 4(P+1) n_c + 10 flop,
+# a CG iteration adds 10 flop of vector updates, a right-hand side 12 flop,
+# and the S.F quadrature 2M flop per collocation node.  Per node of an SI(2)
+# correction sweep: one SIPG application per CG iteration, one for the
+# stage-2 start residual and one for the cached L u; two convective
+# applications.
+def sweep_flops(P, ncomp, M, nsweeps, iters, nv):
+    mv = 8 * (P + 1) + 20
+    cv = 4 * (P + 1) * ncomp + 10
+    per_node = 2 * mv + 2 * cv + 2 * 12 + 2 * M
+    return float(nv) * (nsweeps * M * per_node + iters * (mv + 10))
 
 
-# PCG kernel algorithmic bytes (FP64): per node, setup = read rhs terms
-# (nterms, 5 on average in a sweep) + x, write r: ~7 streams; per iteration
-# the minimal CG traffic of 7 streams (read p, x, r, Ap, write Ap, x, r, p
-# fused as in standard CG accounting) -> 7 * 8 bytes per node and iteration.
-PCG_ITER_STREAMS = 7
-PCG_SETUP_STREAMS = 7
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
+
+
+def make_ctx(S, w, stream, prec, rtol, use_graph):
+    return S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=rtol, cg_maxit=1000,
+                     use_graph=use_graph)
+
+
+def run_steps(S, ctx, du, dt, ncyc, start, nsteps):
+    for _ in range(nsteps):
+        S.sisdc_step(ctx.ctx, du, 0.0, dt, ncyc, start, 1)
 
 
 def main_arm(args):
@@ -265,10 +265,10 @@ def main_arm(args):
 
     w = workload(args)
     prec = S.SISDC_MIXED if args.precision == "mixed" else S.SISDC_FP64
+    other = S.SISDC_FP64 if prec == S.SISDC_MIXED else S.SISDC_MIXED
     stream = torch.cuda.Stream(device=dev)
     use_graph = 0 if args.no_graph else 1
-    ctx = S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
-                    use_graph=use_graph)
+    ctx = make_ctx(S, w, stream, prec, args.cg_rtol, use_graph)
     nc, n, M = ctx.info(-1)
     hx, hy = np.zeros(n), np.zeros(n)
     S.sisdc_level_coords(ctx.levels[-1], hx, hy)
@@ -283,11 +283,7 @@ def main_arm(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     torch.cuda.synchronize()
 
-    def step(u):
-        S.sisdc_step(ctx.ctx, u, 0.0, dt, ncyc, start, 1)
-
-    for _ in range(args.warmup):
-        step(du)
+    run_steps(S, ctx, du, dt, ncyc, start, args.warmup)
     S.sisdc_sync(ctx.ctx)
     S.sisdc_reset_stats(ctx.ctx)
 
@@ -302,7 +298,7 @@ def main_arm(args):
         with torch.cuda.stream(stream):
             flush.fill_(float(k))
         evs[k][0].record(stream)
-        step(du)
+        S.sisdc_step(ctx.ctx, du, 0.0, dt, ncyc, start, 1)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -341,12 +337,10 @@ def main_arm(args):
     e2e_val = world * dofs_per_step * ke / (t_e2e * 1e-3)
     ctx.close()
 
-    # ---- dominant kernel: live CUDA-event timing of the PCG launches (eager) --
-    kctx = S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
-                     use_graph=0)
+    # ---- dominant kernel: live CUDA-event timing of the fine-level sweeps ----
+    kctx = make_ctx(S, w, stream, prec, args.cg_rtol, 0)
     dk = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
-    for _ in range(2):
-        S.sisdc_step(kctx.ctx, dk, 0.0, dt, ncyc, start, 1)
+    run_steps(S, kctx, dk, dt, ncyc, start, 2)
     S.sisdc_sync(kctx.ctx)
     S.sisdc_reset_stats(kctx.ctx)
     S.sisdc_set_kernel_timing(kctx.ctx, True, len(w["levels"]) - 1)
@@ -361,15 +355,42 @@ def main_arm(args):
     S.sisdc_sync(kctx.ctx)
     kctx.close()
     launches_per_step = kstats["launches"] / args.steps
-    hbm_peak, peak_kind = measured_peaks()
-    alg_bytes = 8.0 * (PCG_SETUP_STREAMS * nv * kt["launches"] + PCG_ITER_STREAMS * kt["nodes_x_iters"])
-    per_launch_bytes = alg_bytes / max(1, kt["launches"])
+    nsw = kt["dof_sweeps"] / max(1, nv)
+    flops = sweep_flops(lv["P"], nc, M, nsw / max(1, kt["launches"]), kt["iters"] / max(1, kt["launches"]), nv)
     avg_ms = kt["ms"] / max(1, kt["launches"])
-    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-    tr_iter, tr_fixed = profile_traffic("k_pcg")
-    traffic = None
-    if tr_iter is not None:
-        traffic = (tr_fixed * nv * kt["launches"] + tr_iter * kt["nodes_x_iters"]) / max(1, kt["launches"])
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+
+    # ---- the other precision form and time-to-solution at equal L2 error ----
+    forms = {}
+    win = max(4, min(20, args.steps))
+    ref_ctx = make_ctx(S, w, stream, S.SISDC_FP64, min(args.cg_rtol, 1e-13), 1)
+    ur = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+    torch.cuda.synchronize()
+    run_steps(S, ref_ctx, ur, dt / 4, 6, start, 4 * win)
+    S.sisdc_sync(ref_ctx.ctx)
+    ref_ctx.close()
+    for pf, name in ((S.SISDC_FP64, "fp64_plain"), (S.SISDC_MIXED, "mixed_tuned")):
+        fctx = make_ctx(S, w, stream, pf, args.cg_rtol, 1)
+        uf = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+        run_steps(S, fctx, uf, dt, ncyc, start, 2)                 # capture + warm
+        S.sisdc_sync(fctx.ctx)                                     # the reset must follow them
+        uf.copy_(torch.from_numpy(np.ascontiguousarray(u0)))
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        run_steps(S, fctx, uf, dt, ncyc, start, win)
+        a1.record(stream)
+        S.sisdc_sync(fctx.ctx)
+        tms = a0.elapsed_time(a1)
+        err = float(torch.linalg.vector_norm(uf - ur) / torch.linalg.vector_norm(ur))
+        forms[name] = {"ms_per_step": tms / win, "dof_sweeps_per_s": dofs_per_step * win / (tms * 1e-3),
+                       "time_to_solution_ms": tms, "rel_l2_error_vs_reference": err}
+        fctx.close()
+    tts = {"window_steps": win, "reference": "FP64 GPU path at dt/4 with 6 V-cycles per step",
+           "error_ratio_tuned_over_plain": forms["mixed_tuned"]["rel_l2_error_vs_reference"] /
+           max(1e-300, forms["fp64_plain"]["rel_l2_error_vs_reference"]),
+           "speedup_tuned_over_plain": forms["fp64_plain"]["time_to_solution_ms"] /
+           forms["mixed_tuned"]["time_to_solution_ms"]}
 
     if rank != 0:
         return
@@ -390,23 +411,28 @@ def main_arm(args):
         "dtype": "f64" if prec == S.SISDC_FP64 else "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload + (" (8x8 elements)" if args.small else ""),
+                   "precision": args.precision,
                    "fine_dofs": nv, "levels": w["levels"], "nodes": w["nodes"], "dt": dt,
                    "ncycles": ncyc, "fine_sweeps_per_step": ncyc + 1, "start": w["start"],
                    "si_stages": 2, "cg_rtol": args.cg_rtol, "cuda_graph": bool(use_graph),
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_pcg (fine level)", "achieved": achieved,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "avg_launch_us": avg_ms * 1e3,
-                     "launches": kt["launches"], "avg_iters": kt["iters"] / max(1, kt["launches"]),
+        "roofline": {"bound": "alu", "kernel": "k_sweep correction launches, fine level",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20)",
+                     "avg_launch_us": avg_ms * 1e3, "launches": kt["launches"],
+                     "cg_iters_per_launch": kt["iters"] / max(1, kt["launches"]),
+                     "algorithmic_flop_per_launch": flops,
                      "kernel_share_of_step": kt["ms"] / max(1e-9, eager_s * 1e3)},
+        "forms": forms, "time_to_solution": tts,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nv * 8, "d2h_bytes_per_step": nv * 8},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "cg": {"solves_per_step": stats["cg_solves"] / args.steps,
                "iters_per_solve": stats["cg_iters"] / max(1, stats["cg_solves"]),
-               "max_iters": stats["cg_max_iters"]},
+               "max_iters": stats["cg_max_iters"], "ir_steps": stats["ir_steps"]},
     }
     print(json.dumps(out))
     if dist:

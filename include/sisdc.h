@@ -232,6 +232,14 @@ sisdc_status sisdc_vcycle(sisdc_ctx ctx, const double* d_u0, double* d_U, double
 sisdc_status sisdc_step(sisdc_ctx ctx, double* d_u, double t, double dt, int ncycles,
                         int start, int post_sweep);
 
+/* Diagnostics of a state d_u[NV] (Sec. 7-8 report L2 errors per level): per
+ * component c the GLL-quadrature L2 norm of u - ref (ref = d_ref, or 0 when
+ * NULL), sqrt(sum_e sum_ij J w_i w_j (u - ref)^2), the discrete mass
+ * sum_e sum_ij J w_i w_j u, and max |u - ref|.  Deterministic reduction
+ * order; synchronous; host arrays of ncomp doubles (each may be NULL). */
+sisdc_status sisdc_norms(sisdc_level lv, const double* d_u, const double* d_ref, double* h_l2,
+                         double* h_mass, double* h_maxabs);
+
 /* Wait for the context stream; report device-side conditions (NOCONV,
  * TIMEOUT, NONFINITE) recorded since the previous sisdc_sync and clear them. */
 sisdc_status sisdc_sync(sisdc_ctx ctx);
@@ -241,15 +249,16 @@ sisdc_status sisdc_get_stats(sisdc_ctx ctx, sisdc_stats* out);
 sisdc_status sisdc_reset_stats(sisdc_ctx ctx);
 
 /* Measurement hook.  When enabled (eager mode only: use_graph = 0), every
- * launch of the implicit-solve kernel on level index `level` (-1 = all
- * levels) is bracketed by CUDA events on the context stream and its CG
- * iteration count is recorded.  sisdc_get_kernel_timing synchronises the
- * stream, returns the summed kernel time in ms, the number of timed
- * launches, their summed iterations and sum(iterations * NV of the level),
- * and restarts the count. */
+ * launch of the persistent correction-sweep kernel on level index `level`
+ * (-1 = all levels) is bracketed by CUDA events on the context stream and
+ * its CG iteration count is recorded.  sisdc_get_kernel_timing synchronises
+ * the stream, returns the summed kernel time in ms, the number of timed
+ * launches, their summed CG iterations, sum(iterations * NV of the level)
+ * and the DOF-sweeps they performed (sum of nsweeps * NV), and restarts the
+ * count. */
 sisdc_status sisdc_set_kernel_timing(sisdc_ctx ctx, int enable, int level);
 sisdc_status sisdc_get_kernel_timing(sisdc_ctx ctx, double* h_ms_total, long long* h_launches,
-                                     long long* h_iters, long long* h_nodes_x_iters);
+                                     long long* h_iters, long long* h_nodes_x_iters, long long* h_dof_sweeps);
 
 /* Message of the last failing call on this context ("" if none). */
 const char* sisdc_last_error(sisdc_ctx ctx);

@@ -99,6 +99,7 @@ struct SweepArgs {
     double rtol;
     int maxit;
     int epb;
+    int* iters_out;         // CG iterations of this launch (summed over its solves; nullable)
     cudaStream_t stream;
 };
 // returns the cooperative grid (0 if unavailable); epb = elements per block
@@ -134,5 +135,10 @@ struct TransferArgs {
     int add;              // out += instead of out =
 };
 cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s);
+
+// diagnostics: scratch holds partials and, at offset ncomp*NORM_BLOCKS*3,
+// the result [ncomp][3] = (L2 norm of u - ref, mass of u, max |u - ref|)
+int norms_scratch_doubles(int ncomp);
+cudaError_t launch_norms(const Geo& g, const double* u, const double* ref, double* scratch, cudaStream_t s);
 
 }  // namespace sisdc

@@ -139,4 +139,65 @@ cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---- diagnostics: GLL-weighted L2 norm, discrete mass, max norm -------------
+// Deterministic: pass 1 writes one partial per (component, block) in a fixed
+// tree order; pass 2 sums the partials of each component in index order.
+constexpr int NORM_BLOCKS = 256;
+
+__global__ void k_norms_partial(const Geo g, const double* __restrict__ u, const double* __restrict__ ref,
+                                double* part) {
+    __shared__ double scratch[32];
+    const int c = blockIdx.y;
+    const long long n = g.N;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * per, i1 = min(n, i0 + per);
+    double s2 = 0.0, s1 = 0.0, mx = 0.0;
+    for (long long k = i0 + threadIdx.x; k < i1; k += blockDim.x) {
+        const int node = (int)(k % g.q);
+        const int i = node % g.nq, j = node / g.nq;
+        const double wgt = g.dim == 2 ? (0.5 * g.hx * g.w[i]) * (0.5 * g.hy * g.w[j]) : 0.5 * g.hx * g.w[i];
+        const double v = u[c * n + k];
+        const double e = ref ? v - ref[c * n + k] : v;
+        s2 += wgt * e * e;
+        s1 += wgt * v;
+        mx = fmax(mx, fabs(e));
+    }
+    const double t2 = block_sum(s2, scratch);
+    const double t1 = block_sum(s1, scratch);
+    const double tm = block_max(mx, scratch);
+    if (threadIdx.x == 0) {
+        double* o = part + ((size_t)c * gridDim.x + blockIdx.x) * 3;
+        o[0] = t2;
+        o[1] = t1;
+        o[2] = tm;
+    }
+}
+
+__global__ void k_norms_final(const double* part, int nb, double* out) {
+    const int c = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double s2 = 0.0, s1 = 0.0, mx = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double* o = part + ((size_t)c * nb + b) * 3;
+        s2 += o[0];
+        s1 += o[1];
+        mx = fmax(mx, o[2]);
+    }
+    out[3 * c + 0] = sqrt(s2);
+    out[3 * c + 1] = s1;
+    out[3 * c + 2] = mx;
+}
+
+int norms_scratch_doubles(int ncomp) { return ncomp * (NORM_BLOCKS * 3 + 3); }
+
+cudaError_t launch_norms(const Geo& g, const double* u, const double* ref, double* scratch, cudaStream_t s) {
+    double* part = scratch;
+    double* out = scratch + (size_t)g.ncomp * NORM_BLOCKS * 3;
+    k_norms_partial<<<dim3(NORM_BLOCKS, g.ncomp), 256, 0, s>>>(g, u, ref, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_norms_final<<<g.ncomp, 32, 0, s>>>(part, NORM_BLOCKS, out);
+    return cudaGetLastError();
+}
+
 }  // namespace sisdc

@@ -63,6 +63,7 @@ struct sisdc_ctx_s {
     int timing_level = -1;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_level;
+    std::vector<int> ev_sweeps;
     size_t ev_used = 0;
     int* d_iters = nullptr;              // iterations of each timed launch
     size_t iters_cap = 0;
@@ -70,6 +71,7 @@ struct sisdc_ctx_s {
     int* d_err = nullptr;
     long long* d_stats = nullptr;
     double* d_part = nullptr;
+    double* d_norms = nullptr;   // diagnostics scratch
     int max_grid = 0;
     std::string err;
     long long launches = 0;
@@ -177,37 +179,7 @@ void k_pcg(sisdc_level_s* lv, double* x, const Terms& t, Coef cimp) {
     a.rtol = c->prob.cg_rtol;
     a.maxit = c->prob.cg_maxit;
     a.iters_out = nullptr;
-    const bool timed = c->timing && (c->timing_level < 0 || c->timing_level == lv->index);
-    if (timed) {
-        const size_t k = c->ev_used / 2;
-        if (c->ev_used + 2 > c->ev.size()) {
-            for (int q = 0; q < 2; ++q) {
-                cudaEvent_t e;
-                check(c, cudaEventCreate(&e), "event create");
-                c->ev.push_back(e);
-            }
-        }
-        if (k >= c->iters_cap) {
-            const size_t cap = c->iters_cap ? 2 * c->iters_cap : 1024;
-            int* p = nullptr;
-            check(c, cudaStreamSynchronize(c->stream), "sync");
-            check(c, cudaMalloc(&p, cap * sizeof(int)), "timing buffer");
-            if (c->d_iters) {
-                check(c, cudaMemcpy(p, c->d_iters, c->iters_cap * sizeof(int), cudaMemcpyDeviceToDevice), "copy");
-                cudaFree(c->d_iters);
-            }
-            c->d_iters = p;
-            c->iters_cap = cap;
-        }
-        a.iters_out = c->d_iters + k;
-        c->ev_level.push_back(lv->index);
-        check(c, cudaEventRecord(c->ev[c->ev_used], c->stream), "event record");
-    }
     check(c, launch_pcg(a, lv->pcg_grid, lv->pcg_block, c->stream), "PCG kernel");
-    if (timed) {
-        check(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream), "event record");
-        c->ev_used += 2;
-    }
     c->launches++;
 }
 
@@ -302,7 +274,41 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.maxit = c->prob.cg_maxit;
     a.epb = lv->sw_epb;
     a.stream = c->stream;
+    a.iters_out = nullptr;
+    const bool timed = c->timing && mode == SW_CORRECT && (c->timing_level < 0 || c->timing_level == lv->index);
+    if (timed) {
+        const size_t k = c->ev_used / 2;
+        if (c->ev_used + 2 > c->ev.size()) {
+            for (int q = 0; q < 2; ++q) {
+                cudaEvent_t e;
+                check(c, cudaEventCreate(&e), "event create");
+                c->ev.push_back(e);
+            }
+        }
+        if (k >= c->iters_cap) {
+            const size_t cap = c->iters_cap ? 2 * c->iters_cap : 1024;
+            int* p = nullptr;
+            check(c, cudaStreamSynchronize(c->stream), "sync");
+            check(c, cudaMalloc(&p, cap * sizeof(int)), "timing buffer");
+            check(c, cudaMemset(p, 0, cap * sizeof(int)), "timing buffer");
+            if (c->d_iters) {
+                check(c, cudaMemcpy(p, c->d_iters, c->iters_cap * sizeof(int), cudaMemcpyDeviceToDevice), "copy");
+                cudaFree(c->d_iters);
+            }
+            c->d_iters = p;
+            c->iters_cap = cap;
+        }
+        a.iters_out = c->d_iters + k;
+        check(c, cudaMemsetAsync(a.iters_out, 0, sizeof(int), c->stream), "memset");
+        c->ev_level.push_back(lv->index);
+        c->ev_sweeps.push_back(nsweeps);
+        check(c, cudaEventRecord(c->ev[c->ev_used], c->stream), "event record");
+    }
     check(c, launch_sweep(a, lv->sw_grid, lv->sw_block), "sweep kernel");
+    if (timed) {
+        check(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream), "event record");
+        c->ev_used += 2;
+    }
     c->launches++;
 }
 
@@ -463,6 +469,7 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, ST_N * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_part, (8 + MMAX + 1) * (size_t)c->max_grid * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_norms, norms_scratch_doubles(prob->ncomp) * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, ST_N * sizeof(long long));
@@ -491,6 +498,7 @@ void sisdc_destroy(sisdc_ctx c) {
     cudaFree(c->d_err);
     cudaFree(c->d_stats);
     cudaFree(c->d_part);
+    cudaFree(c->d_norms);
     delete c;
 }
 
@@ -782,6 +790,27 @@ sisdc_status sisdc_step(sisdc_ctx c, double* u, double t, double dt, int ncycles
     return SISDC_OK;
 }
 
+sisdc_status sisdc_norms(sisdc_level lv, const double* u, const double* ref, double* l2, double* mass,
+                         double* maxabs) {
+    if (!lv || !u) return SISDC_E_ARG;
+    sisdc_ctx_s* c = lv->ctx;
+    const int nc = c->prob.ncomp;
+    cudaError_t e = launch_norms(lv->geo, u, ref, c->d_norms, c->stream);
+    std::vector<double> h(3 * nc);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), c->d_norms + (size_t)norms_scratch_doubles(nc) - 3 * nc, 3 * nc * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("norms: ") + cudaGetErrorString(e));
+    c->launches += 2;
+    for (int q = 0; q < nc; ++q) {
+        if (l2) l2[q] = h[3 * q];
+        if (mass) mass[q] = h[3 * q + 1];
+        if (maxabs) maxabs[q] = h[3 * q + 2];
+    }
+    return SISDC_OK;
+}
+
 sisdc_status sisdc_sync(sisdc_ctx c) {
     if (!c) return SISDC_E_ARG;
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -835,11 +864,12 @@ sisdc_status sisdc_set_kernel_timing(sisdc_ctx c, int enable, int level) {
     c->timing_level = level;
     c->ev_used = 0;
     c->ev_level.clear();
+    c->ev_sweeps.clear();
     return SISDC_OK;
 }
 
 sisdc_status sisdc_get_kernel_timing(sisdc_ctx c, double* ms_total, long long* launches, long long* iters,
-                                     long long* nodes_x_iters) {
+                                     long long* nodes_x_iters, long long* dof_sweeps) {
     if (!c) return SISDC_E_ARG;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("sync: ") + cudaGetErrorString(e));
@@ -850,7 +880,7 @@ sisdc_status sisdc_get_kernel_timing(sisdc_ctx c, double* ms_total, long long* l
         if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("copy: ") + cudaGetErrorString(e));
     }
     double tot = 0.0;
-    long long its = 0, nxi = 0;
+    long long its = 0, nxi = 0, sweeps_nv = 0;
     for (size_t k = 0; k < n; ++k) {
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]);
@@ -858,13 +888,16 @@ sisdc_status sisdc_get_kernel_timing(sisdc_ctx c, double* ms_total, long long* l
         tot += ms;
         its += it[k];
         nxi += (long long)it[k] * c->levels[c->ev_level[k]]->NV;
+        sweeps_nv += (long long)c->ev_sweeps[k] * c->levels[c->ev_level[k]]->NV;
     }
     if (ms_total) *ms_total = tot;
     if (launches) *launches = (long long)n;
     if (iters) *iters = its;
     if (nodes_x_iters) *nodes_x_iters = nxi;
+    if (dof_sweeps) *dof_sweeps = sweeps_nv;
     c->ev_used = 0;
     c->ev_level.clear();
+    c->ev_sweeps.clear();
     return SISDC_OK;
 }
 

@@ -306,6 +306,7 @@ struct Sweeper {
 
     __device__ void stat_solve(int it, bool fin, bool conv_ok) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (a.iters_out) *a.iters_out += it;
             atomicAdd((unsigned long long*)&a.stats[ST_SOLVES], 1ull);
             atomicAdd((unsigned long long*)&a.stats[ST_ITERS], (unsigned long long)it);
             atomicMax((unsigned long long*)&a.stats[ST_MAXIT], (unsigned long long)it);

@@ -88,9 +88,10 @@ def load():
         "sisdc_reset_stats": (c_int, [c_void_p]),
         "sisdc_last_error": (ctypes.c_char_p, [c_void_p]),
         "sisdc_set_kernel_timing": (c_int, [c_void_p, c_int, c_int]),
+        "sisdc_norms": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "sisdc_solve_noalloc": (c_int, [P(sisdc_level_desc), c_int, c_double, c_void_p, c_void_p, c_double,
                                         c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
-        "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll)]),
+        "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll), P(c_ll)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -212,6 +213,15 @@ def sisdc_step(ctx, u, t, dt, ncycles, start, post_sweep):
     _check(load().sisdc_step(ctx, _ptr(u), t, dt, ncycles, start, 1 if post_sweep else 0), ctx)
 
 
+def sisdc_norms(lv, u, ref=None):
+    """(l2[ncomp], mass[ncomp], maxabs[ncomp]) of u (or of u - ref)."""
+    import numpy as np
+    nc = sisdc_level_info(lv)[0]
+    l2, mass, mx = np.zeros(nc), np.zeros(nc), np.zeros(nc)
+    _check(load().sisdc_norms(lv, _ptr(u), _ptr(ref), _hptr(l2), _hptr(mass), _hptr(mx)), lv=lv)
+    return l2, mass, mx
+
+
 def sisdc_sync(ctx):
     _check(load().sisdc_sync(ctx), ctx)
 
@@ -233,10 +243,11 @@ def sisdc_set_kernel_timing(ctx, enable, level=-1):
 
 
 def sisdc_get_kernel_timing(ctx):
-    ms, n, it, nxi = c_double(), c_ll(), c_ll(), c_ll()
+    ms, n, it, nxi, ds = c_double(), c_ll(), c_ll(), c_ll(), c_ll()
     _check(load().sisdc_get_kernel_timing(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(it),
-                                          ctypes.byref(nxi)), ctx)
-    return {"ms": ms.value, "launches": n.value, "iters": it.value, "nodes_x_iters": nxi.value}
+                                          ctypes.byref(nxi), ctypes.byref(ds)), ctx)
+    return {"ms": ms.value, "launches": n.value, "iters": it.value, "nodes_x_iters": nxi.value,
+            "dof_sweeps": ds.value}
 
 
 def sisdc_last_error(ctx):

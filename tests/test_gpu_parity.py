@@ -293,3 +293,20 @@ def test_device_error_flags(dev):
         S.sisdc_sync(ctx.ctx)
     assert ei.value.status == S.SISDC_E_NONFINITE
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["cd1d", "burgers", "euler"])
+def test_norms_parity(dev, case):
+    """Diagnostics: GLL L2 norm, discrete mass, max norm against the oracle."""
+    w = CASES[case]
+    ctx = make_ctx(w)
+    sp = oracle_space(w, w["levels"][-1])
+    u = random_state(w, sp.shape, 21)
+    ref = random_state(w, sp.shape, 22)
+    l2, mass, mx = S.sisdc_norms(ctx.levels[-1], T(u, dev), T(ref, dev))
+    for q in range(sp.ncomp):
+        eq = (u - ref)[q:q + 1]
+        assert abs(l2[q] - np.sqrt(np.sum(sp.mass * eq * eq))) < 1e-12 * l2[q]
+        assert abs(mx[q] - np.max(np.abs(eq))) == 0.0
+    assert np.allclose(mass, sp.integral(u), rtol=1e-12, atol=1e-12)
+    ctx.close()
