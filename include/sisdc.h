@@ -43,6 +43,7 @@ extern "C" {
 
 typedef struct sisdc_ctx_s* sisdc_ctx;
 typedef struct sisdc_level_s* sisdc_level;
+typedef struct sisdc_mlp_s* sisdc_mlp;
 
 typedef enum {
     SISDC_OK = 0,
@@ -259,6 +260,49 @@ sisdc_status sisdc_reset_stats(sisdc_ctx ctx);
 sisdc_status sisdc_set_kernel_timing(sisdc_ctx ctx, int enable, int level);
 sisdc_status sisdc_get_kernel_timing(sisdc_ctx ctx, double* h_ms_total, long long* h_launches,
                                      long long* h_iters, long long* h_nodes_x_iters, long long* h_dof_sweeps);
+
+/* --- learned initial guess / preconditioner of the implicit stage ----------
+ * Not in the paper: an element-patch perceptron predicts, from the 3x3
+ * element patch of a nodal residual field r (scaled by its RMS s, plus the
+ * feature 0.1 log(c / h^2)), the correction of the centre element,
+ * z = r_centre + s MLP(r_patch / s) (the residual itself is the exact
+ * correction as c -> 0; the network learns the deviation);
+ * per element and component, n_in = 9 Q + 1 -> hidden -> hidden (tanh) -> Q.
+ * Weights BF16 (bf16 = 1) or FP32 (bf16 = 0) with FP32 accumulation, FP32
+ * master copy and Adam for training.  2D levels only. */
+sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long seed, int bf16, sisdc_mlp* out);
+void sisdc_mlp_destroy(sisdc_mlp mlp);
+sisdc_status sisdc_mlp_info(sisdc_mlp mlp, int* n_in, int* hidden, int* n_out, long long* nparam);
+/* Parameters [W1 (n_in x H) | b1 | W2 (H x H) | b2 | W3 (H x Q) | b3], row-major FP32 master copy;
+ * either pointer may be NULL (synchronous). */
+sisdc_status sisdc_mlp_params(sisdc_mlp mlp, float* h_get, const float* h_set);
+/* Loss 0.5 mean (MLP(x) - (dx - r)/s)^2 over all elements/components/nodes of one
+ * logged solve (nodal residual d_r = b - (x0 - c L x0), correction d_dx,
+ * coefficient c) and its gradient (host arrays; synchronous; no update). */
+sisdc_status sisdc_mlp_loss_grad(sisdc_mlp mlp, const double* d_r, const double* d_dx, double c, double* h_loss,
+                                 float* h_grad);
+/* epochs of Adam steps, one step per logged solve k (d_r + k NV, d_dx + k NV,
+ * h_c[k]); *h_loss = mean loss of the last epoch. */
+sisdc_status sisdc_mlp_train(sisdc_mlp mlp, const double* d_r, const double* d_dx, const double* h_c, int nsolves,
+                             int epochs, double lr, double* h_loss);
+/* d_z (+)= r + s MLP(r / s) for every element and component (add != 0 adds). */
+sisdc_status sisdc_mlp_apply(sisdc_mlp mlp, const double* d_r, double c, double* d_z, int add);
+const char* sisdc_mlp_last_error(sisdc_mlp mlp);
+
+/* Log, for every implicit solve of the FP64 form on level index `level`, the
+ * initial nodal residual b - (x0 - c L x0) into d_r[k][NV], the correction x - x0
+ * into d_dx[k][NV] and c into d_c[k] (k < capacity); NULL d_r disables.
+ * Resets the count; sisdc_get_solve_log_count returns it (synchronous). */
+sisdc_status sisdc_set_solve_log(sisdc_ctx ctx, int level, double* d_r, double* d_dx, double* d_c, int capacity);
+sisdc_status sisdc_get_solve_log_count(sisdc_ctx ctx, int* h_count);
+
+/* Solve (I - c L) x = rhs to the context's cg_rtol: mode 0 = Jacobi-PCG from
+ * d_x (as sisdc_solve); mode 1 = d_x += MLP(nodal residual), then PCG;
+ * mode 2 = flexible CG (Polak-Ribiere) preconditioned by the MLP after the
+ * same initial guess, with Jacobi-PCG warm-started from the current iterate
+ * as the fallback on breakdown.  *h_iters = CG iterations (synchronous). */
+sisdc_status sisdc_solve_learned(sisdc_level lv, sisdc_mlp mlp, double c, const double* d_rhs, double* d_x, int mode,
+                                 int* h_iters);
 
 /* Message of the last failing call on this context ("" if none). */
 const char* sisdc_last_error(sisdc_ctx ctx);

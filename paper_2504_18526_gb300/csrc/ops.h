@@ -6,7 +6,7 @@
 namespace sisdc {
 
 // ---- SIPG diffusion (ops_sipg.cu) -------------------------------------------
-enum ApplyMode : int { APPLY_A = 0, APPLY_LAP = 1, APPLY_LAP_F = 2, APPLY_OP = 3 };
+enum ApplyMode : int { APPLY_A = 0, APPLY_LAP = 1, APPLY_LAP_F = 2, APPLY_OP = 3, APPLY_RES = 4, APPLY_RESN = 5 };
 
 struct ApplyArgs {
     Geo g;
@@ -14,9 +14,9 @@ struct ApplyArgs {
     const double* tr;     // traces of u (from launch_traces)
     double* out;
     double* out2;         // APPLY_LAP_F: F = cc + nu * Lu
-    const double* cc;
+    const double* cc;     // APPLY_LAP_F: c cache; APPLY_RES: right-hand side
     double nu;
-    Coef c;               // APPLY_OP: Mass u + c A u
+    Coef c;               // APPLY_OP: Mass u + c A u; APPLY_RES: Mass rhs - (Mass u + c A u)
     int mode;
 };
 
@@ -100,6 +100,14 @@ struct SweepArgs {
     int maxit;
     int epb;
     int* iters_out;         // CG iterations of this launch (summed over its solves; nullable)
+    // solve log (FP64 form): for every implicit solve, the initial nodal
+    // residual b - (x0 - c L x0) and the correction x - x0 into slot k of log_r /
+    // log_dx ([cap][NV]) and c into log_c[k]; k counts on from *log_count.
+    double* log_r;
+    double* log_dx;
+    double* log_c;
+    int* log_count;
+    int log_cap;
     cudaStream_t stream;
 };
 // returns the cooperative grid (0 if unavailable); epb = elements per block
@@ -139,6 +147,10 @@ cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s);
 // diagnostics: scratch holds partials and, at offset ncomp*NORM_BLOCKS*3,
 // the result [ncomp][3] = (L2 norm of u - ref, mass of u, max |u - ref|)
 int norms_scratch_doubles(int ncomp);
+// deterministic dot products: out[0] = sum a b w, w = 1 or the Jacobi factor
+// 1 / (mass + c diagA) of each node (jacobi != 0); scratch as for norms
+cudaError_t launch_dot(const Geo& g, const double* a, const double* b, int jacobi, double c, double* scratch,
+                       cudaStream_t s);
 cudaError_t launch_norms(const Geo& g, const double* u, const double* ref, double* scratch, cudaStream_t s);
 
 }  // namespace sisdc

@@ -190,6 +190,51 @@ __global__ void k_norms_final(const double* part, int nb, double* out) {
 
 int norms_scratch_doubles(int ncomp) { return ncomp * (NORM_BLOCKS * 3 + 3); }
 
+__global__ void k_dot_partial(const Geo g, const double* __restrict__ a, const double* __restrict__ b, int jacobi,
+                              double c, double* part) {
+    __shared__ double scratch[32];
+    const long long n = (long long)g.ncomp * g.N;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * per, i1 = min(n, i0 + per);
+    double s = 0.0;
+    for (long long k = i0 + threadIdx.x; k < i1; k += blockDim.x) {
+        double w = 1.0;
+        if (jacobi) {
+            const int node = (int)(k % g.q);
+            const int i = node % g.nq, j = node / g.nq;
+            double mass, dg;
+            if (g.dim == 2) {
+                const double mx = 0.5 * g.hx * g.w[i], my = 0.5 * g.hy * g.w[j];
+                mass = mx * my;
+                dg = my * g.dline_x[i] + mx * g.dline_y[j];
+            } else {
+                mass = 0.5 * g.hx * g.w[i];
+                dg = g.dline_x[i];
+            }
+            w = 1.0 / (mass + c * dg);
+        }
+        s += a[k] * b[k] * w;
+    }
+    const double t = block_sum(s, scratch);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_dot_final(const double* part, int nb, double* out) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    out[0] = s;
+}
+
+cudaError_t launch_dot(const Geo& g, const double* a, const double* b, int jacobi, double c, double* scratch,
+                       cudaStream_t s) {
+    k_dot_partial<<<NORM_BLOCKS, 256, 0, s>>>(g, a, b, jacobi, c, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_dot_final<<<1, 32, 0, s>>>(scratch, NORM_BLOCKS, scratch + NORM_BLOCKS);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_norms(const Geo& g, const double* u, const double* ref, double* scratch, cudaStream_t s) {
     double* part = scratch;
     double* out = scratch + (size_t)g.ncomp * NORM_BLOCKS * 3;

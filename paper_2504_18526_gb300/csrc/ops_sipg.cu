@@ -206,6 +206,12 @@ __global__ void k_apply(const ApplyArgs a) {
             a.out2[idx] = a.cc[idx] + a.nu * lu;
             break;
         }
+        case APPLY_RES:
+            a.out[idx] = mass * a.cc[idx] - (mass * su[le * S::Q + node] + coef_value(a.c) * Au);
+            break;
+        case APPLY_RESN:
+            a.out[idx] = a.cc[idx] - (su[le * S::Q + node] + coef_value(a.c) * Au / mass);
+            break;
         default: a.out[idx] = mass * su[le * S::Q + node] + coef_value(a.c) * Au; break;
     }
 }

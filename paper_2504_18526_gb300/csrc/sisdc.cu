@@ -13,6 +13,7 @@
 // graph.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -72,6 +73,11 @@ struct sisdc_ctx_s {
     long long* d_stats = nullptr;
     double* d_part = nullptr;
     double* d_norms = nullptr;   // diagnostics scratch
+    // solve log of one level (training data of the learned initial guess)
+    int log_level = -1;
+    double *log_r = nullptr, *log_dx = nullptr, *log_c = nullptr;
+    int log_cap = 0;
+    int* d_log_count = nullptr;
     int max_grid = 0;
     std::string err;
     long long launches = 0;
@@ -275,6 +281,13 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.epb = lv->sw_epb;
     a.stream = c->stream;
     a.iters_out = nullptr;
+    if (c->log_r && lv->index == c->log_level && c->prob.precision == SISDC_FP64) {
+        a.log_r = c->log_r;
+        a.log_dx = c->log_dx;
+        a.log_c = c->log_c;
+        a.log_count = c->d_log_count;
+        a.log_cap = c->log_cap;
+    }
     const bool timed = c->timing && mode == SW_CORRECT && (c->timing_level < 0 || c->timing_level == lv->index);
     if (timed) {
         const size_t k = c->ev_used / 2;
@@ -470,6 +483,8 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, ST_N * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_part, (8 + MMAX + 1) * (size_t)c->max_grid * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_norms, norms_scratch_doubles(prob->ncomp) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_log_count, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_log_count, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, ST_N * sizeof(long long));
@@ -499,6 +514,7 @@ void sisdc_destroy(sisdc_ctx c) {
     cudaFree(c->d_stats);
     cudaFree(c->d_part);
     cudaFree(c->d_norms);
+    cudaFree(c->d_log_count);
     delete c;
 }
 
@@ -903,4 +919,145 @@ sisdc_status sisdc_get_kernel_timing(sisdc_ctx c, double* ms_total, long long* l
 
 const char* sisdc_last_error(sisdc_ctx c) { return c ? c->err.c_str() : "null context"; }
 
+sisdc_status sisdc_set_solve_log(sisdc_ctx c, int level, double* d_r, double* d_dx, double* d_c, int capacity) {
+    if (!c) return SISDC_E_ARG;
+    if (d_r && (!d_dx || !d_c || capacity < 1 || level < 0 || level >= (int)c->levels.size()))
+        return fail(c, SISDC_E_ARG, "solve log needs buffers, a capacity and an existing level");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemset(c->d_log_count, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, cudaGetErrorString(e));
+    c->log_level = d_r ? level : -1;
+    c->log_r = d_r;
+    c->log_dx = d_dx;
+    c->log_c = d_c;
+    c->log_cap = d_r ? capacity : 0;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_get_solve_log_count(sisdc_ctx c, int* h_count) {
+    if (!c || !h_count) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h_count, c->d_log_count, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, cudaGetErrorString(e));
+    if (*h_count > c->log_cap) *h_count = c->log_cap;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_mlp_apply(sisdc_mlp p, const double* d_r, double c, double* d_z, int add);
+
+namespace {
+double host_dot(sisdc_level_s* lv, const double* a, const double* b, int jacobi, double cval) {
+    sisdc_ctx_s* c = lv->ctx;
+    check(c, launch_dot(lv->geo, a, b, jacobi, cval, c->d_norms, c->stream), "dot kernel");
+    double v = 0.0;
+    check(c, cudaMemcpyAsync(&v, c->d_norms + 256, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
+    check(c, cudaStreamSynchronize(c->stream), "sync");
+    c->launches += 2;
+    return v;
+}
+
+// M-weighted residual M rhs - (M + cA) x
+void residual_into(sisdc_level_s* lv, const double* x, const double* rhs, double cval, double* out) {
+    k_lap(lv, x, out, APPLY_RES, nullptr, rhs, Coef{cval, 0.0, nullptr});
+}
+// nodal residual rhs - (x - c L x), the input of the learned correction
+void nodal_residual_into(sisdc_level_s* lv, const double* x, const double* rhs, double cval, double* out) {
+    k_lap(lv, x, out, APPLY_RESN, nullptr, rhs, Coef{cval, 0.0, nullptr});
+}
+}  // namespace
+
+sisdc_status sisdc_solve_learned(sisdc_level lv, sisdc_mlp mlp, double cval, const double* rhs, double* x, int mode,
+                                 int* h_iters) {
+    if (!lv || !rhs || !x || !(cval > 0.0) || mode < 0 || mode > 2 || (mode > 0 && !mlp)) return SISDC_E_ARG;
+    sisdc_ctx_s* c = lv->ctx;
+    const long long NV = lv->NV;
+    try {
+        if (mode <= 1) {
+            if (mode == 1) {
+                nodal_residual_into(lv, x, rhs, cval, lv->cg_r);
+                sisdc_status st = sisdc_mlp_apply(mlp, lv->cg_r, cval, x, 1);
+                if (st != SISDC_OK) return fail(c, st, "MLP application failed");
+            }
+            return sisdc_solve(lv, cval, rhs, x, h_iters);
+        }
+        // flexible CG, MLP preconditioner (Polak-Ribiere beta), MLP initial guess
+        double* R = lv->cg_r;
+        double* Z = lv->dC;
+        double* Pv = lv->cg_p;
+        double* AP = lv->cg_Ap;
+        double* Rold = lv->V;
+        double* Dv = lv->V + NV;
+        check(c, cudaMemsetAsync(lv->tmpc, 0, NV * sizeof(double), c->stream), "memset");
+        residual_into(lv, lv->tmpc, rhs, cval, Dv);                // M b
+        const double bb = host_dot(lv, Dv, Dv, 1, cval);
+        const double tol2 = std::max(c->prob.cg_rtol * c->prob.cg_rtol * bb, 1e-300);
+        nodal_residual_into(lv, x, rhs, cval, R);
+        sisdc_status st = sisdc_mlp_apply(mlp, R, cval, x, 1);
+        if (st != SISDC_OK) return fail(c, st, "MLP application failed");
+        residual_into(lv, x, rhs, cval, R);
+        nodal_residual_into(lv, x, rhs, cval, lv->tmpc);
+        st = sisdc_mlp_apply(mlp, lv->tmpc, cval, Z, 0);
+        if (st != SISDC_OK) return fail(c, st, "MLP application failed");
+        copy_d2d(lv, Pv, Z, NV);
+        double rz = host_dot(lv, R, Z, 0, cval);
+        int it = 0;
+        while (it < c->prob.cg_maxit) {
+            const double rr = host_dot(lv, R, R, 1, cval);
+            if (!(rr > tol2)) break;
+            if (!(rz > 0.0)) {                                     // breakdown: fall back to Jacobi-PCG
+                int more = 0;
+                sisdc_status s2 = sisdc_solve(lv, cval, rhs, x, &more);
+                if (h_iters) *h_iters = it + more;
+                return s2;
+            }
+            k_lap(lv, Pv, AP, APPLY_OP, nullptr, nullptr, Coef{cval, 0.0, nullptr});
+            const double alpha = rz / host_dot(lv, Pv, AP, 0, cval);
+            Terms tx;
+            tx.add(x, 1.0);
+            tx.add(Pv, alpha);
+            k_lin(lv, x, tx);
+            copy_d2d(lv, Rold, R, NV);
+            Terms tr;
+            tr.add(R, 1.0);
+            tr.add(AP, -alpha);
+            k_lin(lv, R, tr);
+            nodal_residual_into(lv, x, rhs, cval, lv->tmpc);
+            st = sisdc_mlp_apply(mlp, lv->tmpc, cval, Z, 0);
+            if (st != SISDC_OK) return fail(c, st, "MLP application failed");
+            Terms td;
+            td.add(R, 1.0);
+            td.add(Rold, -1.0);
+            k_lin(lv, Rold, td);                                   // r_new - r_old
+            const double beta = host_dot(lv, Z, Rold, 0, cval) / rz;
+            rz = host_dot(lv, R, Z, 0, cval);
+            Terms tp;
+            tp.add(Z, 1.0);
+            tp.add(Pv, beta);
+            k_lin(lv, Pv, tp);
+            ++it;
+        }
+        if (h_iters) *h_iters = it;
+        if (it >= c->prob.cg_maxit) return fail(c, SISDC_E_NOCONV, "flexible CG reached cg_maxit");
+    } catch (const Fail& f) {
+        return f.st;
+    }
+    return SISDC_OK;
+}
+
+
+
 }  // extern "C"
+
+namespace sisdc {
+void level_shape(sisdc_level lv, int* nc, int* nex, int* ney, int* q, double* hx, double* hy, int* dim) {
+    *nc = lv->ctx->prob.ncomp;
+    *nex = lv->geo.nex;
+    *ney = lv->geo.ney;
+    *q = lv->Q;
+    *hx = lv->geo.hx;
+    *hy = lv->geo.hy;
+    *dim = lv->desc.dim;
+}
+cudaStream_t level_stream(sisdc_level lv) { return lv->ctx->stream; }
+}  // namespace sisdc

@@ -65,6 +65,7 @@ struct Sweeper {
     long long ntiles, N, NV;
     double mass, diagA;
     int solve_parity;
+    int log_base, log_n;                  // solve-log slot of the next solve
 
     struct Terms {
         int n;
@@ -150,6 +151,8 @@ struct Sweeper {
         N = g.N;
         NV = (long long)NC * N;
         solve_parity = 0;
+        log_base = a.log_count ? __ldcg(a.log_count) : 0;
+        log_n = 0;
         __syncthreads();
         mass_diag(i, j, mass, diagA);
     }
@@ -328,6 +331,12 @@ struct Sweeper {
         set_dinv(c);
         const double dinv = sdinv[node];
         double acc_bb = 0.0, acc = 0.0;
+        const int slot = log_base + log_n;
+        const bool logit = a.log_r && slot < a.log_cap;
+        ++log_n;
+        double* lr = logit ? a.log_r + (long long)slot * NV : nullptr;
+        double* ldx = logit ? a.log_dx + (long long)slot * NV : nullptr;
+        if (logit && blockIdx.x == 0 && threadIdx.x == 0) a.log_c[slot] = c;
         tiles([&](const long long e0, const int nle) {
             const bool act = le < nle;
             const long long e = e0 + le;
@@ -357,6 +366,10 @@ struct Sweeper {
                     const double Ax = Lx0 ? -mass * __ldcg(Lx0 + id) : opA64(le, cc);
                     const double rr = mb - (mass * xv + c * Ax);
                     a.r[id] = rr;
+                    if (logit) {
+                        lr[id] = rr / mass;      // nodal residual b - (x0 - c L x0)
+                        ldx[id] = xv;
+                    }
                     acc_bb += mb * mb * dinv;
                     acc += rr * (rr * dinv);
                 }
@@ -433,6 +446,17 @@ struct Sweeper {
             ++it;
             par ^= 1;
             fin = isfinite(rz);
+        }
+        if (logit) {
+            tiles([&](const long long e0, const int nle) {
+                if (le < nle) {
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) {
+                        const long long id = vidx(cc, e0 + le);
+                        ldx[id] = __ldcg(x + id) - __ldcg(ldx + id);
+                    }
+                }
+            });
         }
         stat_solve(it, fin, !(rz > tol2));
         return true;
@@ -882,6 +906,7 @@ struct Sweeper {
 
     __device__ void finish() {
         __syncthreads();
+        if (a.log_count && blockIdx.x == 0 && threadIdx.x == 0) *a.log_count = log_base + log_n;
         if (blockIdx.x == 0) {
             for (int t = threadIdx.x; t <= MMAX; t += blockDim.x) {
                 a.lam[t] = slam_old[t];

@@ -89,6 +89,17 @@ def load():
         "sisdc_last_error": (ctypes.c_char_p, [c_void_p]),
         "sisdc_set_kernel_timing": (c_int, [c_void_p, c_int, c_int]),
         "sisdc_norms": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "sisdc_mlp_create": (c_int, [c_void_p, c_int, ctypes.c_ulonglong, c_int, P(c_void_p)]),
+        "sisdc_mlp_destroy": (None, [c_void_p]),
+        "sisdc_mlp_info": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int), P(c_ll)]),
+        "sisdc_mlp_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "sisdc_mlp_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_double, P(c_double), c_void_p]),
+        "sisdc_mlp_train": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_double, P(c_double)]),
+        "sisdc_mlp_apply": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_int]),
+        "sisdc_mlp_last_error": (ctypes.c_char_p, [c_void_p]),
+        "sisdc_set_solve_log": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int]),
+        "sisdc_get_solve_log_count": (c_int, [c_void_p, P(c_int)]),
+        "sisdc_solve_learned": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_int, P(c_int)]),
         "sisdc_solve_noalloc": (c_int, [P(sisdc_level_desc), c_int, c_double, c_void_p, c_void_p, c_double,
                                         c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
         "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll), P(c_ll)]),
@@ -220,6 +231,68 @@ def sisdc_norms(lv, u, ref=None):
     l2, mass, mx = np.zeros(nc), np.zeros(nc), np.zeros(nc)
     _check(load().sisdc_norms(lv, _ptr(u), _ptr(ref), _hptr(l2), _hptr(mass), _hptr(mx)), lv=lv)
     return l2, mass, mx
+
+
+def _mcheck(st, mlp):
+    if st != SISDC_OK:
+        raise SisdcError(st, load().sisdc_mlp_last_error(mlp).decode() if mlp else "")
+
+
+def sisdc_mlp_create(lv, hidden, seed=0, bf16=1):
+    out = c_void_p()
+    _check(load().sisdc_mlp_create(lv, hidden, seed, bf16, ctypes.byref(out)), lv=lv)
+    return out.value
+
+
+def sisdc_mlp_destroy(mlp):
+    load().sisdc_mlp_destroy(mlp)
+
+
+def sisdc_mlp_info(mlp):
+    a, b, c, d = c_int(), c_int(), c_int(), c_ll()
+    _mcheck(load().sisdc_mlp_info(mlp, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), mlp)
+    return a.value, b.value, c.value, d.value
+
+
+def sisdc_mlp_params(mlp, get=None, set_=None):
+    _mcheck(load().sisdc_mlp_params(mlp, None if get is None else get.ctypes.data,
+                                    None if set_ is None else set_.ctypes.data), mlp)
+
+
+def sisdc_mlp_loss_grad(mlp, r, dx, c, grad=None):
+    l = c_double()
+    _mcheck(load().sisdc_mlp_loss_grad(mlp, _ptr(r), _ptr(dx), c, ctypes.byref(l),
+                                       None if grad is None else grad.ctypes.data), mlp)
+    return l.value
+
+
+def sisdc_mlp_train(mlp, r, dx, cs, nsolves, epochs, lr):
+    import numpy as np
+    cs = np.ascontiguousarray(cs, dtype=np.float64)
+    l = c_double()
+    _mcheck(load().sisdc_mlp_train(mlp, _ptr(r), _ptr(dx), cs.ctypes.data, nsolves, epochs, lr, ctypes.byref(l)),
+            mlp)
+    return l.value
+
+
+def sisdc_mlp_apply(mlp, r, c, z, add=False):
+    _mcheck(load().sisdc_mlp_apply(mlp, _ptr(r), c, _ptr(z), 1 if add else 0), mlp)
+
+
+def sisdc_set_solve_log(ctx, level, r=None, dx=None, cs=None, capacity=0):
+    _check(load().sisdc_set_solve_log(ctx, level, _ptr(r), _ptr(dx), _ptr(cs), capacity), ctx)
+
+
+def sisdc_get_solve_log_count(ctx):
+    n = c_int()
+    _check(load().sisdc_get_solve_log_count(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def sisdc_solve_learned(lv, mlp, c, rhs, x, mode):
+    it = c_int()
+    _check(load().sisdc_solve_learned(lv, mlp, c, _ptr(rhs), _ptr(x), mode, ctypes.byref(it)), lv=lv)
+    return it.value
 
 
 def sisdc_sync(ctx):
