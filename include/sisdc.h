@@ -304,6 +304,86 @@ sisdc_status sisdc_get_solve_log_count(sisdc_ctx ctx, int* h_count);
 sisdc_status sisdc_solve_learned(sisdc_level lv, sisdc_mlp mlp, double c, const double* d_rhs, double* d_x, int mode,
                                  int* h_iters);
 
+/* --- batched ensemble of independent convection-diffusion problems ---------
+ *
+ * Many independent instances of u_t + a . grad u = nu lap u (Sec. 2, the
+ * scalar convection-diffusion case) on the periodic unit square, each with
+ * its own element grid, degree P, velocity a, viscosity nu and time step,
+ * advanced together by two-level SI-MLSDC steps (Algorithm 2; Cascade start,
+ * Algorithm 3, or the predictor start).  The coarse level of an instance has
+ * degree ceil(P/2) on the same element grid (p-coarsening, Sec. 6.2) and Mc
+ * collocation nodes of the same kind.  Instances of one degree share one
+ * persistent cooperative launch per sweep; every instance keeps its own
+ * implicit solves (own CG coefficients and stopping test), so the results
+ * are those of solving the instances one by one. */
+typedef struct sisdc_ens_s* sisdc_ens;
+
+typedef struct {
+    int nel[2];          /* elements in x and y (>= 1; nel[0] * nel[1] <= 2^24)  */
+    int P;               /* fine polynomial degree, 2..8                         */
+    double nu;           /* viscosity (>= 0)                                     */
+    double adv[2];       /* velocity                                             */
+    double dt;           /* time step (> 0)                                      */
+} sisdc_ens_instance;
+
+typedef struct {
+    int M, Mc;           /* fine / coarse collocation nodes (1 <= Mc <= M <= 8)  */
+    sisdc_nodes nodes;
+    sisdc_precision precision;   /* SISDC_MIXED: FP32 inner CG for P >= 3 levels */
+    int si_stages;       /* 1 or 2                                                */
+    double cg_rtol;
+    int cg_maxit;
+    int Nc;              /* coarse sweeps per V-cycle                             */
+    int ncycles;         /* V-cycles per step                                     */
+    int start;           /* SISDC_START_CASCADE or SISDC_START_PREDICTOR          */
+    int post_sweep;      /* final fine sweep after the last cycle                 */
+    int use_graph;       /* capture one ensemble step as a CUDA graph             */
+} sisdc_ens_opts;
+
+/* Create an ensemble of n instances on the current device and the stream
+ * `cuda_stream` (NULL = legacy stream).  All work arrays are allocated here
+ * (about 8 M + 4 doubles per fine node plus 8 Mc + 4 per coarse node).
+ * SISDC_E_ARG for an invalid instance or option. */
+sisdc_status sisdc_ens_create(const sisdc_ens_instance* inst, int n, const sisdc_ens_opts* opts, void* cuda_stream,
+                              sisdc_ens* out);
+void sisdc_ens_destroy(sisdc_ens ens);
+
+/* Packed state layout: instance k occupies doubles offsets[k] ..
+ * offsets[k] + nel[0] nel[1] (P+1)^2 - 1 of the state vector, as
+ * [ey][ex][j][i] (GLL nodes, i fastest); *total = length of the vector.
+ * Either pointer may be NULL. */
+sisdc_status sisdc_ens_layout(sisdc_ens ens, long long* h_offsets, long long* h_total);
+
+/* Advance every instance by nsteps steps of its own dt; d_u = packed state
+ * (device, caller-owned), updated in place.  Asynchronous on the stream. */
+sisdc_status sisdc_ens_step(sisdc_ens ens, double* d_u, int nsteps);
+
+/* Tile-shape autotuner: for every level of every degree group, times
+ * `nsweeps` correction sweeps from the state d_u (spread over the nodes) for
+ * each candidate (elements per tile, blocks per SM) and keeps the fastest.
+ * d_u is not modified.  h_config (nullable) receives the result as for
+ * sisdc_ens_config.  Synchronous. */
+sisdc_status sisdc_ens_autotune(sisdc_ens ens, const double* d_u, int nsweeps, int* h_config);
+/* Current tile shapes: per group and level (fine, then coarse) the 4 ints
+ * (group degree, level degree, elements per tile, blocks in the grid);
+ * h_config holds 8 * sisdc_ens_num_groups(ens) ints. */
+sisdc_status sisdc_ens_config(sisdc_ens ens, int* h_config);
+int sisdc_ens_num_groups(sisdc_ens ens);
+/* Set the tile shape of one level (fine != 0: fine level) of group `group`
+ * (groups in increasing degree): epb elements per tile (epb (P+1)^2 <= 512
+ * threads), `grid` persistent blocks (at most the co-resident count; fewer
+ * when the level has fewer tiles).  Synchronous. */
+sisdc_status sisdc_ens_set_tiles(sisdc_ens ens, int group, int fine, int epb, int grid);
+
+/* Synchronise and report device error flags (as sisdc_sync). */
+sisdc_status sisdc_ens_sync(sisdc_ens ens);
+/* Counters (synchronous): sweeps[0] / sweeps[1] = coarse / fine sweeps
+ * (counted per group launch); h_inst_iters (nullable, n entries) = fine-level
+ * CG iterations of each instance. */
+sisdc_status sisdc_ens_get_stats(sisdc_ens ens, sisdc_stats* out, long long* h_inst_iters);
+sisdc_status sisdc_ens_reset_stats(sisdc_ens ens);
+const char* sisdc_ens_last_error(sisdc_ens ens);
+
 /* Message of the last failing call on this context ("" if none). */
 const char* sisdc_last_error(sisdc_ctx ctx);
 

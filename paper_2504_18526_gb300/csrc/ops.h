@@ -153,4 +153,54 @@ cudaError_t launch_dot(const Geo& g, const double* a, const double* b, int jacob
                        cudaStream_t s);
 cudaError_t launch_norms(const Geo& g, const double* u, const double* ref, double* scratch, cudaStream_t s);
 
+// ---- ensemble of independent 2D convection-diffusion problems (ens.cuh) ------
+// One instance of an ensemble level: its elements are e0 .. e0 + nex*ney - 1
+// of the level (row-major [ey][ex]), its tiles t0 .. t0 + nt - 1.  Copied
+// into shared memory as 64-bit words: keep every member 8-byte sized or paired.
+struct EnsInst {
+    long long e0;
+    int nex, ney;
+    int t0, nt;
+    double hx, hy, sx, sy, ihx, ihy, taux, tauy;
+    double liftLx, liftRx, liftLy, liftRy;   // (2/h)/w_0, (2/h)/w_P
+    double ax, ay, nu;
+    double lam;                              // max(|a_x|, |a_y|)
+    double dt;                               // the instance's time step
+};
+
+struct EnsArgs {
+    const EnsInst* inst;    // [ninst]
+    int ninst;
+    const int4* tiles;      // [ntiles] (instance, owner-local index, first element, elements)
+    long long ntiles;
+    int epb;                // elements per tile; the block has epb * Q threads
+    const int* nloc;        // [grid] instances touched by each block
+    const int* loc_inst;    // [grid][lmax] their indices
+    int lmax;
+    void* loc;              // [grid][lmax] per-block solve state
+    double* loc_dinv;       // [grid][lmax][Q] per-block Jacobi factors
+    long long N;            // nodes of the level
+    const double *D, *K, *w, *dl;   // degree-P tables; dl = h * (diagonal of the 1D SIPG line operator)
+    int mode, nsweeps, stages, M;
+    double dtau[MMAX];
+    double W[MMAX * MMAX];
+    const double* u0;
+    double* U;
+    const double* G;
+    double *F, *CC, *LU, *Qb, *c0, *dC, *tmpc;
+    double* r;
+    void *p, *p2, *Ap, *rf;
+    double* part;           // (2 * 4 * ninst + 2) * grid partial sums
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* err;
+    long long* stats;
+    double rtol;
+    int maxit;
+    long long* inst_iters;  // [ninst] CG iterations per instance (nullable)
+};
+// blocks per SM of the ensemble kernel for tiles of epb elements (0: unavailable)
+int ens_occupancy(int nq, int mix, int epb);
+cudaError_t launch_ens_sweep(const EnsArgs& a, int nq, int mix, int grid, cudaStream_t s);
+
 }  // namespace sisdc

@@ -32,6 +32,7 @@
 
 #include "ops.h"
 #include "pde.cuh"
+#include "sipg.cuh"
 
 namespace sisdc {
 
@@ -217,16 +218,6 @@ struct Sweeper {
     __device__ static int line_node(int f, int k, int q) { return f < 2 ? k * NQ + q : q * NQ + k; }
 
     // ---- SIPG face terms and operator, in arithmetic V ------------------------
-    template <class V>
-    __device__ void face_line(const V* v, int f, const V* Dt, V& val, V& der) const {
-        const int end = (f & 1) ? NQ - 1 : 0;
-        val = v[end];
-        V s = V(0);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) s += Dt[end * NQ + q] * v[q];
-        der = s * (f < 2 ? V(g.sx) : V(g.sy));
-    }
-
     // jumps [u] and averages {u'} on the faces of the tile's elements: own
     // lines from the tile tu, neighbour lines from getv(c, e, node).
     template <class V, class GetV>
@@ -247,17 +238,8 @@ struct Sweeper {
                 vo[q] = u[line_node(f, k, q)];
                 vn[q] = getv(c, en, line_node(f ^ 1, k, q));
             }
-            V ov, od, nv, nd;
-            face_line(vo, f, Dt, ov, od);
-            face_line(vn, f ^ 1, Dt, nv, nd);
             V jump, avg;
-            if ((f & 1) == 0) {
-                jump = nv - ov;
-                avg = V(0.5) * (nd + od);
-            } else {
-                jump = ov - nv;
-                avg = V(0.5) * (od + nd);
-            }
+            sipg_face<NQ>(g, vo, vn, f, Dt, jump, avg);
             V* o = tf + ((l * NC + c) * NF + f) * 2 * NQ;
             o[k] = jump;
             o[NQ + k] = avg;
@@ -267,24 +249,7 @@ struct Sweeper {
     // (A u)(i, j) for component c of local element l
     template <class V>
     __device__ V opA(int l, int c, const V* tu, const V* tf, const V* Dt, const V* Kt, const V* wt) const {
-        const V* u = tu + (l * NC + c) * Q;
-        const V* f = tf + (l * NC + c) * TRS;
-        V ax = V(0);
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) ax += Kt[i * NQ + k] * u[j * NQ + k];
-        ax *= V(g.sx);
-        ax -= V(g.ihx) * (Dt[(NQ - 1) * NQ + i] * f[2 * NQ + j] + Dt[i] * f[j]);
-        if (i == NQ - 1) ax += -f[3 * NQ + j] + V(g.taux) * f[2 * NQ + j];
-        if (i == 0) ax += f[NQ + j] - V(g.taux) * f[j];
-        if (DIM == 1) return ax;
-        V ay = V(0);
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) ay += Kt[j * NQ + k] * u[k * NQ + i];
-        ay *= V(g.sy);
-        ay -= V(g.ihy) * (Dt[(NQ - 1) * NQ + j] * f[6 * NQ + i] + Dt[j] * f[4 * NQ + i]);
-        if (j == NQ - 1) ay += -f[7 * NQ + i] + V(g.tauy) * f[6 * NQ + i];
-        if (j == 0) ay += f[5 * NQ + i] - V(g.tauy) * f[4 * NQ + i];
-        return (V(0.5) * V(g.hy) * wt[j]) * ax + (V(0.5) * V(g.hx) * wt[i]) * ay;
+        return sipg_opA<NQ, DIM, V>(g, i, j, tu + (l * NC + c) * Q, tf + (l * NC + c) * TRS, Dt, Kt, wt);
     }
     __device__ double opA64(int l, int c) const { return opA<double>(l, c, su, sf, sD, sK, sw); }
     __device__ RT opAR(int l, int c) const { return opA<RT>(l, c, ru, rf, rD, rK, rw); }

@@ -46,6 +46,11 @@ WORKLOADS = {
                 dict(nel=(64, 64), P=7, M=5)],
         nodes="lobatto", cfl=0.5, nsteps=200, ncycles=3, start="fmg1",
         vortex_beta=5.0, mach=0.5, angle_deg=45.0),
+    # 512 independent 2D convection-diffusion problems of mixed sizes and degrees
+    "ensemble512": dict(
+        id=5, pde="convdiff", dim=2, ncomp=1, ninst=512, nel_range=(8, 48), P_range=(3, 8),
+        nu_range=(1e-4, 1e-2), fourier_K=6, fourier_amp=1.0, cfl=0.5,
+        M=5, Mc=3, nodes="radau_right", nsteps=100, ncycles=3, start="cascade"),
 }
 
 
@@ -156,6 +161,47 @@ def scaled(name, nel=None, P=None, levels=None):
         for lv in w["levels"]:
             lv["nel"] = tuple(nel)
     return w
+
+
+def ensemble_instances(n=512, nel_range=(8, 48), P_range=(3, 8), nu_range=(1e-4, 1e-2), cfl=0.5,
+                       seed_extra=0):
+    """n instance descriptions of the ensemble workload: element grid n_e x n_e
+    with n_e ~ U{nel_range}, degree P ~ U{P_range}, nu log-uniform in nu_range,
+    velocity (cos t, sin t) with t ~ U[0, 2 pi), dt from the CFL number on the
+    instance's own grid; plus the seed of its initial data."""
+    rng = rng_for(5, seed_extra)
+    out = []
+    for k in range(n):
+        ne = int(rng.integers(nel_range[0], nel_range[1] + 1))
+        P = int(rng.integers(P_range[0], P_range[1] + 1))
+        nu = float(10.0 ** rng.uniform(math.log10(nu_range[0]), math.log10(nu_range[1])))
+        th = float(rng.uniform(0.0, 2.0 * math.pi))
+        adv = (math.cos(th), math.sin(th))
+        dt = cfl_dt(cfl, 1.0 / ne, P, max(abs(adv[0]), abs(adv[1])))
+        out.append(dict(nel=(ne, ne), P=P, nu=nu, adv=adv, dt=dt, seed=1 + k + 10000 * int(seed_extra)))
+    return out
+
+
+def ensemble_modes(inst, K=6, amp=1.0):
+    """Fourier modes |k| <= K of one instance, amplitude amp / sqrt(#modes)
+    (normalised so that the data's RMS does not grow with K)."""
+    modes = fourier_modes(rng_for(5, inst["seed"]), K, 1)
+    return modes, amp / math.sqrt(len(modes))
+
+
+def ensemble_exact(inst, X, Y, t, K=6, amp=1.0):
+    """Exact solution of u_t + a . grad u = nu lap u on the periodic unit square
+    for the instance's Fourier data: every mode is shifted by a t and damped
+    by exp(-4 pi^2 nu |k|^2 t)."""
+    modes, A = ensemble_modes(inst, K, amp)
+    ax, ay = inst["adv"]
+    Xs, Ys = X - ax * t, Y - ay * t
+    out = np.zeros((1,) + np.shape(X))
+    for kx, ky, a, b in modes:
+        damp = math.exp(-4.0 * math.pi ** 2 * inst["nu"] * (kx * kx + ky * ky) * t)
+        ph = 2.0 * math.pi * (kx * Xs + ky * Ys)
+        out[0] += A * damp * (a[0] * np.cos(ph) + b[0] * np.sin(ph))
+    return out
 
 
 def random_field(shape, seed, scale=1.0):

@@ -41,6 +41,16 @@ class sisdc_stats(ctypes.Structure):
                 ("ir_steps", c_ll), ("sweeps", c_ll * 8), ("launches", c_ll)]
 
 
+class sisdc_ens_instance(ctypes.Structure):
+    _fields_ = [("nel", c_int * 2), ("P", c_int), ("nu", c_double), ("adv", c_double * 2), ("dt", c_double)]
+
+
+class sisdc_ens_opts(ctypes.Structure):
+    _fields_ = [("M", c_int), ("Mc", c_int), ("nodes", c_int), ("precision", c_int), ("si_stages", c_int),
+                ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("ncycles", c_int), ("start", c_int),
+                ("post_sweep", c_int), ("use_graph", c_int)]
+
+
 class SisdcError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -54,7 +64,7 @@ def header_symbols():
     """Entry points declared in include/sisdc.h."""
     with open(HEADER) as fh:
         text = fh.read()
-    return sorted(set(re.findall(r"^\s*(?:sisdc_status|void|const char\*)\s+(sisdc_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:sisdc_status|void|int|const char\*)\s+(sisdc_\w+)\s*\(",
                                  text, flags=re.M)))
 
 
@@ -103,6 +113,18 @@ def load():
         "sisdc_solve_noalloc": (c_int, [P(sisdc_level_desc), c_int, c_double, c_void_p, c_void_p, c_double,
                                         c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
         "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll), P(c_ll)]),
+        "sisdc_ens_create": (c_int, [P(sisdc_ens_instance), c_int, P(sisdc_ens_opts), c_void_p, P(c_void_p)]),
+        "sisdc_ens_destroy": (None, [c_void_p]),
+        "sisdc_ens_layout": (c_int, [c_void_p, c_void_p, P(c_ll)]),
+        "sisdc_ens_step": (c_int, [c_void_p, c_void_p, c_int]),
+        "sisdc_ens_autotune": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+        "sisdc_ens_config": (c_int, [c_void_p, c_void_p]),
+        "sisdc_ens_num_groups": (c_int, [c_void_p]),
+        "sisdc_ens_set_tiles": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
+        "sisdc_ens_sync": (c_int, [c_void_p]),
+        "sisdc_ens_get_stats": (c_int, [c_void_p, P(sisdc_stats), c_void_p]),
+        "sisdc_ens_reset_stats": (c_int, [c_void_p]),
+        "sisdc_ens_last_error": (ctypes.c_char_p, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,6 +347,126 @@ def sisdc_get_kernel_timing(ctx):
 
 def sisdc_last_error(ctx):
     return load().sisdc_last_error(ctx).decode()
+
+
+# ---- batched ensemble ------------------------------------------------------------
+def _echeck(st, ens):
+    if st != SISDC_OK:
+        raise SisdcError(st, load().sisdc_ens_last_error(ens).decode() if ens else "")
+
+
+def sisdc_ens_create(instances, opts, stream=0):
+    arr = (sisdc_ens_instance * len(instances))(*instances)
+    out = c_void_p()
+    _echeck(load().sisdc_ens_create(arr, len(instances), ctypes.byref(opts), c_void_p(stream), ctypes.byref(out)),
+            None)
+    return out.value
+
+
+def sisdc_ens_destroy(ens):
+    load().sisdc_ens_destroy(ens)
+
+
+def sisdc_ens_layout(ens, n):
+    import numpy as np
+    off = np.zeros(n, dtype=np.int64)
+    tot = c_ll()
+    _echeck(load().sisdc_ens_layout(ens, off.ctypes.data, ctypes.byref(tot)), ens)
+    return off, tot.value
+
+
+def sisdc_ens_step(ens, u, nsteps=1):
+    _echeck(load().sisdc_ens_step(ens, _ptr(u), nsteps), ens)
+
+
+def sisdc_ens_num_groups(ens):
+    return load().sisdc_ens_num_groups(ens)
+
+
+def sisdc_ens_config(ens):
+    import numpy as np
+    cfg = np.zeros(8 * sisdc_ens_num_groups(ens), dtype=np.int32)
+    _echeck(load().sisdc_ens_config(ens, cfg.ctypes.data), ens)
+    return cfg.reshape(-1, 4)
+
+
+def sisdc_ens_autotune(ens, u, nsweeps=1):
+    import numpy as np
+    cfg = np.zeros(8 * sisdc_ens_num_groups(ens), dtype=np.int32)
+    _echeck(load().sisdc_ens_autotune(ens, _ptr(u), nsweeps, cfg.ctypes.data), ens)
+    return cfg.reshape(-1, 4)
+
+
+def sisdc_ens_set_tiles(ens, group, fine, epb, grid):
+    _echeck(load().sisdc_ens_set_tiles(ens, group, 1 if fine else 0, epb, grid), ens)
+
+
+def sisdc_ens_sync(ens):
+    _echeck(load().sisdc_ens_sync(ens), ens)
+
+
+def sisdc_ens_get_stats(ens, n=0):
+    import numpy as np
+    s = sisdc_stats()
+    it = np.zeros(max(n, 1), dtype=np.int64)
+    _echeck(load().sisdc_ens_get_stats(ens, ctypes.byref(s), it.ctypes.data if n else None), ens)
+    out = {"cg_solves": s.cg_solves, "cg_iters": s.cg_iters, "cg_max_iters": s.cg_max_iters,
+           "cg_noconv": s.cg_noconv, "ir_steps": s.ir_steps, "sweeps": list(s.sweeps[:2]),
+           "launches": s.launches}
+    if n:
+        out["inst_iters"] = it
+    return out
+
+
+def sisdc_ens_reset_stats(ens):
+    _echeck(load().sisdc_ens_reset_stats(ens), ens)
+
+
+def sisdc_ens_last_error(ens):
+    return load().sisdc_ens_last_error(ens).decode()
+
+
+def make_ens_instance(d):
+    s = sisdc_ens_instance()
+    s.nel[0], s.nel[1] = d["nel"]
+    s.P = d["P"]
+    s.nu = d["nu"]
+    s.adv[0], s.adv[1] = d["adv"]
+    s.dt = d["dt"]
+    return s
+
+
+def make_ens_opts(M=5, Mc=3, nodes="radau_right", precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12,
+                  cg_maxit=1000, Nc=2, ncycles=3, start="cascade", post_sweep=1, use_graph=0):
+    o = sisdc_ens_opts()
+    o.M, o.Mc, o.nodes, o.precision, o.si_stages = M, Mc, NODE_IDS[nodes], precision, si_stages
+    o.cg_rtol, o.cg_maxit, o.Nc, o.ncycles = cg_rtol, cg_maxit, Nc, ncycles
+    o.start, o.post_sweep, o.use_graph = START_IDS[start], post_sweep, use_graph
+    return o
+
+
+class Ensemble:
+    """Owns one ensemble handle built from instance dicts (nel, P, nu, adv, dt)."""
+
+    def __init__(self, instances, stream=0, **kw):
+        self.instances = list(instances)
+        self.ens = sisdc_ens_create([make_ens_instance(d) for d in self.instances], make_ens_opts(**kw), stream)
+        self.offsets, self.total = sisdc_ens_layout(self.ens, len(self.instances))
+
+    def size(self, k):
+        d = self.instances[k]
+        return d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2
+
+    def close(self):
+        if self.ens:
+            sisdc_ens_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- construction from a workload description (marshalling) -------------------

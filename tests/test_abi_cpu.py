@@ -34,9 +34,11 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sisdc.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sisdc_level_desc),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sisdc_level_desc),'
         ' sizeof(sisdc_problem), sizeof(sisdc_stats), offsetof(sisdc_level_desc, lo),'
-        ' offsetof(sisdc_problem, cg_rtol), offsetof(sisdc_stats, launches)); return 0;}\n')
+        ' offsetof(sisdc_problem, cg_rtol), offsetof(sisdc_stats, launches),'
+        ' sizeof(sisdc_ens_instance), offsetof(sisdc_ens_instance, dt), sizeof(sisdc_ens_opts),'
+        ' offsetof(sisdc_ens_opts, cg_rtol)); return 0;}\n')
     exe = tmp_path / "layout"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
@@ -44,7 +46,9 @@ def test_struct_layouts_match_header(tmp_path):
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(sisdc.sisdc_level_desc), ctypes.sizeof(sisdc.sisdc_problem),
                     ctypes.sizeof(sisdc.sisdc_stats), sisdc.sisdc_level_desc.lo.offset,
-                    sisdc.sisdc_problem.cg_rtol.offset, sisdc.sisdc_stats.launches.offset]
+                    sisdc.sisdc_problem.cg_rtol.offset, sisdc.sisdc_stats.launches.offset,
+                    ctypes.sizeof(sisdc.sisdc_ens_instance), sisdc.sisdc_ens_instance.dt.offset,
+                    ctypes.sizeof(sisdc.sisdc_ens_opts), sisdc.sisdc_ens_opts.cg_rtol.offset]
 
 
 def test_invalid_problem_rejected_without_gpu(lib):
@@ -52,3 +56,17 @@ def test_invalid_problem_rejected_without_gpu(lib):
     with pytest.raises(sisdc.SisdcError) as ei:
         sisdc.sisdc_create(p)
     assert ei.value.status == sisdc.SISDC_E_ARG
+
+
+def test_invalid_ensemble_rejected_without_gpu(lib):
+    good = dict(nel=(4, 4), P=3, nu=1e-3, adv=(1.0, 0.0), dt=1e-3)
+    for bad in (dict(good, P=9), dict(good, P=1), dict(good, dt=0.0), dict(good, nel=(0, 4)),
+                dict(good, nu=-1.0), dict(good, adv=(float("nan"), 0.0))):
+        with pytest.raises(sisdc.SisdcError) as ei:
+            sisdc.sisdc_ens_create([sisdc.make_ens_instance(bad)], sisdc.make_ens_opts())
+        assert ei.value.status == sisdc.SISDC_E_ARG
+    for opts in (sisdc.make_ens_opts(M=9), sisdc.make_ens_opts(Mc=6), sisdc.make_ens_opts(start="fmg1"),
+                 sisdc.make_ens_opts(si_stages=3), sisdc.make_ens_opts(cg_rtol=0.0)):
+        with pytest.raises(sisdc.SisdcError) as ei:
+            sisdc.sisdc_ens_create([sisdc.make_ens_instance(good)], opts)
+        assert ei.value.status == sisdc.SISDC_E_ARG
