@@ -30,6 +30,11 @@ __device__ __forceinline__ double coef_value(const Coef& c) {
     return v;
 }
 
+// Block size for `n` working threads, rounded up to whole warps: the block
+// reductions shuffle with full warp masks, so no warp may be partial.  The
+// extra threads are idle (their element index is past the tile).
+inline int warp_round(int n) { return (n + 31) & ~31; }
+
 // Geometry and tables of one level, passed by value.
 struct Geo {
     int dim, nq, nqy, q;          // nodes per direction / per element

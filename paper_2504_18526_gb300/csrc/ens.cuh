@@ -193,7 +193,7 @@ struct EnsSweeper {
     // passes `sel`; store(li, total) runs on one lane per instance
     template <class Sel, class Store>
     __device__ void totals(const double* part, int k, Sel sel, Store store) {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = max(1, (int)(blockDim.x >> 5));
         for (int li = w; li < nloc; li += nw) {
             if (!sel(L[li])) continue;
             const int inst = loc_inst[li];
@@ -749,8 +749,8 @@ size_t ens_smem(int epb) {
 // blocks per SM for a block of epb*Q threads (0 if it cannot run)
 template <int NQ, bool MIX>
 int ens_occupancy_impl(int epb) {
-    const int bs = epb * NQ * NQ;
-    if (bs > 512 || bs < 1) return 0;
+    if (epb < 1 || epb * NQ * NQ > 512) return 0;
+    const int bs = warp_round(epb * NQ * NQ);
     const size_t sh = ens_smem<NQ, MIX>(epb);
     if (cudaFuncSetAttribute(k_ens_sweep<NQ, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess)
         return 0;
@@ -763,7 +763,7 @@ template <int NQ, bool MIX>
 cudaError_t ens_launch_impl(const EnsArgs& a, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)(a.epb * NQ * NQ));
+    cfg.blockDim = dim3((unsigned)warp_round(a.epb * NQ * NQ));
     cfg.dynamicSmemBytes = ens_smem<NQ, MIX>(a.epb);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -140,7 +140,7 @@ static cudaError_t conv_impl(const ConvArgs& a, cudaStream_t s) {
     const int epb = Q >= 256 ? 1 : 256 / Q;
     const long long grid = (a.g.nel + epb - 1) / epb;
     const size_t sh = (NQ * NQ + NQ + 32 + (size_t)epb * 2 * NC * Q) * sizeof(double);
-    k_conv<NQ, DIM, PDE><<<(unsigned)grid, epb * Q, sh, s>>>(a);
+    k_conv<NQ, DIM, PDE><<<(unsigned)grid, warp_round(epb * Q), sh, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -443,7 +443,7 @@ template <int NQ, int DIM>
 static int pcg_grid_impl(const Geo& g, int* block) {
     using S = Sh<NQ, DIM>;
     const int epb = S::Q >= 1024 ? 1 : 1024 / S::Q;
-    const int bs = epb * S::Q;
+    const int bs = warp_round(epb * S::Q);   // in-kernel epb = blockDim / Q is unchanged (epb is maximal)
     const size_t sh = pcg_smem<NQ, DIM>(epb);
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);

@@ -907,7 +907,7 @@ int sweep_config_impl(const Geo& g, int* epb_out, int* block_out) {
     int epb = (int)(want < 1 ? 1 : (want > maxepb ? maxepb : want));
     const int minepb = (32 + S::Q - 1) / S::Q;     // at least one warp per block
     if (epb < minepb) epb = minepb > maxepb ? maxepb : minepb;
-    const int bs = epb * S::Q;
+    const int bs = warp_round(epb * S::Q);
     const size_t sh = sweep_smem<NQ, DIM, PDE, MIX>(epb);
     cudaFuncSetAttribute(k_sweep<NQ, DIM, PDE, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     int per = 0;

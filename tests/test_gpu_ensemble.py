@@ -82,7 +82,7 @@ def test_ensemble_matches_oracle_per_instance(dev, variant, tiles):
     insts = small_instances()
     kw = (dict(nodes="radau_right", si_stages=2, start="cascade") if variant == "radau_si2_cascade"
           else dict(nodes="lobatto", si_stages=1, start="predictor"))
-    E = S.Ensemble(insts, cg_rtol=1e-14, cg_maxit=10000, use_graph=0, **kw)
+    E = S.Ensemble(insts, cg_rtol=1e-14, cg_maxit=500, use_graph=0, **kw)
     if tiles == "ragged":
         # several tiles per instance with a ragged last tile, few blocks:
         # blocks own tiles of several instances and instances span blocks
@@ -106,7 +106,7 @@ def single_path_steps(d, u0, nsteps, dev, precision=S.SISDC_FP64, rtol=1e-14):
     w = dict(pde="convdiff", dim=2, ncomp=1, adv=d["adv"], nu=d["nu"], lo=(0.0, 0.0), hi=(1.0, 1.0),
              nodes="radau_right",
              levels=[dict(nel=d["nel"], P=(d["P"] + 1) // 2, M=3), dict(nel=d["nel"], P=d["P"], M=5)])
-    ctx = S.Context(w, cg_rtol=rtol, cg_maxit=10000, precision=precision)
+    ctx = S.Context(w, cg_rtol=rtol, cg_maxit=500, precision=precision)
     u = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
     for _ in range(nsteps):
         S.sisdc_step(ctx.ctx, u, 0.0, d["dt"], 3, S.SISDC_START_CASCADE, 1)
@@ -122,7 +122,7 @@ def test_ensemble_matches_single_problem_path_and_autotune(dev):
     before and after the autotuner changes the tile shapes."""
     insts = inputs.ensemble_instances(24)
     insts = [dict(d, nel=(min(d["nel"][0], 16), min(d["nel"][1], 16))) for d in insts]
-    E = S.Ensemble(insts, cg_rtol=1e-14, cg_maxit=10000, use_graph=1)
+    E = S.Ensemble(insts, cg_rtol=1e-14, cg_maxit=500, use_graph=1)
     u0 = pack(E, dev)
     refs = [single_path_steps(d, initial(d).ravel(), 2, dev) for d in insts]
     for tuned in (False, True):
@@ -153,7 +153,7 @@ def test_mixed_precision_error_within_bar(dev):
     insts = [dict(d, nel=(min(d["nel"][0], 12), min(d["nel"][1], 12))) for d in insts]
     res = {}
     for prec in (S.SISDC_FP64, S.SISDC_MIXED):
-        E = S.Ensemble(insts, cg_rtol=1e-12, cg_maxit=10000, use_graph=1, precision=prec)
+        E = S.Ensemble(insts, cg_rtol=1e-12, cg_maxit=500, use_graph=1, precision=prec)
         u = pack(E, dev)
         S.sisdc_ens_step(E.ens, u, 10)
         S.sisdc_ens_sync(E.ens)
@@ -172,7 +172,7 @@ def test_full_ensemble_sampled_parity(dev):
     smallest instances against the oracle, the largest against the
     single-problem CUDA path (both relative L2 <= 1e-12)."""
     insts = inputs.ensemble_instances()
-    E = S.Ensemble(insts, cg_rtol=1e-14, cg_maxit=10000, use_graph=1)
+    E = S.Ensemble(insts, cg_rtol=1e-14, cg_maxit=500, use_graph=1)
     u = pack(E, dev)
     S.sisdc_ens_step(E.ens, u, 1)
     S.sisdc_ens_sync(E.ens)
