@@ -752,7 +752,10 @@ int ens_occupancy_impl(int epb) {
     if (epb < 1 || epb * NQ * NQ > 512) return 0;
     const int bs = warp_round(epb * NQ * NQ);
     const size_t sh = ens_smem<NQ, MIX>(epb);
-    if (cudaFuncSetAttribute(k_ens_sweep<NQ, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess)
+    // the attribute covers the largest tile, so that every shape stays launchable
+    const size_t shmax = ens_smem<NQ, MIX>(512 / (NQ * NQ));
+    if (cudaFuncSetAttribute(k_ens_sweep<NQ, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax) !=
+        cudaSuccess)
         return 0;
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ens_sweep<NQ, MIX>, bs, sh) != cudaSuccess) return 0;

@@ -909,7 +909,10 @@ int sweep_config_impl(const Geo& g, int* epb_out, int* block_out) {
     if (epb < minepb) epb = minepb > maxepb ? maxepb : minepb;
     const int bs = warp_round(epb * S::Q);
     const size_t sh = sweep_smem<NQ, DIM, PDE, MIX>(epb);
-    cudaFuncSetAttribute(k_sweep<NQ, DIM, PDE, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    // the attribute covers the largest tile, so that levels of the same degree
+    // with other tile sizes stay launchable
+    cudaFuncSetAttribute(k_sweep<NQ, DIM, PDE, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_smem<NQ, DIM, PDE, MIX>(maxepb));
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<NQ, DIM, PDE, MIX>, bs, sh) != cudaSuccess ||
         per < 1)
