@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="8x8 elements (profiling case)")
+    ap.add_argument("--per-instance", type=int, default=0,
+                    help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -145,6 +147,33 @@ def oracle_sample(args):
     sweeps = ncyc + 1
     print(json.dumps({"seconds": el, "steps": reps, "dof_sweeps": fine_dofs(w) * sweeps * reps,
                       "finite": bool(np.all(np.isfinite(u)))}))
+
+
+def ensemble_oracle_sample(args):
+    """One oracle time step of each of the smallest ensemble instances (FP64)."""
+    import numpy as np
+    from paper_2504_18526_gb300 import inputs
+    from oracle.dg import ConvDiff, DGSpace
+    from oracle.mlsdc import MLSDC
+    from oracle.sdc import Level
+    w = inputs.WORKLOADS["ensemble512"]
+    insts = inputs.ensemble_instances(w["ninst"])
+    order = np.argsort([d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2 for d in insts])
+    t0 = time.perf_counter()
+    dofs = 0
+    k = 0
+    while k < len(order) and (k < 2 or time.perf_counter() - t0 < 10.0):
+        d = insts[order[k]]
+        sp = lambda P: DGSpace(2, d["nel"], P, (0.0, 0.0), (1.0, 1.0), ConvDiff(d["adv"], d["nu"]),
+                               cg_rtol=args.cg_rtol, cg_maxit=1000)
+        fine = sp(d["P"])
+        ml = MLSDC([Level(sp((d["P"] + 1) // 2), w["nodes"], w["Mc"]), Level(fine, w["nodes"], w["M"])], stages=2, Nc=2)
+        X, Y = fine.coords()
+        ml.step(inputs.ensemble_exact(d, X, Y, 0.0), d["dt"], w["ncycles"], start=w["start"])
+        dofs += X.size * (w["ncycles"] + 1)
+        k += 1
+    print(json.dumps({"seconds": time.perf_counter() - t0, "steps": 1, "instances": k, "dof_sweeps": dofs,
+                      "finite": True}))
 
 
 def run_oracle_child(args, steps):
@@ -439,11 +468,158 @@ def main_arm(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# ensemble workload: 512 independent convection-diffusion problems
+# ---------------------------------------------------------------------------
+def ensemble_arm(args):
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import inputs, sisdc as S
+    from paper_2504_18526_gb300.build import build
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build()
+    S.load()
+    w = inputs.WORKLOADS["ensemble512"]
+    insts = inputs.ensemble_instances(w["ninst"])
+    stream = torch.cuda.Stream(device=dev)
+    ncyc = w["ncycles"]
+    nodes = [d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2 for d in insts]
+    dofs_per_step = sum(nodes) * (ncyc + 1)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def exact_field(E, t_of):
+        from oracle.dg import ConvDiff, DGSpace
+        u = np.zeros(E.total)
+        for k, d in enumerate(insts):
+            sp = DGSpace(2, d["nel"], d["P"], (0.0, 0.0), (1.0, 1.0), ConvDiff(d["adv"], d["nu"]))
+            X, Y = sp.coords()
+            u[E.offsets[k]:E.offsets[k] + nodes[k]] = inputs.ensemble_exact(d, X, Y, t_of(d)).ravel()
+        return u
+
+    forms, main = {}, None
+    nsteps_total = args.warmup + args.steps
+    u0_host = ex_host = None
+    for prec_name in (args.precision, "mixed" if args.precision == "fp64" else "fp64"):
+        prec = S.SISDC_MIXED if prec_name == "mixed" else S.SISDC_FP64
+        E = S.Ensemble(insts, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
+                       M=w["M"], Mc=w["Mc"], nodes=w["nodes"], ncycles=ncyc, start=w["start"],
+                       use_graph=0 if args.no_graph else 1)
+        if u0_host is None:       # the packed layout does not depend on the precision
+            u0_host = exact_field(E, lambda d: 0.0)
+            ex_host = exact_field(E, lambda d: nsteps_total * d["dt"])
+        u0 = torch.from_numpy(u0_host).to(dev)
+        cfg = S.sisdc_ens_autotune(E.ens, u0, 1)
+        u = u0.clone()
+        S.sisdc_ens_step(E.ens, u, args.warmup)
+        S.sisdc_ens_sync(E.ens)
+        S.sisdc_ens_reset_stats(E.ens)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            evs[k][0].record(stream)
+            S.sisdc_ens_step(E.ens, u, 1)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        S.sisdc_ens_sync(E.ens)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        st = S.sisdc_ens_get_stats(E.ens, len(insts))
+        ex = torch.from_numpy(ex_host).to(dev)
+        rel = []
+        for k in range(len(insts)):
+            a, b = E.offsets[k], E.offsets[k] + nodes[k]
+            rel.append(float(torch.linalg.vector_norm(u[a:b] - ex[a:b]) / torch.linalg.vector_norm(ex[a:b])))
+        # algorithmic FP64 work of the fine-level sweeps per step (coarse level not counted)
+        iters = st["inst_iters"] / args.steps
+        flops = sum(sweep_flops(d["P"], 1, w["M"], ncyc + 1, iters[k], nodes[k]) for k, d in enumerate(insts))
+        achieved = flops / (ms / args.steps * 1e-3) / 1e12
+        forms[prec_name] = {
+            "ms_per_step": ms / args.steps, "dof_sweeps_per_s": dofs_per_step * args.steps / (ms * 1e-3),
+            "rel_l2_error_vs_exact": {"mean": float(np.mean(rel)), "max": float(np.max(rel))},
+            "steps_for_error": nsteps_total,
+            "cg_iters_per_solve": st["cg_iters"] / max(1, st["cg_solves"]),
+            "ir_steps": st["ir_steps"], "launches_per_step": st["launches"] / args.steps,
+            "fine_sweep_fp64_tflops": achieved,
+            "tiles": cfg.tolist(), "clocks": clocks}
+        if main is None:
+            main = dict(forms[prec_name], ms=ms, clocks=clocks, achieved=achieved, flops=flops, st=st)
+        E.close()
+
+    per_inst = None
+    if args.per_instance > 0:
+        # the same instances stepped one by one through the single-problem path (FP64)
+        idx = list(range(0, len(insts), max(1, len(insts) // args.per_instance)))[: args.per_instance]
+        tot_ms, tot_nodes = 0.0, 0
+        for k in idx:
+            d = insts[k]
+            wk = dict(pde="convdiff", dim=2, ncomp=1, adv=d["adv"], nu=d["nu"], lo=(0.0, 0.0), hi=(1.0, 1.0),
+                      nodes=w["nodes"], levels=[dict(nel=d["nel"], P=(d["P"] + 1) // 2, M=w["Mc"]),
+                                                dict(nel=d["nel"], P=d["P"], M=w["M"])])
+            ctx = S.Context(wk, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, cg_maxit=1000, use_graph=1)
+            from oracle.dg import ConvDiff, DGSpace
+            X, Y = DGSpace(2, d["nel"], d["P"], (0.0, 0.0), (1.0, 1.0), ConvDiff(d["adv"], d["nu"])).coords()
+            uk = torch.from_numpy(inputs.ensemble_exact(d, X, Y, 0.0).ravel().copy()).to(dev)
+            for _ in range(2):
+                S.sisdc_step(ctx.ctx, uk, 0.0, d["dt"], ncyc, S.START_IDS[w["start"]], 1)
+            S.sisdc_sync(ctx.ctx)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            S.sisdc_step(ctx.ctx, uk, 0.0, d["dt"], ncyc, S.START_IDS[w["start"]], 1)
+            a1.record(stream)
+            S.sisdc_sync(ctx.ctx)
+            tot_ms += a0.elapsed_time(a1)
+            tot_nodes += nodes[k]
+            ctx.close()
+        per_inst = {"instances": len(idx), "ms_for_sample": tot_ms,
+                    "dof_sweeps_per_s": tot_nodes * (ncyc + 1) / (tot_ms * 1e-3),
+                    "note": "FP64 single-problem path, one graph-captured step per instance, sequential"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", "ensemble512",
+                            "--cg-rtol", str(args.cg_rtol)], capture_output=True, text=True, env=env, cwd=ROOT)
+        if r.returncode == 0:
+            o = json.loads(r.stdout.strip().splitlines()[-1])
+            cpu = {"value": o["dof_sweeps"] / o["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "one oracle time step of each of the %d smallest instances (%.1f s, FP64 numpy, "
+                             "1 thread)" % (o["instances"], o["seconds"]), "cpu": cpu_model()}
+    out = {
+        "metric": METRIC, "value": dofs_per_step * args.steps / (main["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "ensemble512", "instances": len(insts), "fine_nodes": sum(nodes),
+                   "fine_sweeps_per_step": ncyc + 1, "levels": "fine P, coarse ceil(P/2); Radau-Right 5/3",
+                   "precision": args.precision, "cuda_graph": not args.no_graph,
+                   "l2": "state larger than L2 (174 MB per vector) and 512 MB flush between steps"},
+        "roofline": {"bound": "alu", "kernel": "k_ens_sweep (all launches of a step; fine-level work counted)",
+                     "achieved": main["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": main["achieved"] / FP64_PEAK_TFLOPS, "traffic": None,
+                     "algorithmic_flop_per_step": main["flops"]},
+        "forms": forms, "per_instance_path": per_inst, "cpu_baseline": cpu, "clocks": main["clocks"],
+        "gpu_launches": int(round(main["st"]["launches"])),
+    }
+    print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.oracle_sample:
-        oracle_sample(a)
+        if a.workload == "ensemble512":
+            ensemble_oracle_sample(a)
+        else:
+            oracle_sample(a)
     elif a.impl == "reference":
         reference_arm(a)
+    elif a.workload == "ensemble512":
+        ensemble_arm(a)
     else:
         main_arm(a)

@@ -192,16 +192,19 @@ def ensemble_modes(inst, K=6, amp=1.0):
 def ensemble_exact(inst, X, Y, t, K=6, amp=1.0):
     """Exact solution of u_t + a . grad u = nu lap u on the periodic unit square
     for the instance's Fourier data: every mode is shifted by a t and damped
-    by exp(-4 pi^2 nu |k|^2 t)."""
+    by exp(-4 pi^2 nu |k|^2 t).  a cos(phi) + b sin(phi) is evaluated as
+    Re((a - i b) e^{i phi}) with e^{i phi} = e^{i 2 pi kx x} e^{i 2 pi ky y}."""
     modes, A = ensemble_modes(inst, K, amp)
     ax, ay = inst["adv"]
-    Xs, Ys = X - ax * t, Y - ay * t
-    out = np.zeros((1,) + np.shape(X))
+    Xs = np.asarray(X, dtype=float) - ax * t
+    Ys = np.asarray(Y, dtype=float) - ay * t
+    ex = {k: np.exp(2j * math.pi * k * Xs) for k in range(-K, K + 1)}
+    ey = {k: np.exp(2j * math.pi * k * Ys) for k in range(-K, K + 1)}
+    acc = np.zeros(Xs.shape, dtype=complex)
     for kx, ky, a, b in modes:
         damp = math.exp(-4.0 * math.pi ** 2 * inst["nu"] * (kx * kx + ky * ky) * t)
-        ph = 2.0 * math.pi * (kx * Xs + ky * Ys)
-        out[0] += A * damp * (a[0] * np.cos(ph) + b[0] * np.sin(ph))
-    return out
+        acc += (A * damp * complex(a[0], -b[0])) * (ex[kx] * ey[ky])
+    return acc.real[None]
 
 
 def random_field(shape, seed, scale=1.0):
