@@ -54,14 +54,17 @@ struct EnsSweeper {
     static constexpr int NSLOT = 4;          // partial-sum slots per set (two sets alternate)
 
     static size_t smem_bytes(int epb) {
-        const size_t d = 2 * NQ * NQ + 2 * NQ + 32 + (size_t)epb * Q + (size_t)epb * TRS + (size_t)epb * 2 * Q;
+        const size_t d = 2 * NQ * NQ + 2 * NQ + 32 + 2 * 3 * 32 + (size_t)epb * Q + (size_t)epb * TRS +
+                         (size_t)epb * 2 * Q;
         const size_t r = MIX ? (2 * NQ * NQ + NQ + (size_t)epb * Q + (size_t)epb * TRS) : 0;
-        return sizeof(EnsInst) + d * sizeof(double) + r * sizeof(RT) + 16;
+        return ENS_LSMEM * sizeof(EnsInst) + d * sizeof(double) + r * sizeof(RT) + 16;
     }
 
     const EnsArgs& a;
-    EnsInst* sI;          // the current tile's instance (shared memory)
-    double *sD, *sK, *sw, *sdl, *scratch, *su, *sf, *sF;
+    EnsInst* sI;          // the block's instances (shared memory): all of them when
+                          // nloc <= ENS_LSMEM (pre), else the current tile's in slot 0
+    bool pre;
+    double *sD, *sK, *sw, *sdl, *scratch, *wsum, *su, *sf, *sF;
     RT *rD, *rK, *rw, *ru, *rf;
     int le, node, i, j, G;
     int solve_parity;
@@ -73,12 +76,13 @@ struct EnsSweeper {
     __device__ EnsSweeper(const EnsArgs& args) : a(args) {
         extern __shared__ double sm[];
         sI = reinterpret_cast<EnsInst*>(sm);
-        sD = sm + sizeof(EnsInst) / sizeof(double);
+        sD = sm + ENS_LSMEM * sizeof(EnsInst) / sizeof(double);
         sK = sD + NQ * NQ;
         sw = sK + NQ * NQ;
         sdl = sw + NQ;
         scratch = sdl + NQ;
-        su = scratch + 32;
+        wsum = scratch + 32;      // [2][3][32] per-warp sums of the last two tiles
+        su = wsum + 2 * 3 * 32;
         sf = su + a.epb * Q;
         sF = sf + a.epb * TRS;
         RT* rb = reinterpret_cast<RT*>(sF + a.epb * 2 * Q);
@@ -118,10 +122,25 @@ struct EnsSweeper {
         loc_inst = a.loc_inst + (size_t)blockIdx.x * a.lmax;
         L = reinterpret_cast<EnsLocal*>(a.loc) + (size_t)blockIdx.x * a.lmax;
         dinv_tab = a.loc_dinv + (size_t)blockIdx.x * a.lmax * Q;
+        pre = nloc <= ENS_LSMEM;
+        if (pre) {
+            const int words = (int)(sizeof(EnsInst) / 8);
+            for (int t = threadIdx.x; t < nloc * words; t += blockDim.x) {
+                const int li = t / words, k = t - li * words;
+                reinterpret_cast<unsigned long long*>(sI + li)[k] =
+                    __ldg(reinterpret_cast<const unsigned long long*>(a.inst + loc_inst[li]) + k);
+            }
+        }
         __syncthreads();
     }
 
-    // ---- instance geometry (staged in shared memory per tile) -------------------
+    // ---- instance geometry --------------------------------------------------------
+    // local instance li (global index inst): from the preloaded table, or
+    // staged into slot 0 (block-wide; contains barriers)
+    __device__ const EnsInst& inst_of(int li, int inst) {
+        if (pre) return sI[li];
+        return load_inst(inst);
+    }
     __device__ const EnsInst& load_inst(int inst) {
         __syncthreads();
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.inst + inst);
@@ -160,33 +179,51 @@ struct EnsSweeper {
     // `which` is 1 (or 2).
     template <int K, class Fn>
     __device__ void tiles(double* part, int which, Fn fn) {
+        // thread 0 keeps the running sums of the current instance (cur); the
+        // warp sums of a tile are added after the tile's closing barrier, in
+        // warp order, so every sum has a fixed order
         double run[K > 0 ? K : 1];
-        int cur = -1;
+        int cur = -1, pend = -1, pbuf = 0, buf = 0;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
         for (int k = 0; k < K; ++k) run[k] = 0.0;
+        auto consume = [&]() {
+            if (cur != pend) {
+                if (cur >= 0)
+                    for (int k = 0; k < K; ++k) part[((size_t)k * a.ninst + cur) * G + blockIdx.x] = run[k];
+                cur = pend;
+                for (int k = 0; k < K; ++k) run[k] = 0.0;
+            }
+            for (int k = 0; k < K; ++k) {
+                double s = 0.0;
+                for (int w = 0; w < nw; ++w) s += wsum[(pbuf * 3 + k) * 32 + w];
+                run[k] += s;
+            }
+        };
         for (long long t = blockIdx.x; t < a.ntiles; t += G) {
             const int4 td = __ldg(a.tiles + t);       // (instance, local index, first element, elements)
             if (which == 1 && !L[td.y].act) continue;
             if (which == 2 && !L[td.y].oact) continue;
-            const EnsInst& I = load_inst(td.x);
+            if (K > 0 && threadIdx.x == 0 && pend >= 0) consume();
+            const EnsInst& I = inst_of(td.y, td.x);
             double acc[K > 0 ? K : 1];
             for (int k = 0; k < K; ++k) acc[k] = 0.0;
             fn(I, (long long)td.z, td.w, td.y, acc);
             if (K > 0) {
-                if (threadIdx.x == 0 && cur != td.x) {
-                    if (cur >= 0)
-                        for (int k = 0; k < K; ++k) part[((size_t)k * a.ninst + cur) * G + blockIdx.x] = run[k];
-                    cur = td.x;
-                    for (int k = 0; k < K; ++k) run[k] = 0.0;
-                }
                 for (int k = 0; k < K; ++k) {
-                    const double s = block_sum(acc[k], scratch);
-                    if (threadIdx.x == 0) run[k] += s;
+                    const double v = warp_sum(acc[k]);
+                    if (lane == 0) wsum[(buf * 3 + k) * 32 + wid] = v;
                 }
+                pend = td.x;
+                pbuf = buf;
+                buf ^= 1;
             }
             __syncthreads();
         }
-        if (K > 0 && threadIdx.x == 0 && cur >= 0)
-            for (int k = 0; k < K; ++k) part[((size_t)k * a.ninst + cur) * G + blockIdx.x] = run[k];
+        if (K > 0 && threadIdx.x == 0) {
+            if (pend >= 0) consume();
+            if (cur >= 0)
+                for (int k = 0; k < K; ++k) part[((size_t)k * a.ninst + cur) * G + blockIdx.x] = run[k];
+        }
     }
 
     // total of slot k of instance loc_inst[li] for every local instance that
@@ -271,15 +308,28 @@ struct EnsSweeper {
 
     // per-instance implicit coefficient and Jacobi factors of node m
     __device__ void set_coeffs(int m) {
+        if (pre) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < nloc * Q; t += blockDim.x) {
+                const int li = t / Q, q = t - li * Q;
+                const EnsInst& I = sI[li];
+                const double dtm = I.dt * a.dtau[m];
+                const double c = dtm * nut(I, dtm);
+                double ms, dg;
+                mass_diag(I, q % NQ, q / NQ, ms, dg);
+                dinv_tab[(size_t)li * Q + q] = 1.0 / (ms + c * dg);
+            }
+        }
         for (int li = 0; li < nloc; ++li) {
-            const EnsInst& I = load_inst(loc_inst[li]);
+            const EnsInst& I = pre ? sI[li] : load_inst(loc_inst[li]);
             const double dtm = I.dt * a.dtau[m];
             const double c = dtm * nut(I, dtm);
-            for (int t = threadIdx.x; t < Q; t += blockDim.x) {
-                double ms, dg;
-                mass_diag(I, t % NQ, t / NQ, ms, dg);
-                dinv_tab[(size_t)li * Q + t] = 1.0 / (ms + c * dg);
-            }
+            if (!pre)
+                for (int t = threadIdx.x; t < Q; t += blockDim.x) {
+                    double ms, dg;
+                    mass_diag(I, t % NQ, t / NQ, ms, dg);
+                    dinv_tab[(size_t)li * Q + t] = 1.0 / (ms + c * dg);
+                }
             if (threadIdx.x == 0) {
                 EnsLocal& s = L[li];
                 s.c = c;

@@ -148,6 +148,7 @@ struct sisdc_ens_s {
     std::string err;
     cudaGraphExec_t gexec = nullptr;
     double* g_u = nullptr;
+    long long g_launches = 0, g_sweeps[2] = {0, 0};   // per replay of the captured step
 };
 
 namespace {
@@ -676,9 +677,16 @@ sisdc_status sisdc_ens_step(sisdc_ens c, double* u, int nsteps) {
                     c->gexec = nullptr;
                 }
                 cudaGraph_t graph = nullptr;
+                const long long l0 = c->launches, s0 = c->sweeps[0], s1 = c->sweeps[1];
                 check(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
                 try {
                     enqueue_step(c, u);
+                    c->g_launches = c->launches - l0;
+                    c->g_sweeps[0] = c->sweeps[0] - s0;
+                    c->g_sweeps[1] = c->sweeps[1] - s1;
+                    c->launches = l0;
+                    c->sweeps[0] = s0;
+                    c->sweeps[1] = s1;
                 } catch (...) {
                     cudaStreamEndCapture(c->stream, &graph);
                     if (graph) cudaGraphDestroy(graph);
@@ -691,6 +699,9 @@ sisdc_status sisdc_ens_step(sisdc_ens c, double* u, int nsteps) {
                 c->g_u = u;
             }
             check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+            c->launches += c->g_launches;
+            c->sweeps[0] += c->g_sweeps[0];
+            c->sweeps[1] += c->g_sweeps[1];
         }
     } catch (const Fail& f) {
         return f.st;

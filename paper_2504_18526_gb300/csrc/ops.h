@@ -168,6 +168,9 @@ struct EnsInst {
     double dt;                               // the instance's time step
 };
 
+// instance records a block keeps in shared memory for the whole launch
+constexpr int ENS_LSMEM = 128;
+
 struct EnsArgs {
     const EnsInst* inst;    // [ninst]
     int ninst;

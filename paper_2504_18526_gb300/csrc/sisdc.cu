@@ -87,6 +87,7 @@ struct sisdc_ctx_s {
     double* g_u = nullptr;
     double g_dt = 0.0;
     int g_ncycles = -1, g_start = -1, g_post = -1;
+    long long g_launches = 0, g_sweeps[8] = {0};   // per replay of the captured step
 };
 
 namespace {
@@ -785,9 +786,18 @@ sisdc_status sisdc_step(sisdc_ctx c, double* u, double t, double dt, int ncycles
               c->g_post == post)) {
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
             cudaGraph_t graph = nullptr;
+            const long long l0 = c->launches;
+            long long s0[8];
+            for (int l = 0; l < 8; ++l) s0[l] = c->sweeps[l];
             check(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             try {
                 enqueue_step(c, u, dt, ncycles, start, post);
+                c->g_launches = c->launches - l0;
+                c->launches = l0;
+                for (int l = 0; l < 8; ++l) {
+                    c->g_sweeps[l] = c->sweeps[l] - s0[l];
+                    c->sweeps[l] = s0[l];
+                }
             } catch (...) {
                 cudaStreamEndCapture(c->stream, &graph);
                 if (graph) cudaGraphDestroy(graph);
@@ -800,6 +810,8 @@ sisdc_status sisdc_step(sisdc_ctx c, double* u, double t, double dt, int ncycles
             c->g_u = u; c->g_dt = dt; c->g_ncycles = ncycles; c->g_start = start; c->g_post = post;
         }
         check(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+        c->launches += c->g_launches;
+        for (int l = 0; l < 8; ++l) c->sweeps[l] += c->g_sweeps[l];
     } catch (const Fail& f) {
         return f.st;
     }
