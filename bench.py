@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="8x8 elements (profiling case)")
+    ap.add_argument("--ninst", type=int, default=0, help="ensemble: first N instances only (profiling case)")
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble: default tile shapes")
     ap.add_argument("--per-instance", type=int, default=0,
                     help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -483,6 +485,8 @@ def ensemble_arm(args):
     S.load()
     w = inputs.WORKLOADS["ensemble512"]
     insts = inputs.ensemble_instances(w["ninst"])
+    if args.ninst > 0:
+        insts = insts[:args.ninst]
     stream = torch.cuda.Stream(device=dev)
     ncyc = w["ncycles"]
     nodes = [d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2 for d in insts]
@@ -510,7 +514,7 @@ def ensemble_arm(args):
             u0_host = exact_field(E, lambda d: 0.0)
             ex_host = exact_field(E, lambda d: nsteps_total * d["dt"])
         u0 = torch.from_numpy(u0_host).to(dev)
-        cfg = S.sisdc_ens_autotune(E.ens, u0, 1)
+        cfg = S.sisdc_ens_config(E.ens) if args.no_autotune else S.sisdc_ens_autotune(E.ens, u0, 1)
         u = u0.clone()
         S.sisdc_ens_step(E.ens, u, args.warmup)
         S.sisdc_ens_sync(E.ens)
@@ -596,7 +600,8 @@ def ensemble_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": "ensemble512", "instances": len(insts), "fine_nodes": sum(nodes),
+        "config": {"workload": "ensemble512" + (" (first %d instances)" % len(insts) if args.ninst else ""),
+                   "instances": len(insts), "fine_nodes": sum(nodes), "autotuned": not args.no_autotune,
                    "fine_sweeps_per_step": ncyc + 1, "levels": "fine P, coarse ceil(P/2); Radau-Right 5/3",
                    "precision": args.precision, "cuda_graph": not args.no_graph,
                    "l2": "state larger than L2 (174 MB per vector) and 512 MB flush between steps"},
