@@ -112,6 +112,43 @@ class Euler2:
         return np.abs(u[2] / u[0]) + self.sound(u)
 
 
+class NavierStokes2(Euler2):
+    """2D compressible Navier-Stokes (Sec. 2.2): the Euler fluxes plus the
+    viscous flux of a Newtonian fluid with Stokes' hypothesis and Fourier heat
+    conduction, in units with gas constant 1: temperature T = p / rho,
+    viscosity mu = 1 / Re, conductivity kappa = mu gamma / ((gamma - 1) Pr).
+    Viscous flux F_v^x = (0, tau_xx, tau_xy, v_x tau_xx + v_y tau_xy + kappa T_x)
+    (and F_v^y alike) with tau = mu (grad v + grad v^T - 2/3 div v I).
+    The viscous term is explicit (in f only); the implicit diffusion-type term
+    of the SI integrators uses the scalar nu_d = max(4/3, gamma / Pr) mu / rho_ref
+    (reading: rho_ref = the smallest density of the initial data)."""
+
+    def __init__(self, gamma, Re, Pr, rho_ref=1.0):
+        super().__init__(gamma)
+        self.mu = 1.0 / float(Re)
+        self.Pr = float(Pr)
+        self.kappa = self.mu * self.gamma / ((self.gamma - 1.0) * self.Pr)
+        self.nu_d = max(4.0 / 3.0, self.gamma / self.Pr) * self.mu / float(rho_ref)
+        self.viscous = True
+
+    def primitive(self, u):
+        """(v_x, v_y, T) at every node."""
+        r = u[0]
+        return np.stack([u[1] / r, u[2] / r, self.pressure(u) / r])
+
+    def viscous_flux(self, W, gx, gy):
+        """F_v^x, F_v^y from the primitive values W and their gradients."""
+        vx, vy = W[0], W[1]
+        div = gx[0] + gy[1]
+        txx = self.mu * (2.0 * gx[0] - (2.0 / 3.0) * div)
+        tyy = self.mu * (2.0 * gy[1] - (2.0 / 3.0) * div)
+        txy = self.mu * (gy[0] + gx[1])
+        zero = np.zeros_like(vx)
+        Fx = np.stack([zero, txx, txy, vx * txx + vy * txy + self.kappa * gx[2]])
+        Fy = np.stack([zero, txy, tyy, vx * txy + vy * tyy + self.kappa * gy[2]])
+        return Fx, Fy
+
+
 # --------------------------------------------------------------------------
 # DG-SEM level
 # --------------------------------------------------------------------------
@@ -237,10 +274,46 @@ class DGSpace:
         return -self.A(u) / self.mass
 
     def diff(self, u):
-        """Physical diffusion term of f (nu L u; zero for Euler)."""
+        """Physical diffusion term of f: nu L u, or the Navier-Stokes viscous
+        term (zero for Euler)."""
+        if getattr(self.pde, "viscous", False):
+            return self.visc(u)
         if self.pde.nu == 0.0:
             return np.zeros_like(u)
         return self.pde.nu * self.lap(u)
+
+    # ---- viscous term (BR1) -------------------------------------------------
+    def _lift_derivative(self, v, axis, h, sign):
+        """Strong-form DG derivative of v along x (axis=-1) or y (axis=-2)
+        with central face values {v} (Bassi-Rebay 1):
+        (2/h) D v + (2/h)/w_P (v* - v) at the upper end - (2/h)/w_0 (v* - v)
+        at the lower end, v* the average of the two traces; `sign` = +1
+        (the same form serves the gradient and the divergence)."""
+        D, w = self.D, self.w
+        if axis == -1:
+            d = (2.0 / h) * np.einsum('ik,...k->...i', D, v)
+            up, lo = v[..., -1], v[..., 0]                           # [..., ey, ex, j]
+            star = 0.5 * (up + np.roll(lo, -1, axis=-2))          # interface e | e+1 (x)
+            d[..., -1] += sign * (2.0 / h) / w[-1] * (star - up)
+            d[..., 0] -= sign * (2.0 / h) / w[0] * (np.roll(star, 1, axis=-2) - lo)
+        else:
+            d = (2.0 / h) * np.einsum('jk,...kx->...jx', D, v)
+            up, lo = v[..., -1, :], v[..., 0, :]                     # [..., ey, ex, i]
+            star = 0.5 * (up + np.roll(lo, -1, axis=-3))          # interface e | e+1 (y)
+            d[..., -1, :] += sign * (2.0 / h) / w[-1] * (star - up)
+            d[..., 0, :] -= sign * (2.0 / h) / w[0] * (np.roll(star, 1, axis=-3) - lo)
+        return d
+
+    def visc(self, u):
+        """div F_v(u, grad u) by BR1: lifted gradients of the primitive
+        variables with central traces, then the divergence of the viscous flux
+        with central face fluxes (both in strong form)."""
+        pde = self.pde
+        W = pde.primitive(u)                                        # [3, ey, ex, j, i]
+        gx = self._lift_derivative(W, -1, self.hx, 1.0)
+        gy = self._lift_derivative(W, -2, self.hy, 1.0)
+        Fx, Fy = pde.viscous_flux(W, gx, gy)
+        return self._lift_derivative(Fx, -1, self.hx, 1.0) + self._lift_derivative(Fy, -2, self.hy, 1.0)
 
     @property
     def nu_d(self):

@@ -46,6 +46,13 @@ WORKLOADS = {
                 dict(nel=(64, 64), P=7, M=5)],
         nodes="lobatto", cfl=0.5, nsteps=200, ncycles=3, start="fmg1",
         vortex_beta=5.0, mach=0.5, angle_deg=45.0),
+    # 2D compressible Navier-Stokes doubly periodic shear layer, 128x128 elements, P = 5
+    "ns_shear": dict(
+        id=4, pde="ns", dim=2, ncomp=4, gamma=1.4, Re=2500.0, Pr=0.72, mach=0.3,
+        lo=(0.0, 0.0), hi=(1.0, 1.0),
+        levels=[dict(nel=(128, 128), P=3, M=3), dict(nel=(128, 128), P=5, M=5)],
+        nodes="radau_right", cfl=0.5, nsteps=100, ncycles=3, start="cascade",
+        shear_delta=1.0 / 80.0, perturb_amp=0.05),
     # 512 independent 2D convection-diffusion problems of mixed sizes and degrees
     "ensemble512": dict(
         id=5, pde="convdiff", dim=2, ncomp=1, ninst=512, nel_range=(8, 48), P_range=(3, 8),
@@ -117,13 +124,27 @@ def isentropic_vortex(X, Y, t=0.0, gamma=1.4, beta=5.0, mach=0.5, angle_deg=45.0
     return np.stack([rho, rho * vx, rho * vy, E])
 
 
+def shear_layer(X, Y, gamma=1.4, mach=0.3, delta=1.0 / 80.0, amp=0.05, seed_extra=0):
+    """Conserved variables of the doubly periodic shear layer on [0,1]^2:
+    rho = 1, v_x = tanh((y - 1/4)/delta) for y <= 1/2 and tanh((3/4 - y)/delta)
+    above, v_y = amp sin(2 pi (x + phi)) with a seeded phase phi in [0, 1),
+    p = 1 / (gamma Mach^2)."""
+    phi = float(rng_for(4, seed_extra).uniform(0.0, 1.0))
+    vx = np.where(Y <= 0.5, np.tanh((Y - 0.25) / delta), np.tanh((0.75 - Y) / delta))
+    vy = amp * np.sin(2.0 * math.pi * (X + phi))
+    rho = np.ones_like(X)
+    p = np.full_like(X, 1.0 / (gamma * mach * mach))
+    E = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy)
+    return np.stack([rho, rho * vx, rho * vy, E])
+
+
 def max_wave_speed(pde, u, gamma=1.4, adv=(1.0, 0.0)):
     """Largest characteristic speed of the initial data (sets dt from CFL)."""
     if pde == "convdiff":
         return max(abs(adv[0]), abs(adv[1]))
     if pde == "burgers":
         return float(2.0 * np.max(np.abs(u)))
-    if pde == "euler":
+    if pde in ("euler", "ns"):
         rho = u[0]
         vx, vy = u[1] / rho, u[2] / rho
         p = (gamma - 1.0) * (u[3] - 0.5 * rho * (vx * vx + vy * vy))
@@ -147,6 +168,8 @@ def initial_state(name, X, Y, seed_extra=0):
     if name == "euler_vortex":
         return isentropic_vortex(X, Y, 0.0, w["gamma"], w["vortex_beta"], w["mach"],
                                  w["angle_deg"], w["lo"], w["hi"])
+    if name == "ns_shear":
+        return shear_layer(X, Y, w["gamma"], w["mach"], w["shear_delta"], w["perturb_amp"], seed_extra)
     raise ValueError(name)
 
 

@@ -2,7 +2,7 @@
 array plumbing between numpy (oracle) and torch (CUDA library)."""
 import numpy as np
 
-from oracle.dg import DGSpace, ConvDiff, Burgers2, Euler2
+from oracle.dg import DGSpace, ConvDiff, Burgers2, Euler2, NavierStokes2
 from oracle.mlsdc import MLSDC
 from oracle.sdc import Level
 
@@ -14,6 +14,8 @@ def oracle_pde(w):
         return Burgers2(w["nu"])
     if w["pde"] == "euler":
         return Euler2(w["gamma"])
+    if w["pde"] == "ns":
+        return NavierStokes2(w["gamma"], w["Re"], w["Pr"], w.get("rho_ref", 1.0))
     raise ValueError(w["pde"])
 
 
@@ -45,6 +47,6 @@ def physical_euler_state(shape, rng):
 
 def random_state(w, shape, seed):
     rng = np.random.default_rng(1000 + seed)
-    if w["pde"] == "euler":
+    if w["pde"] in ("euler", "ns"):
         return physical_euler_state(shape, rng)
     return rng.standard_normal(shape)

@@ -187,3 +187,21 @@ def test_convdiff1d_exact_solution():
         errs.append(fine.l2(u - inputs.convdiff1d_exact(X, nsteps * dt)))
     assert errs[0] < 2e-4
     assert errs[0] / errs[1] > 16.0        # at least 4th order under joint refinement
+
+
+def test_ns_step_conserves_mass_momentum_energy():
+    """Shear-layer data on a coarse grid: one two-level SI-MLSDC step conserves
+    all four integrals to round-off (conservative convective, viscous and SIPG
+    operators on a periodic mesh) and changes the state."""
+    from oracle.dg import NavierStokes2
+    w = inputs.WORKLOADS["ns_shear"]
+    pde = NavierStokes2(w["gamma"], 200.0, w["Pr"])
+    mk = lambda p: DGSpace(2, (4, 4), p, (0.0, 0.0), (1.0, 1.0), pde, cg_rtol=1e-15)
+    fine = mk(4)
+    X, Y = fine.coords()
+    u0 = inputs.shear_layer(X, Y, w["gamma"], w["mach"], delta=0.1)
+    ml = MLSDC([Level(mk(2), "radau_right", 3), Level(fine, "radau_right", 5)], stages=2)
+    u1 = ml.step(u0, 2e-4, 2)
+    scale = np.max(np.abs(fine.integral(u0))) + 1.0
+    assert np.max(np.abs(fine.integral(u1) - fine.integral(u0))) < 1e-13 * scale
+    assert np.max(np.abs(u1 - u0)) > 1e-6
