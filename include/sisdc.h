@@ -61,11 +61,18 @@ typedef enum { SISDC_RADAU_RIGHT = 0, SISDC_LOBATTO = 1 } sisdc_nodes;
 
 /* PDEs (Sec. 2 and the workloads): scalar convection-diffusion with constant
  * velocity adv, two-component viscous Burgers with flux u (x) u, 2D
- * compressible Euler with a perfect gas of ratio gamma. */
+ * compressible Euler with a perfect gas of ratio gamma, and 2D compressible
+ * Navier-Stokes (Sec. 2.2: Newtonian stress with Stokes' hypothesis, Fourier
+ * heat flux; units with gas constant 1, T = p / rho, viscosity mu,
+ * conductivity mu gamma / ((gamma - 1) Pr)).  The Navier-Stokes viscous term
+ * enters f explicitly, discretised by BR1 (lifted gradients of (v, T) with
+ * central traces, central viscous face fluxes); the implicit term of the SI
+ * integrators is nu_tilde L with nu_d = max(4/3, gamma / Pr) mu / rho_ref. */
 typedef enum {
     SISDC_PDE_CONVDIFF = 0,
     SISDC_PDE_BURGERS = 1,
-    SISDC_PDE_EULER = 2
+    SISDC_PDE_EULER = 2,
+    SISDC_PDE_NS = 3
 } sisdc_pde;
 
 /* SISDC_FP64: every step in FP64.  SISDC_MIXED: operator applications and
@@ -109,6 +116,9 @@ typedef struct {
     int cg_maxit;       /* iteration cap of the implicit solves               */
     int Nc;             /* coarse sweeps per V-cycle (Algorithm 2; default 2) */
     int use_graph;      /* 1: sisdc_step replays a captured CUDA graph        */
+    double mu;          /* dynamic viscosity 1/Re (Navier-Stokes)             */
+    double Pr;          /* Prandtl number (Navier-Stokes)                     */
+    double rho_ref;     /* reference density of nu_d (Navier-Stokes; > 0)     */
 } sisdc_problem;
 
 typedef struct {
@@ -158,6 +168,13 @@ sisdc_status sisdc_apply_conv(sisdc_level lv, const double* d_u, double* d_c);
 
 /* d_Lu = L d_u with L = -M^{-1} A, A the SIPG stiffness (per component). */
 sisdc_status sisdc_apply_lap(sisdc_level lv, const double* d_u, double* d_Lu);
+
+/* d_out = f(d_u), the full right-hand side of the PDE on this level (Sec. 2):
+ * c(u) plus nu L u (convection-diffusion, Burgers) or plus the BR1 viscous
+ * term (Navier-Stokes).  Device arrays [ncomp][nel][Q].  Runs the persistent
+ * sweep kernel on the level's work arrays, whose caches it invalidates (the
+ * next sweep refreshes them). */
+sisdc_status sisdc_apply_f(sisdc_level lv, const double* d_u, double* d_out);
 
 /* Solve (I - c L) x = rhs, i.e. (M + c A) x = M rhs, by Jacobi-preconditioned
  * CG; d_x holds the initial guess on entry and the solution on exit.  The

@@ -21,7 +21,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 SOURCES = (["ops_sipg.cu", "ops_conv.cu", "ops_misc.cu", "tables.cpp", "sisdc.cu", "noalloc.cu", "mlp.cu",
             "sweep_dispatch.cu", "ensemble.cu", "ens_lo.cu", "ens_hi.cu", "ens_lo_mix.cu", "ens_hi_mix.cu"] +
-           ["sweep_%s_%s%s.cu" % (p, h, m) for p in ("cd", "bu", "eu") for h in ("lo", "hi") for m in ("", "_mix")])
+           ["sweep_%s_%s%s.cu" % (p, h, m) for p in ("cd", "bu", "eu", "ns") for h in ("lo", "hi") for m in ("", "_mix")])
 
 
 def nvcc():

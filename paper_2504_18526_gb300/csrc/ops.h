@@ -66,7 +66,8 @@ struct ConvArgs {
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s);
 
 // ---- persistent sweep kernel (sweep.cuh, sweep_*.cu) ------------------------
-enum SweepMode : int { SW_REFRESH = 0, SW_PREDICT = 1, SW_CORRECT = 2 };
+// SW_FEVAL: f(u0) into fout (one state; uses the level's work arrays)
+enum SweepMode : int { SW_REFRESH = 0, SW_PREDICT = 1, SW_CORRECT = 2, SW_FEVAL = 3 };
 
 struct SweepArgs {
     Geo g;
@@ -74,6 +75,10 @@ struct SweepArgs {
     double gamma, ax, ay;   // flux parameters
     double nu;              // physical diffusion in f
     double nu_d;            // nu_d of nu_tilde = nu_d + dt_m/2 lam_max^2
+    double mu, kappa;       // Navier-Stokes viscosity and heat conductivity
+    double* FV;             // Navier-Stokes viscous flux scratch [6][N]: F_v^x, F_v^y of
+                            // the momentum and energy components
+    double* fout;           // SW_FEVAL output [NV]
     int mode, nsweeps, stages, M;
     double dt;
     double dtau[MMAX];

@@ -19,6 +19,7 @@ struct Pde;
 template <>
 struct Pde<0> {   // scalar convection-diffusion, F = a u
     static constexpr int NC = 1;
+    static constexpr bool VISC = false;
     template <class T> __device__ static void fx(const PdeParams& a, const T* u, T* f) { f[0] = T(a.ax) * u[0]; }
     template <class T> __device__ static void fy(const PdeParams& a, const T* u, T* f) { f[0] = T(a.ay) * u[0]; }
     template <class T> __device__ static T rx(const PdeParams& a, const T*) { return fabs(T(a.ax)); }
@@ -28,6 +29,7 @@ struct Pde<0> {   // scalar convection-diffusion, F = a u
 template <>
 struct Pde<1> {   // two-component Burgers, F = u (x) u
     static constexpr int NC = 2;
+    static constexpr bool VISC = false;
     template <class T> __device__ static void fx(const PdeParams&, const T* u, T* f) {
         f[0] = u[0] * u[0];
         f[1] = u[0] * u[1];
@@ -43,6 +45,7 @@ struct Pde<1> {   // two-component Burgers, F = u (x) u
 template <>
 struct Pde<2> {   // 2D compressible Euler, perfect gas
     static constexpr int NC = 4;
+    static constexpr bool VISC = false;
     template <class T> __device__ static T pres(const PdeParams& a, const T* u) {
         return (T(a.gamma) - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
     }
@@ -65,6 +68,35 @@ struct Pde<2> {   // 2D compressible Euler, perfect gas
     }
     template <class T> __device__ static T ry(const PdeParams& a, const T* u) {
         return fabs(u[2] / u[0]) + sqrt(T(a.gamma) * pres(a, u) / u[0]);
+    }
+};
+
+// 2D compressible Navier-Stokes: the Euler fluxes (convective part) plus a
+// viscous flux evaluated from the primitive variables w = (v_x, v_y, T),
+// T = p / rho, and their gradients (Sec. 2.2; gas constant 1).
+template <>
+struct Pde<3> : Pde<2> {
+    static constexpr bool VISC = true;
+    template <class T> __device__ static void primitive(const PdeParams& a, const T* u, T* w) {
+        const T ir = T(1) / u[0];
+        w[0] = u[1] * ir;
+        w[1] = u[2] * ir;
+        w[2] = Pde<2>::pres(a, u) * ir;
+    }
+    // momentum and energy components of F_v^x (fx) and F_v^y (fy); gx, gy =
+    // x and y derivatives of w; tau = mu (grad v + grad v^T - 2/3 div v I)
+    template <class T>
+    __device__ static void vflux(T mu, T kappa, const T* w, const T* gx, const T* gy, T* fx, T* fy) {
+        const T div = gx[0] + gy[1];
+        const T txx = mu * (T(2) * gx[0] - (T(2) / T(3)) * div);
+        const T tyy = mu * (T(2) * gy[1] - (T(2) / T(3)) * div);
+        const T txy = mu * (gy[0] + gx[1]);
+        fx[0] = txx;
+        fx[1] = txy;
+        fx[2] = w[0] * txx + w[1] * txy + kappa * gx[2];
+        fy[0] = txy;
+        fy[1] = tyy;
+        fy[2] = w[0] * txy + w[1] * tyy + kappa * gy[2];
     }
 };
 

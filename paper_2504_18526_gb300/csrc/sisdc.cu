@@ -43,6 +43,7 @@ struct sisdc_level_s {
     double *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *trx = nullptr, *trp = nullptr;
     double* cg_p2 = nullptr;    // second search-direction buffer of the sweep kernel
     double* cg_rf = nullptr;    // FP32 inner residual of the mixed-precision refinement
+    double* FV = nullptr;       // Navier-Stokes viscous fluxes [6][N]
     int sw_grid = 0, sw_epb = 0, sw_block = 0;
     double* lam = nullptr;      // [2][MMAX+1]: old, new spectral radius slots
     int pcg_grid = 0, pcg_block = 0;
@@ -108,8 +109,20 @@ sisdc_status fail(sisdc_ctx_s* c, sisdc_status st, const std::string& msg) {
     return st;
 }
 
-double nu_d(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER ? 0.0 : p.nu; }
-double nu_phys(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER ? 0.0 : p.nu; }
+// nu_d of nu_tilde = nu_d + dt_m/2 lam_max^2: the physical diffusivity for
+// convection-diffusion and Burgers, none for Euler, and for Navier-Stokes the
+// largest of the momentum and heat diffusivities 4/3 mu / rho and
+// gamma mu / (Pr rho) at the reference density
+double nu_d(const sisdc_problem& p) {
+    if (p.pde == SISDC_PDE_EULER) return 0.0;
+    if (p.pde == SISDC_PDE_NS) return std::max(4.0 / 3.0, p.gamma / p.Pr) * p.mu / p.rho_ref;
+    return p.nu;
+}
+// diffusivity of the nu L u term of f (the Navier-Stokes viscous term is separate)
+double nu_phys(const sisdc_problem& p) { return p.pde == SISDC_PDE_EULER || p.pde == SISDC_PDE_NS ? 0.0 : p.nu; }
+double kappa_ns(const sisdc_problem& p) {
+    return p.pde == SISDC_PDE_NS ? p.mu * p.gamma / ((p.gamma - 1.0) * p.Pr) : 0.0;
+}
 
 double* Um(sisdc_level_s* lv, double* U, int m) { return U + (long long)m * lv->NV; }
 
@@ -119,7 +132,7 @@ void k_conv(sisdc_level_s* lv, const double* u, double* out, double* lam, int mo
     sisdc_ctx_s* c = lv->ctx;
     ConvArgs a{};
     a.g = lv->geo;
-    a.pde = c->prob.pde;
+    a.pde = c->prob.pde == SISDC_PDE_NS ? SISDC_PDE_EULER : c->prob.pde;   // the NS convective flux is Euler's
     a.gamma = c->prob.gamma;
     a.ax = c->prob.adv[0];
     a.ay = c->prob.adv[1];
@@ -246,7 +259,7 @@ void k_transfer(sisdc_level_s* fine, int op, const double* in, double* out, int 
 // ---- method building blocks ----------------------------------------------------
 // One cooperative launch of the persistent sweep kernel (sweep.cuh).
 void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, const double* G, double dt,
-                      int nsweeps) {
+                      int nsweeps, double* fout = nullptr) {
     sisdc_ctx_s* c = lv->ctx;
     SweepArgs a{};
     a.g = lv->geo;
@@ -256,6 +269,10 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.ay = c->prob.adv[1];
     a.nu = nu_phys(c->prob);
     a.nu_d = nu_d(c->prob);
+    a.mu = c->prob.pde == SISDC_PDE_NS ? c->prob.mu : 0.0;
+    a.kappa = kappa_ns(c->prob);
+    a.FV = lv->FV;
+    a.fout = fout;
     a.mode = mode;
     a.nsweeps = nsweeps;
     a.stages = c->prob.si_stages;
@@ -459,12 +476,13 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (!prob || !out) return SISDC_E_ARG;
     *out = nullptr;
     const int nc_expect = prob->pde == SISDC_PDE_CONVDIFF ? 1 : prob->pde == SISDC_PDE_BURGERS ? 2
-                          : prob->pde == SISDC_PDE_EULER  ? 4 : -1;
+                          : (prob->pde == SISDC_PDE_EULER || prob->pde == SISDC_PDE_NS) ? 4 : -1;
     if (nc_expect < 0 || prob->ncomp != nc_expect) return SISDC_E_ARG;
     if (prob->si_stages != 1 && prob->si_stages != 2) return SISDC_E_ARG;
     if (prob->precision != SISDC_FP64 && prob->precision != SISDC_MIXED) return SISDC_E_ARG;
     if (!(prob->cg_rtol > 0.0) || prob->cg_maxit < 1 || prob->Nc < 0) return SISDC_E_ARG;
-    if (prob->pde == SISDC_PDE_EULER && !(prob->gamma > 1.0)) return SISDC_E_ARG;
+    if ((prob->pde == SISDC_PDE_EULER || prob->pde == SISDC_PDE_NS) && !(prob->gamma > 1.0)) return SISDC_E_ARG;
+    if (prob->pde == SISDC_PDE_NS && !(prob->mu > 0.0 && prob->Pr > 0.0 && prob->rho_ref > 0.0)) return SISDC_E_ARG;
     if (prob->nu < 0.0) return SISDC_E_ARG;
     sisdc_ctx_s* c = new sisdc_ctx_s();
     c->prob = *prob;
@@ -524,6 +542,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     *out = nullptr;
     if (d->dim != 1 && d->dim != 2) return fail(c, SISDC_E_ARG, "dim must be 1 or 2");
     if (d->dim == 1 && c->prob.pde != SISDC_PDE_CONVDIFF) return fail(c, SISDC_E_ARG, "1D supports convection-diffusion only");
+    if ((long long)d->nel[0] * (d->dim == 2 ? d->nel[1] : 1) > (1LL << 30)) return fail(c, SISDC_E_ARG, "too many elements");
     if (d->P < 1 || d->P > 8) return fail(c, SISDC_E_ARG, "P must be in 1..8");
     if (d->M < 1 || d->M > MMAX) return fail(c, SISDC_E_ARG, "M must be in 1..8");
     if (d->nodes != SISDC_RADAU_RIGHT && d->nodes != SISDC_LOBATTO) return fail(c, SISDC_E_ARG, "bad node kind");
@@ -602,7 +621,8 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     // work arrays
     const long long NV = lv->NV, MV = (long long)lv->M * NV;
     const long long ntr = (long long)c->prob.ncomp * lv->nel * 2 * d->dim * 2 * nq;
-    const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1);
+    const long long nfv = c->prob.pde == SISDC_PDE_NS ? 6 * lv->N : 0;
+    const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1) + nfv;
     if (e == cudaSuccess) e = cudaMalloc(&lv->d_mem, total * sizeof(double));
     if (e != cudaSuccess) {
         cudaFree(lv->d_tab);
@@ -621,6 +641,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     lv->cg_p = take(NV); lv->cg_Ap = take(NV); lv->cg_p2 = take(NV); lv->cg_rf = take(NV);
     lv->trx = take(ntr); lv->trp = take(ntr);
     lv->lam = take(2 * (MMAX + 1));
+    lv->FV = nfv ? take(nfv) : nullptr;
     if (lv->index > 0) {
         double* t = lv->d_tab + htab.size();
         lv->d_Ix = t + off_Ix; lv->d_Px = t + off_Px; lv->d_Rx = t + off_Rx;
@@ -701,6 +722,19 @@ sisdc_status sisdc_apply_conv(sisdc_level lv, const double* u, double* out) {
 sisdc_status sisdc_apply_lap(sisdc_level lv, const double* u, double* out) {
     if (!lv || !u || !out) return SISDC_E_ARG;
     SISDC_TRY(lv->ctx, k_lap(lv, u, out, APPLY_LAP));
+}
+
+sisdc_status sisdc_apply_f(sisdc_level lv, const double* u, double* out) {
+    if (!lv || !u || !out) return SISDC_E_ARG;
+    sisdc_ctx_s* c = lv->ctx;
+    try {
+        run_sweep_kernel(lv, SW_FEVAL, u, lv->U, nullptr, 1.0, 0, out);
+        lv->valid = false;
+        check(c, cudaGetLastError(), "f evaluation");
+    } catch (const Fail& f) {
+        return f.st;
+    }
+    return SISDC_OK;
 }
 
 sisdc_status sisdc_solve(sisdc_level lv, double cval, const double* rhs, double* x, int* iters) {

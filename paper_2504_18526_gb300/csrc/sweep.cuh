@@ -592,10 +592,14 @@ struct Sweeper {
     // c(X) for the block's elements into out (CT); mode CONV_DELTA also
     // writes dC = c - out_old; f64 (optional) receives c in FP64 (the start of
     // the cached f); optional spectral-radius partial into lamslot.
+    // Navier-Stokes with f64 given: also the BR1 lifted gradients of the
+    // primitive variables w = (v_x, v_y, T) (central traces {w}) and the
+    // viscous flux from them, into a.FV; its divergence is added to f by lap().
     template <class V>
     __device__ void conv(const double* X, int mode, CT* out, double* f64, double* lamslot) {
         V* sFv = std::is_same<V, double>::value ? reinterpret_cast<V*>(sF64) : reinterpret_cast<V*>(sFR);
         const V* Dv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sD) : reinterpret_cast<const V*>(rD);
+        const bool visc = PD::VISC && f64 != nullptr;
         double lmax = 0.0;
         tiles([&](const long long e0, const int nle) {
             const bool act = le < nle;
@@ -603,9 +607,18 @@ struct Sweeper {
             V u[NC], Fx[NC], Fy[NC];
             V* sFx = sFv + (size_t)le * 2 * NC * Q;
             V* sFy = sFx + NC * Q;
+            V w[3], gx[3], gy[3];
+            V* sW = reinterpret_cast<V*>(su) + (size_t)le * NC * Q;    // primitive values (tile buffer is free here)
             if (act) {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) u[cc] = (V)__ldcg(X + vidx(cc, e));
+                if constexpr (PD::VISC) {
+                    if (visc) {
+                        PD::primitive(pp, u, w);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) sW[k * Q + node] = w[k];
+                    }
+                }
                 PD::fx(pp, u, Fx);
                 lmax = fmax(lmax, (double)PD::rx(pp, u));
 #pragma unroll
@@ -636,6 +649,31 @@ struct Sweeper {
                         cv[cc] -= V(g.sy) * s;
                     }
                 }
+                if constexpr (PD::VISC) {
+                    if (visc) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            V s = V(0), t = V(0);
+#pragma unroll
+                            for (int k = 0; k < NQ; ++k) {
+                                s += Dv[i * NQ + k] * sW[q * Q + j * NQ + k];
+                                t += Dv[j * NQ + k] * sW[q * Q + k * NQ + i];
+                            }
+                            gx[q] = V(g.sx) * s;
+                            gy[q] = V(g.sy) * t;
+                        }
+                    }
+                }
+                // BR1 face correction of the gradient: +- lift ({w} - w) at the
+                // end nodes, from the neighbour's trace value at the same face node
+                auto lift_w = [&](const V* un_, V* gd, V lift) {
+                    if constexpr (PD::VISC) {
+                        V wn[3];
+                        PD::primitive(pp, un_, wn);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) gd[q] += lift * (V(0.5) * (w[q] + wn[q]) - w[q]);
+                    }
+                };
                 V un[NC], Fs[NC];
                 if (i == NQ - 1) {
                     const long long en = neighbour(e, 1);
@@ -644,6 +682,7 @@ struct Sweeper {
                     rusanov<PDE, true>(pp, u, un, Fs);
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(g.liftRx) * (Fs[cc] - Fx[cc]);
+                    if (visc) lift_w(un, gx, V(g.liftRx));
                 }
                 if (i == 0) {
                     const long long en = neighbour(e, 0);
@@ -652,6 +691,7 @@ struct Sweeper {
                     rusanov<PDE, true>(pp, un, u, Fs);
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) cv[cc] += V(g.liftLx) * (Fs[cc] - Fx[cc]);
+                    if (visc) lift_w(un, gx, -V(g.liftLx));
                 }
                 if (DIM == 2) {
                     if (j == NQ - 1) {
@@ -661,6 +701,7 @@ struct Sweeper {
                         rusanov<PDE, false>(pp, u, un, Fs);
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(g.liftRy) * (Fs[cc] - Fy[cc]);
+                        if (visc) lift_w(un, gy, V(g.liftRy));
                     }
                     if (j == 0) {
                         const long long en = neighbour(e, 2);
@@ -669,6 +710,19 @@ struct Sweeper {
                         rusanov<PDE, false>(pp, un, u, Fs);
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) cv[cc] += V(g.liftLy) * (Fs[cc] - Fy[cc]);
+                        if (visc) lift_w(un, gy, -V(g.liftLy));
+                    }
+                }
+                if constexpr (PD::VISC) {
+                    if (visc) {
+                        V fx[3], fy[3];
+                        PD::vflux(V(a.mu), V(a.kappa), w, gx, gy, fx, fy);
+                        const long long id0 = e * Q + node;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            a.FV[q * N + id0] = (double)fx[q];
+                            a.FV[(3 + q) * N + id0] = (double)fy[q];
+                        }
                     }
                 }
 #pragma unroll
@@ -697,9 +751,13 @@ struct Sweeper {
         tiles([&](const long long e0, const int nle) {
             const bool act = le < nle;
             const long long e = e0 + le;
+            double* sV = sF64 + (size_t)le * 6 * Q;     // own viscous fluxes (Navier-Stokes)
             if (act) {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) tu[(le * NC + cc) * Q + node] = (V)__ldcg(X + vidx(cc, e));
+                if constexpr (PD::VISC)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) sV[q * Q + node] = __ldcg(a.FV + q * N + e * Q + node);
             }
             __syncthreads();
             faces<V>(nle, e0, tu, tf, Dv, [&](int cc, long long en, int nd) { return (V)__ldcg(X + cc * N + en * Q + nd); });
@@ -711,6 +769,39 @@ struct Sweeper {
                     const V lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) / massv;
                     LUm[id] = (CT)lu;
                     Fm[id] = __ldcg(Fm + id) + a.nu * (double)lu;
+                }
+                if constexpr (PD::VISC) {
+                    // div F_v with central face fluxes: (2/h) D F_v plus
+                    // +- lift ({F_v} - F_v) at the end nodes (BR1)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        double s = 0.0, t = 0.0;
+#pragma unroll
+                        for (int k = 0; k < NQ; ++k) {
+                            s += sD[i * NQ + k] * sV[q * Q + j * NQ + k];
+                            t += sD[j * NQ + k] * sV[(3 + q) * Q + k * NQ + i];
+                        }
+                        double dx = g.sx * s, dy = g.sy * t;
+                        const double fx = sV[q * Q + node], fy = sV[(3 + q) * Q + node];
+                        if (i == NQ - 1) {
+                            const double nb = __ldcg(a.FV + q * N + neighbour(e, 1) * Q + j * NQ);
+                            dx += g.liftRx * (0.5 * (fx + nb) - fx);
+                        }
+                        if (i == 0) {
+                            const double nb = __ldcg(a.FV + q * N + neighbour(e, 0) * Q + j * NQ + NQ - 1);
+                            dx += -g.liftLx * (0.5 * (fx + nb) - fx);
+                        }
+                        if (j == NQ - 1) {
+                            const double nb = __ldcg(a.FV + (3 + q) * N + neighbour(e, 3) * Q + i);
+                            dy += g.liftRy * (0.5 * (fy + nb) - fy);
+                        }
+                        if (j == 0) {
+                            const double nb = __ldcg(a.FV + (3 + q) * N + neighbour(e, 2) * Q + (NQ - 1) * NQ + i);
+                            dy += -g.liftLy * (0.5 * (fy + nb) - fy);
+                        }
+                        const long long id = vidx(1 + q, e);
+                        Fm[id] = __ldcg(Fm + id) + (dx + dy);
+                    }
                 }
             }
             __syncthreads();
@@ -767,11 +858,25 @@ struct Sweeper {
     __device__ CT* Cm(void* A, int m) const { return C(A) + (long long)m * NV; }
 
     // ---- the three modes ------------------------------------------------------
+    // Navier-Stokes: the viscous divergence of lap() reads the neighbours'
+    // viscous fluxes of the preceding conv(), and the next conv() overwrites
+    // them: both need a grid barrier.
+    __device__ bool visc_bar() { return PD::VISC ? bar() : true; }
+
+    __device__ bool feval() {
+        conv<double>(a.u0, CONV_OUT, C(a.tmpc), a.fout, nullptr);
+        if (!visc_bar()) return false;
+        lap<double>(a.u0, C(a.dC), a.fout);
+        return true;
+    }
+
     __device__ bool refresh() {
         conv<double>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
         for (int m = 0; m < a.M; ++m) {
             conv<double>(Um(a.U, m), CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+            if (!visc_bar()) return false;
             lap<double>(Um(a.U, m), Cm(a.LU, m), Um(a.F, m));
+            if (!visc_bar()) return false;
         }
         if (!bar()) return false;
         for (int m = 0; m <= a.M; ++m) {
@@ -813,6 +918,7 @@ struct Sweeper {
                 if (!bar()) return false;
             }
             conv<double>(um, CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+            if (!visc_bar()) return false;
             lap<double>(um, Cm(a.LU, m), Um(a.F, m));
             if (!bar()) return false;
             lam = total_max(a.partmax + (size_t)(m + 1) * G);
@@ -857,6 +963,7 @@ struct Sweeper {
                     }
                 }
                 conv<double>(um, CONV_DELTA, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+                if (!visc_bar()) return false;
                 lap<double>(um, Cm(a.LU, m), Um(a.F, m));
                 if (!bar()) return false;
                 lam = total_max(a.partmax + (size_t)(m + 1) * G);
@@ -885,6 +992,10 @@ template <int NQ, int DIM, int PDE, bool MIX>
 __global__ void __launch_bounds__(512, 1) k_sweep(const __grid_constant__ SweepArgs a) {
     Sweeper<NQ, DIM, PDE, MIX> s(a);
     bool ok;
+    if (a.mode == SW_FEVAL) {
+        s.feval();
+        return;
+    }
     if (a.mode == SW_REFRESH) ok = s.refresh();
     else if (a.mode == SW_PREDICT) ok = s.predict();
     else ok = s.correct();

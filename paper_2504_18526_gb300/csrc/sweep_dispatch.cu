@@ -28,6 +28,15 @@ cudaError_t sweep_launch_pde2_lo_1(const SweepArgs& a, int grid, int block);
 int sweep_config_pde2_hi_1(const Geo& g, int* epb, int* block);
 cudaError_t sweep_launch_pde2_hi_1(const SweepArgs& a, int grid, int block);
 
+int sweep_config_pde3_lo_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde3_lo_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde3_hi_0(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde3_hi_0(const SweepArgs& a, int grid, int block);
+int sweep_config_pde3_lo_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde3_lo_1(const SweepArgs& a, int grid, int block);
+int sweep_config_pde3_hi_1(const Geo& g, int* epb, int* block);
+cudaError_t sweep_launch_pde3_hi_1(const SweepArgs& a, int grid, int block);
+
 int sweep_config(const Geo& g, int pde, int mix, int* epb, int* block) {
     const bool lo = g.nq < 6;
     mix = mix ? 1 : 0;
@@ -37,6 +46,8 @@ int sweep_config(const Geo& g, int pde, int mix, int* epb, int* block) {
     if (pde == 1 && mix == 1) return lo ? sweep_config_pde1_lo_1(g, epb, block) : sweep_config_pde1_hi_1(g, epb, block);
     if (pde == 2 && mix == 0) return lo ? sweep_config_pde2_lo_0(g, epb, block) : sweep_config_pde2_hi_0(g, epb, block);
     if (pde == 2 && mix == 1) return lo ? sweep_config_pde2_lo_1(g, epb, block) : sweep_config_pde2_hi_1(g, epb, block);
+    if (pde == 3 && mix == 0) return lo ? sweep_config_pde3_lo_0(g, epb, block) : sweep_config_pde3_hi_0(g, epb, block);
+    if (pde == 3 && mix == 1) return lo ? sweep_config_pde3_lo_1(g, epb, block) : sweep_config_pde3_hi_1(g, epb, block);
     return 0;
 }
 
@@ -49,6 +60,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int block) {
     if (a.pde == 1 && mix == 1) return lo ? sweep_launch_pde1_lo_1(a, grid, block) : sweep_launch_pde1_hi_1(a, grid, block);
     if (a.pde == 2 && mix == 0) return lo ? sweep_launch_pde2_lo_0(a, grid, block) : sweep_launch_pde2_hi_0(a, grid, block);
     if (a.pde == 2 && mix == 1) return lo ? sweep_launch_pde2_lo_1(a, grid, block) : sweep_launch_pde2_hi_1(a, grid, block);
+    if (a.pde == 3 && mix == 0) return lo ? sweep_launch_pde3_lo_0(a, grid, block) : sweep_launch_pde3_hi_0(a, grid, block);
+    if (a.pde == 3 && mix == 1) return lo ? sweep_launch_pde3_lo_1(a, grid, block) : sweep_launch_pde3_hi_1(a, grid, block);
     return cudaErrorInvalidValue;
 }
 

@@ -1,0 +1,22 @@
+// Instantiations of the persistent sweep kernel (PDE 3 (Navier-Stokes), NQ 2..5, mixed precision).
+#include "sweep.cuh"
+
+namespace sisdc {
+
+int sweep_config_pde3_lo_1(const Geo& g, int* epb, int* block) {
+    switch (g.nq * 10 + g.dim) {
+        case 42: return sweep_config_impl<4, 2, 3, true>(g, epb, block);
+        case 52: return sweep_config_impl<5, 2, 3, true>(g, epb, block);
+        default: return 0;
+    }
+}
+
+cudaError_t sweep_launch_pde3_lo_1(const SweepArgs& a, int grid, int block) {
+    switch (a.g.nq * 10 + a.g.dim) {
+        case 42: return sweep_launch_impl<4, 2, 3, true>(a, grid, block);
+        case 52: return sweep_launch_impl<5, 2, 3, true>(a, grid, block);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sisdc

@@ -19,7 +19,7 @@ SISDC_E_TIMEOUT, SISDC_E_NONFINITE, SISDC_E_OOM, SISDC_E_STATE = -4, -5, -6, -7
 STATUS_NAMES = {0: "SISDC_OK", -1: "SISDC_E_ARG", -2: "SISDC_E_CUDA", -3: "SISDC_E_NOCONV",
                 -4: "SISDC_E_TIMEOUT", -5: "SISDC_E_NONFINITE", -6: "SISDC_E_OOM", -7: "SISDC_E_STATE"}
 SISDC_RADAU_RIGHT, SISDC_LOBATTO = 0, 1
-SISDC_PDE_CONVDIFF, SISDC_PDE_BURGERS, SISDC_PDE_EULER = 0, 1, 2
+SISDC_PDE_CONVDIFF, SISDC_PDE_BURGERS, SISDC_PDE_EULER, SISDC_PDE_NS = 0, 1, 2, 3
 SISDC_FP64, SISDC_MIXED = 0, 1
 SISDC_START_SPREAD, SISDC_START_PREDICTOR, SISDC_START_CASCADE, SISDC_START_FMG1 = 0, 1, 2, 3
 T_INTERP, T_PROJECT, T_RESTRICT, T_PROJECT_SPACE = 0, 1, 2, 3
@@ -33,7 +33,8 @@ class sisdc_level_desc(ctypes.Structure):
 class sisdc_problem(ctypes.Structure):
     _fields_ = [("pde", c_int), ("ncomp", c_int), ("nu", c_double), ("gamma", c_double),
                 ("adv", c_double * 2), ("precision", c_int), ("si_stages", c_int),
-                ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("use_graph", c_int)]
+                ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("use_graph", c_int),
+                ("mu", c_double), ("Pr", c_double), ("rho_ref", c_double)]
 
 
 class sisdc_stats(ctypes.Structure):
@@ -86,6 +87,7 @@ def load():
         "sisdc_level_tables": (c_int, [c_void_p] + [c_void_p] * 5),
         "sisdc_apply_conv": (c_int, [c_void_p, c_void_p, c_void_p]),
         "sisdc_apply_lap": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "sisdc_apply_f": (c_int, [c_void_p, c_void_p, c_void_p]),
         "sisdc_solve": (c_int, [c_void_p, c_double, c_void_p, c_void_p, P(c_int)]),
         "sisdc_predict": (c_int, [c_void_p, c_void_p, c_void_p, c_double]),
         "sisdc_sweep": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int]),
@@ -202,6 +204,10 @@ def sisdc_apply_conv(lv, u, c):
 
 def sisdc_apply_lap(lv, u, Lu):
     _check(load().sisdc_apply_lap(lv, _ptr(u), _ptr(Lu)), lv=lv)
+
+
+def sisdc_apply_f(lv, u, f):
+    _check(load().sisdc_apply_f(lv, _ptr(u), _ptr(f)), lv=lv)
 
 
 def sisdc_solve(lv, c, rhs, x, want_iters=False):
@@ -470,7 +476,8 @@ class Ensemble:
 
 
 # ---- construction from a workload description (marshalling) -------------------
-PDE_IDS = {"convdiff": SISDC_PDE_CONVDIFF, "burgers": SISDC_PDE_BURGERS, "euler": SISDC_PDE_EULER}
+PDE_IDS = {"convdiff": SISDC_PDE_CONVDIFF, "burgers": SISDC_PDE_BURGERS, "euler": SISDC_PDE_EULER,
+           "ns": SISDC_PDE_NS}
 NODE_IDS = {"radau_right": SISDC_RADAU_RIGHT, "lobatto": SISDC_LOBATTO}
 START_IDS = {"spread": SISDC_START_SPREAD, "predictor": SISDC_START_PREDICTOR,
              "cascade": SISDC_START_CASCADE, "fmg1": SISDC_START_FMG1}
@@ -491,6 +498,10 @@ def make_problem(w, precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12, cg_maxit=1
     p.cg_maxit = cg_maxit
     p.Nc = Nc
     p.use_graph = use_graph
+    if w["pde"] == "ns":
+        p.mu = 1.0 / w["Re"]
+        p.Pr = w["Pr"]
+        p.rho_ref = w.get("rho_ref", 1.0)
     return p
 
 

@@ -58,6 +58,9 @@ CASES = {
                   nodes="lobatto",
                   levels=[dict(nel=(4, 6), P=3, M=2), dict(nel=(4, 6), P=5, M=3),
                           dict(nel=(4, 6), P=7, M=5)]),
+    "ns": dict(pde="ns", dim=2, ncomp=4, gamma=1.4, Re=200.0, Pr=0.72, lo=(0.0, 0.0), hi=(1.0, 1.0),
+               nodes="radau_right",
+               levels=[dict(nel=(4, 5), P=3, M=3), dict(nel=(4, 5), P=5, M=5)]),
 }
 
 
@@ -108,6 +111,26 @@ def test_conv_and_lap_parity(dev, case):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", list(CASES))
+def test_apply_f_parity(dev, case):
+    """f(u): convective operator plus nu L u, or plus the BR1 viscous term."""
+    w = CASES[case]
+    ctx = make_ctx(w)
+    for li, lvl in enumerate(w["levels"]):
+        sp = oracle_space(w, lvl)
+        u = random_state(w, sp.shape, 20 + li)
+        du = T(u, dev)
+        out = torch.empty_like(du)
+        S.sisdc_apply_f(ctx.levels[li], du, out)
+        ref = OS.f_eval(sp, u)
+        assert rel_l2(N(out), ref) < 1e-13, (case, li, rel_l2(N(out), ref))
+        if w["pde"] == "ns":   # the viscous part alone, on its own scale
+            vis = N(out) - sp.conv(u)
+            assert np.linalg.norm((vis - sp.visc(u)).ravel()) < 1e-11 * np.linalg.norm(sp.visc(u).ravel())
+    S.sisdc_sync(ctx.ctx)
+    ctx.close()
+
+
 @pytest.mark.parametrize("P", range(1, 9))
 def test_lap_parity_all_degrees(dev, P):
     w = dict(pde="convdiff", dim=2, ncomp=1, adv=(1.0, 0.5), nu=0.01, lo=(0, 0), hi=(1.0, 0.7),
@@ -124,7 +147,7 @@ def test_lap_parity_all_degrees(dev, P):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["cd1d", "cd2d", "burgers", "euler"])
+@pytest.mark.parametrize("case", ["cd1d", "cd2d", "burgers", "euler", "ns"])
 def test_solve_parity(dev, case):
     w = CASES[case]
     ctx = make_ctx(w)
@@ -142,7 +165,7 @@ def test_solve_parity(dev, case):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["cd1d", "cd2d", "burgers", "euler"])
+@pytest.mark.parametrize("case", ["cd1d", "cd2d", "burgers", "euler", "ns"])
 @pytest.mark.parametrize("stages", [1, 2])
 def test_predict_sweep_residual_parity(dev, case, stages):
     w = CASES[case]
@@ -150,15 +173,15 @@ def test_predict_sweep_residual_parity(dev, case, stages):
     om = oracle_ml(w, stages=stages)
     lv = om.levels[-1]
     sp = lv.space
-    u0 = random_state(w, sp.shape, 11) if w["pde"] != "euler" else random_state(w, sp.shape, 11)
-    dt = 0.02 if w["pde"] != "euler" else 0.01
+    u0 = random_state(w, sp.shape, 11)
+    dt = 0.02 if w["pde"] not in ("euler", "ns") else 0.01
     U = OS.predictor(lv, u0, dt, stages)
     dU = torch.empty((lv.M,) + sp.shape, dtype=torch.float64, device=dev)
     du0 = T(u0, dev)
     S.sisdc_predict(ctx.levels[-1], du0, dU, dt)
     assert rel_l2(N(dU), U) < TOL
     g = 1e-3 * np.random.default_rng(5).standard_normal(U.shape)
-    if w["pde"] == "euler":
+    if w["pde"] in ("euler", "ns"):
         g *= 0.1
     U2 = OS.corrector(lv, u0, U, g, dt, stages, 2)
     dg = T(g, dev)
@@ -200,7 +223,7 @@ def test_transfer_parity(dev, case):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["cd1d", "burgers", "euler"])
+@pytest.mark.parametrize("case", ["cd1d", "burgers", "euler", "ns"])
 def test_vcycle_parity(dev, case):
     w = CASES[case]
     ctx = make_ctx(w)
@@ -211,6 +234,9 @@ def test_vcycle_parity(dev, case):
     if w["pde"] == "euler":
         u0 = inputs.isentropic_vortex(X, Y)
         dt = 0.05
+    elif w["pde"] == "ns":
+        u0 = inputs.shear_layer(X, Y, delta=0.1)
+        dt = 2e-3
     elif w["pde"] == "burgers":
         u0 = inputs.burgers2d_initial(X, Y)
         dt = 2e-3
@@ -273,6 +299,45 @@ def test_step_parity_euler_small(dev):
     dt = inputs.cfl_dt(0.5, 20.0 / 5, 7, inputs.max_wave_speed("euler", u0))
     worst, _ = _step_parity(w, u0, dt, 2, 2, "fmg1", dev)
     assert worst < TOL
+
+
+def test_step_parity_ns_small(dev):
+    """Shear-layer data (smoothed to the coarse grid) at Re = 200: two steps
+    of the two-level method with the BR1 viscous term, within 1e-12."""
+    w = dict(inputs.scaled("ns_shear", nel=(6, 5)), Re=200.0)
+    sp = oracle_space(w, w["levels"][-1])
+    X, Y = sp.coords()
+    u0 = inputs.shear_layer(X, Y, w["gamma"], w["mach"], delta=0.08)
+    dt = inputs.cfl_dt(0.5, 1.0 / 6, 5, inputs.max_wave_speed("ns", u0))
+    worst, _ = _step_parity(w, u0, dt, 2, 3, "cascade", dev)
+    assert worst < TOL
+
+
+def test_ns_shear_layer_full_size(dev):
+    """The Navier-Stokes shear layer at full size (128 x 128 elements, P = 5,
+    2.36 M unknowns), one graph-captured step per form: mass, momentum and
+    energy are conserved to the solver tolerance, and the mixed-precision
+    form agrees with the FP64 form."""
+    w = inputs.WORKLOADS["ns_shear"]
+    out = {}
+    for prec in (S.SISDC_FP64, S.SISDC_MIXED):
+        ctx = make_ctx(w, rtol=1e-13, maxit=2000, precision=prec, use_graph=1)
+        nc, n, M = ctx.info(-1)
+        hx, hy = np.zeros(n), np.zeros(n)
+        S.sisdc_level_coords(ctx.levels[-1], hx, hy)
+        u0 = inputs.initial_state("ns_shear", hx, hy)
+        dt = inputs.cfl_dt(w["cfl"], 1.0 / 128, 5, inputs.max_wave_speed("ns", u0))
+        du = T(u0, dev)
+        m0 = S.sisdc_norms(ctx.levels[-1], du)[1]
+        S.sisdc_step(ctx.ctx, du, 0.0, dt, w["ncycles"], S.START_IDS[w["start"]], 1)
+        S.sisdc_sync(ctx.ctx)
+        m1 = S.sisdc_norms(ctx.levels[-1], du)[1]
+        assert np.all(np.abs(m1 - m0) <= 1e-11 * (np.abs(m0) + 1.0)), (m0, m1)
+        u = N(du)
+        assert np.all(np.isfinite(u)) and np.max(np.abs(u - u0)) > 1e-6
+        out[prec] = u
+        ctx.close()
+    assert rel_l2(out[S.SISDC_MIXED], out[S.SISDC_FP64]) < 1e-10
 
 
 def test_device_error_flags(dev):
