@@ -113,30 +113,41 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Grid-wide barrier for cooperative launches with a bounded wait.
-// count/gen live in device memory (zero-initialised once).  On timeout the
-// block records DEV_TIMEOUT in *err and returns false; callers then leave
-// the kernel, so that every wait in the grid ends.
+// Grid-wide barrier for cooperative launches with a bounded wait, over a
+// monotonically increasing arrival counter: `count` is 0 when a launch starts
+// (grid_exit resets it), every barrier adds exactly gridDim.x arrivals, so the
+// k-th barrier's arrivals see old values in [(k-1) G, k G) and wait until the
+// counter reaches k G.  One release-add per block and acquire-load polling;
+// thread 0 waits for the block (bar.sync before and after, so the block's
+// writes are ordered before the release and the acquire before its reads).
+// On timeout the block records DEV_TIMEOUT in *err and returns false; callers
+// then leave the kernel, so that every wait in the grid ends.
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;   // 2 s
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* /*exits*/, int* err) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* vgen = gen;
-        const unsigned g = *vgen;
-        __threadfence();
         const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nb - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
+        const unsigned old = atom_add_release_gpu(count, 1u);
+        const unsigned target = (old / nb + 1u) * nb;
+        if (ld_acquire_gpu(count) < target) {
             const unsigned long long t0 = globaltimer_ns();
             unsigned spins = 0;
-            while (*vgen == g) {
+            while (ld_acquire_gpu(count) < target) {
                 if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
                     atomicOr(err, DEV_TIMEOUT);
                     ok = 0;
@@ -144,11 +155,24 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int
                 }
             }
         }
-        __threadfence();
         s_ok = ok && ((*(volatile int*)err & DEV_TIMEOUT) == 0);
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Every block of a launch that uses grid_barrier calls this once, at its end
+// (on every path): the last block out resets the arrival counter for the next
+// launch on the stream (all blocks have left every barrier by then).
+__device__ __forceinline__ void grid_exit(unsigned* count, unsigned* exits) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd(exits, 1u) == nb - 1u) {
+            atomicExch(count, 0u);
+            atomicExch(exits, 0u);
+        }
+    }
 }
 
 // Sum of gridDim.x partials in a fixed order; every block gets the same bits.

@@ -171,7 +171,7 @@ struct EnsSweeper {
 
     __device__ static int line_node(int f, int k, int q) { return f < 2 ? k * NQ + q : q * NQ + k; }
 
-    __device__ bool bar() { return grid_barrier(a.bar_count, a.bar_gen, a.err); }
+    __device__ bool bar() { return grid_barrier(a.bar_count, a.bar_exit, a.err); }
 
     // Loop over the block's tiles: fn(I, e0, nle, li, acc[K]) accumulates K
     // per-thread values; their block sums go to part[slot0 + k][inst][block].
@@ -789,6 +789,7 @@ __global__ void __launch_bounds__(512, 1) k_ens_sweep(const __grid_constant__ En
     if (a.mode == SW_REFRESH) s.refresh();
     else if (a.mode == SW_PREDICT) s.predict();
     else s.correct();
+    grid_exit(a.bar_count, a.bar_exit);
 }
 
 template <int NQ, bool MIX>

@@ -408,7 +408,7 @@ void run_sweep(sisdc_ens_s* c, EnsGroup& g, int which, int mode, const double* G
     a.r = c->cg_r; a.p = c->cg_p; a.p2 = c->cg_p2; a.Ap = c->cg_Ap; a.rf = c->cg_rf;
     a.part = c->part;
     a.bar_count = c->d_bar;
-    a.bar_gen = c->d_bar + 1;
+    a.bar_exit = c->d_bar + 1;
     a.err = c->d_err;
     a.stats = c->d_stats;
     a.rtol = c->opts.cg_rtol;

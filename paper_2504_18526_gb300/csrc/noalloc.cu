@@ -29,7 +29,7 @@ constexpr int kMaxDevices = 64;
 double* s_scratch[kMaxDevices] = {nullptr};   // device address of the array, per device
 
 // Header layout (in doubles) at the start of the scratch array.
-constexpr size_t H_BAR = 0;       // 2 unsigned (barrier count, generation)
+constexpr size_t H_BAR = 0;       // 2 unsigned (barrier arrival counter, exit counter)
 constexpr size_t H_ERR = 1;       // int error flag
 constexpr size_t H_ITERS = 2;     // int iteration count
 constexpr size_t H_STATS = 4;     // ST_N long long
@@ -149,7 +149,7 @@ extern "C" sisdc_status sisdc_solve_noalloc(const sisdc_level_desc* d, int ncomp
     a.cimp = Coef{c, 0.0, nullptr};
     a.part = part;
     a.bar_count = reinterpret_cast<unsigned*>(base + H_BAR);
-    a.bar_gen = a.bar_count + 1;
+    a.bar_exit = a.bar_count + 1;
     a.err = reinterpret_cast<int*>(base + H_ERR);
     a.stats = reinterpret_cast<long long*>(base + H_STATS);
     a.rtol = rtol;

@@ -34,7 +34,7 @@ struct PCGArgs {
     Coef cimp;            // system (M + c A) x = M b
     double* part;         // 4 * gridDim partial sums
     unsigned* bar_count;
-    unsigned* bar_gen;
+    unsigned* bar_exit;
     int* err;
     long long* stats;
     double rtol;
@@ -98,7 +98,7 @@ struct SweepArgs {
     double* part;           // 8 * grid partial sums
     double* partmax;        // (MMAX+1) * grid partial maxima
     unsigned* bar_count;
-    unsigned* bar_gen;
+    unsigned* bar_exit;
     int* err;
     long long* stats;
     double rtol;
@@ -200,7 +200,7 @@ struct EnsArgs {
     void *p, *p2, *Ap, *rf;
     double* part;           // (2 * 4 * ninst + 2) * grid partial sums
     unsigned* bar_count;
-    unsigned* bar_gen;
+    unsigned* bar_exit;
     int* err;
     long long* stats;
     double rtol;

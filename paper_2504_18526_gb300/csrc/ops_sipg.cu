@@ -220,7 +220,16 @@ __global__ void k_apply(const ApplyArgs a) {
 // Persistent cooperative Jacobi-PCG
 // ---------------------------------------------------------------------------
 template <int NQ, int DIM>
+__device__ __forceinline__ void pcg_body(const PCGArgs& a);
+
+template <int NQ, int DIM>
 __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs a) {
+    pcg_body<NQ, DIM>(a);
+    grid_exit(a.bar_count, a.bar_exit);
+}
+
+template <int NQ, int DIM>
+__device__ __forceinline__ void pcg_body(const PCGArgs& a) {
     using S = Sh<NQ, DIM>;
     extern __shared__ double sm[];
     double* sD = sm;
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs
         const double bs = block_sum(acc, scratch);
         if (threadIdx.x == 0) part[blockIdx.x] = bs;
     }
-    if (!grid_barrier(a.bar_count, a.bar_gen, a.err)) return;
+    if (!grid_barrier(a.bar_count, a.bar_exit, a.err)) return;
 
     // phase 1: r = M b - (M + cA) x, z = D^-1 r, p = z, traces of p
     acc = 0.0;
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs
         const double bs = block_sum(acc, scratch);
         if (threadIdx.x == 0) part[G + blockIdx.x] = bs;
     }
-    if (!grid_barrier(a.bar_count, a.bar_gen, a.err)) return;
+    if (!grid_barrier(a.bar_count, a.bar_exit, a.err)) return;
     const double bb = grid_total(part, scratch);
     double rz = grid_total(part + G, scratch);
     const double tol2 = fmax(a.rtol * a.rtol * bb, 1e-300);
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs
             const double bs = block_sum(acc, scratch);
             if (threadIdx.x == 0) part[2 * G + blockIdx.x] = bs;
         }
-        if (!grid_barrier(a.bar_count, a.bar_gen, a.err)) return;
+        if (!grid_barrier(a.bar_count, a.bar_exit, a.err)) return;
         const double alpha = rz / grid_total(part + 2 * G, scratch);
 
         // phase 3: x += alpha p, r -= alpha Ap, partial r^T z
@@ -355,7 +364,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs
             const double bs = block_sum(acc, scratch);
             if (threadIdx.x == 0) part[3 * G + blockIdx.x] = bs;
         }
-        if (!grid_barrier(a.bar_count, a.bar_gen, a.err)) return;
+        if (!grid_barrier(a.bar_count, a.bar_exit, a.err)) return;
         const double rzn = grid_total(part + 3 * G, scratch);
         const double beta = rzn / rz;
         rz = rzn;
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(const __grid_constant__ PCGArgs
             tile_traces<NQ, DIM>(su, nle, ec0, g, sD, a.trp);
             __syncthreads();
         }
-        if (!grid_barrier(a.bar_count, a.bar_gen, a.err)) return;
+        if (!grid_barrier(a.bar_count, a.bar_exit, a.err)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (a.iters_out) *a.iters_out = it;

@@ -193,7 +193,7 @@ void k_pcg(sisdc_level_s* lv, double* x, const Terms& t, Coef cimp) {
     a.cimp = cimp;
     a.part = c->d_part;
     a.bar_count = c->d_bar;
-    a.bar_gen = c->d_bar + 1;
+    a.bar_exit = c->d_bar + 1;
     a.err = c->d_err;
     a.stats = c->d_stats;
     a.rtol = c->prob.cg_rtol;
@@ -291,7 +291,7 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.part = c->d_part;
     a.partmax = c->d_part + 8 * (size_t)c->max_grid;
     a.bar_count = c->d_bar;
-    a.bar_gen = c->d_bar + 1;
+    a.bar_exit = c->d_bar + 1;
     a.err = c->d_err;
     a.stats = c->d_stats;
     a.rtol = c->prob.cg_rtol;

@@ -170,7 +170,7 @@ struct Sweeper {
         }
     }
 
-    __device__ bool bar() { return grid_barrier(a.bar_count, a.bar_gen, a.err); }
+    __device__ bool bar() { return grid_barrier(a.bar_count, a.bar_exit, a.err); }
 
     __device__ void put_partial(double* slot, double v) {
         const double s = block_sum(v, scratch);
@@ -994,12 +994,13 @@ __global__ void __launch_bounds__(512, 1) k_sweep(const __grid_constant__ SweepA
     bool ok;
     if (a.mode == SW_FEVAL) {
         s.feval();
-        return;
+    } else {
+        if (a.mode == SW_REFRESH) ok = s.refresh();
+        else if (a.mode == SW_PREDICT) ok = s.predict();
+        else ok = s.correct();
+        if (ok) s.finish();
     }
-    if (a.mode == SW_REFRESH) ok = s.refresh();
-    else if (a.mode == SW_PREDICT) ok = s.predict();
-    else ok = s.correct();
-    if (ok) s.finish();
+    grid_exit(a.bar_count, a.bar_exit);
 }
 
 template <int NQ, int DIM, int PDE, bool MIX>
