@@ -261,6 +261,11 @@ def sweep_flops(P, ncomp, M, nsweeps, iters, nv):
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 
+# DRAM bytes (read + write) of one fine-level correction-sweep launch of the
+# burgers2d workload (FP64 form), from the ncu capture summarised in
+# profiles/k_sweep_burgers2d_fp64.md; None for other workloads or forms.
+SWEEP_TRAFFIC_BYTES = {("burgers2d", "fp64"): 22.431488e6 + 16.843264e6}
+
 
 def make_ctx(S, w, stream, prec, rtol, use_graph):
     return S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=rtol, cg_maxit=1000,
@@ -450,7 +455,9 @@ def main_arm(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "k_sweep correction launches, fine level",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None if args.small else SWEEP_TRAFFIC_BYTES.get((args.workload, args.precision)),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
                      "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20)",
                      "avg_launch_us": avg_ms * 1e3, "launches": kt["launches"],
                      "cg_iters_per_launch": kt["iters"] / max(1, kt["launches"]),
