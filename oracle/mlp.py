@@ -1,7 +1,7 @@
 """FP64 reference of the element-patch MLP (test infrastructure only).
 
-The learned part of the implicit stage (not in the paper; a north-star
-addition): for every element and component, the 3x3 element patch of a
+The learned part of the implicit stage (not in the paper; an addition that
+leaves the method unchanged): for every element and component, the 3x3 element patch of a
 residual field r (9 Q nodal values, ordered by neighbour offset (dy, dx) in
 {-1, 0, 1}^2 row-major, each element's nodes in the state layout) is scaled
 by its RMS s, a scalar feature 0.1 log(c / h^2) is appended, and a 3-layer

@@ -74,7 +74,7 @@ def load():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libsisdc.so is not built (run __graft_entry__.build()); "
+        raise RuntimeError("libsisdc.so is not built (run paper_2504_18526_gb300/build.py); "
                            "there is no fallback path")
     lib = ctypes.CDLL(LIB_PATH)
     P = ctypes.POINTER
