@@ -83,14 +83,24 @@ def test_mlp_loss_and_gradient_parity(dev, use_bf16):
     ctx.close()
 
 
-def test_learned_initial_guess_saves_iterations(dev):
-    # Burgers at CFL 4 so that the implicit solves need several CG iterations
-    w = inputs.scaled("burgers2d", nel=(8, 8))
-    lvl = w["levels"][-1]
-    sp = oracle_space(w, lvl)
-    X, Y = sp.coords()
-    u0 = inputs.burgers2d_initial(X, Y)
-    dt = inputs.cfl_dt(4.0, 1.0 / 8, 7, inputs.max_wave_speed("burgers", u0))
+def _workload(name):
+    """A small case of a workload at CFL 4, so that the implicit solves need
+    several CG iterations: (workload, initial state, dt)."""
+    if name == "burgers":
+        w = inputs.scaled("burgers2d", nel=(8, 8))
+        X, Y = oracle_space(w, w["levels"][-1]).coords()
+        u0 = inputs.burgers2d_initial(X, Y)
+    else:   # Navier-Stokes shear layer, smoothed to the coarse grid, Re = 200
+        w = dict(inputs.scaled("ns_shear", nel=(8, 8)), Re=200.0)
+        X, Y = oracle_space(w, w["levels"][-1]).coords()
+        u0 = inputs.shear_layer(X, Y, w["gamma"], w["mach"], delta=0.06)
+    P = w["levels"][-1]["P"]
+    return w, u0, inputs.cfl_dt(4.0, 1.0 / 8, P, inputs.max_wave_speed(w["pde"], u0))
+
+
+@pytest.mark.parametrize("name", ["burgers", "ns"])
+def test_learned_initial_guess_saves_iterations(dev, name):
+    w, u0, dt = _workload(name)
     ctx = S.Context(w, cg_rtol=1e-10, cg_maxit=2000)
     fine = len(w["levels"]) - 1
     nc, n, M = ctx.info(fine)
@@ -134,8 +144,8 @@ def test_learned_initial_guess_saves_iterations(dev):
         torch.cuda.synchronize()
         assert float(torch.linalg.vector_norm(x3 - x) / torch.linalg.vector_norm(x)) < 1e-8
     S.sisdc_sync(ctx.ctx)
-    print("held-out solves %d: plain PCG %d iterations, learned guess + PCG %d, learned flexible CG %d"
-          % (len(test), plain, learned, flexible))
+    print("%s held-out solves %d: plain PCG %d iterations, learned guess + PCG %d, learned flexible CG %d"
+          % (name, len(test), plain, learned, flexible))
     assert learned < plain
     S.sisdc_mlp_destroy(m)
     S.sisdc_set_solve_log(ctx.ctx, fine)
