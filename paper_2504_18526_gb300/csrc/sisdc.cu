@@ -44,7 +44,6 @@ struct sisdc_level_s {
     double* cg_p2 = nullptr;    // second search-direction buffer of the sweep kernel
     double* cg_rf = nullptr;    // FP32 inner residual of the mixed-precision refinement
     double* FV = nullptr;       // Navier-Stokes viscous fluxes [6][N]
-    double *cg_s2 = nullptr, *cg_w2 = nullptr;   // second s, w buffers of the FP64 sweep solve
     int sw_grid = 0, sw_epb = 0, sw_block = 0;
     double* lam = nullptr;      // [2][MMAX+1]: old, new spectral radius slots
     int pcg_grid = 0, pcg_block = 0;
@@ -288,7 +287,6 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.F = lv->F; a.CC = lv->CC; a.LU = lv->LU; a.Qb = lv->Qb;
     a.c0 = lv->c0; a.dC = lv->dC; a.tmpc = lv->tmpc;
     a.r = lv->cg_r; a.p = lv->cg_p; a.p2 = lv->cg_p2; a.Ap = lv->cg_Ap; a.rf = lv->cg_rf;
-    a.s2 = lv->cg_s2; a.w2 = lv->cg_w2;
     a.lam = lv->lam;
     a.part = c->d_part;
     a.partmax = c->d_part + 8 * (size_t)c->max_grid;
@@ -624,7 +622,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     const long long NV = lv->NV, MV = (long long)lv->M * NV;
     const long long ntr = (long long)c->prob.ncomp * lv->nel * 2 * d->dim * 2 * nq;
     const long long nfv = c->prob.pde == SISDC_PDE_NS ? 6 * lv->N : 0;
-    const long long total = 8 * MV + 2 * NV + 3 * NV + 6 * NV + 2 * ntr + 2 * (MMAX + 1) + nfv;
+    const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1) + nfv;
     if (e == cudaSuccess) e = cudaMalloc(&lv->d_mem, total * sizeof(double));
     if (e != cudaSuccess) {
         cudaFree(lv->d_tab);
@@ -641,7 +639,6 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     lv->u0 = take(NV); lv->c0 = take(NV);
     lv->dC = take(NV); lv->tmpc = take(NV); lv->cg_r = take(NV);
     lv->cg_p = take(NV); lv->cg_Ap = take(NV); lv->cg_p2 = take(NV); lv->cg_rf = take(NV);
-    lv->cg_s2 = take(NV); lv->cg_w2 = take(NV);
     lv->trx = take(ntr); lv->trp = take(ntr);
     lv->lam = take(2 * (MMAX + 1));
     lv->FV = nfv ? take(nfv) : nullptr;

@@ -254,9 +254,6 @@ struct Sweeper {
     __device__ double opA64(int l, int c) const { return opA<double>(l, c, su, sf, sD, sK, sw); }
     __device__ RT opAR(int l, int c) const { return opA<RT>(l, c, ru, rf, rD, rK, rw); }
 
-    // s = w + beta s_old of the single-reduction PCG (shared by owner and neighbours)
-    __device__ static double snew(double w, double beta, double sold) { return beta == 0.0 ? w : w + beta * sold; }
-
     // new search direction at one node (shared by owner and neighbours)
     template <class V>
     __device__ static V pnew(V r, V dinv, V beta, V pold) {
@@ -351,109 +348,69 @@ struct Sweeper {
         double rz = total(part + G);
         const double tol2 = fmax(a.rtol * a.rtol * bb, 1e-300);
         bool fin = isfinite(rz) && isfinite(bb);
-        int it = 0;
-        // Single-reduction PCG (Chronopoulos and Gear): with z = D^-1 r,
-        // w = (M + cA) z, s = (M + cA) p, one phase per iteration updates
-        // p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, forms the new
-        // z and w and both inner products (r, z), (z, w); then
-        // alpha = (r, z) / ((z, w) - beta (r, z) / alpha_prev).  r, s and w are
-        // double-buffered: a block forms a neighbour's new z on its face lines
-        // from the neighbour's r, w and s of the previous phase.
-        double* Rb[2] = {a.r, static_cast<double*>(a.rf)};
-        double* Sb[2] = {static_cast<double*>(a.p2), a.s2};
-        double* Wb[2] = {static_cast<double*>(a.Ap), a.w2};
-        double* Pv = static_cast<double*>(a.p);
-        double delta = 0.0;
-        if (fin && rz > tol2 && a.maxit > 0) {
-            // z0 = D^-1 r0 and w0 = (M + c A) z0 (neighbour z0 from the final r0)
+        int it = 0, par = 0;
+        double beta = 0.0;
+        double* P0 = static_cast<double*>(a.p);
+        double* P1 = static_cast<double*>(a.p2);
+        double* AP = static_cast<double*>(a.Ap);
+        while (fin && rz > tol2 && it < a.maxit) {
+            const double* pold = par ? P1 : P0;
+            double* pcur = par ? P0 : P1;
             acc = 0.0;
             tiles([&](const long long e0, const int nle) {
                 const bool act = le < nle;
                 const long long e = e0 + le;
-                double zz[NC];
+                double pn[NC];
                 if (act) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        zz[cc] = __ldcg(Rb[0] + vidx(cc, e)) * dinv;
-                        su[(le * NC + cc) * Q + node] = zz[cc];
+                        const long long id = vidx(cc, e);
+                        pn[cc] = pnew<double>(__ldcg(a.r + id), dinv, beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
+                        pcur[id] = pn[cc];
+                        su[(le * NC + cc) * Q + node] = pn[cc];
                     }
                 }
                 __syncthreads();
                 faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) {
-                    return __ldcg(Rb[0] + cc * N + en * Q + nd) * sdinv[nd];
+                    const long long id = cc * N + en * Q + nd;
+                    return pnew<double>(__ldcg(a.r + id), sdinv[nd], beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
                 });
                 __syncthreads();
                 if (act) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        const double wv = mass * zz[cc] + c * opA64(le, cc);
-                        Wb[0][vidx(cc, e)] = wv;
-                        acc += zz[cc] * wv;
+                        const double Apv = mass * pn[cc] + c * opA64(le, cc);
+                        AP[vidx(cc, e)] = Apv;
+                        acc += pn[cc] * Apv;
                     }
                 }
                 __syncthreads();
             });
             put_partial(part + 2 * G, acc);
             if (!bar()) return false;
-            delta = total(part + 2 * G);
-            fin = isfinite(delta);
-        }
-        double alpha = 0.0, beta = 0.0;
-        int cb = 0;
-        while (fin && rz > tol2 && it < a.maxit) {
-            alpha = it == 0 ? rz / delta : rz / (delta - beta * rz / alpha);
-            const double *Rc = Rb[cb], *Wc = Wb[cb], *Sc = Sb[cb];
-            double *Rn = Rb[cb ^ 1], *Wn = Wb[cb ^ 1], *Sn = Sb[cb ^ 1];
-            double* ps = part + (size_t)(3 + 2 * (it & 1)) * G;   // alternating partial slots
-            double acc_g = 0.0, acc_d = 0.0;
+            const double alpha = rz / total(part + 2 * G);
+            acc = 0.0;
             tiles([&](const long long e0, const int nle) {
-                const bool act = le < nle;
-                const long long e = e0 + le;
-                double zn[NC], rn[NC];
-                if (act) {
+                if (le < nle) {
+                    const long long e = e0 + le;
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
                         const long long id = vidx(cc, e);
-                        const double r = __ldcg(Rc + id), w = __ldcg(Wc + id);
-                        const double sv = snew(w, beta, beta == 0.0 ? 0.0 : __ldcg(Sc + id));
-                        const double pv = pnew<double>(r, dinv, beta, beta == 0.0 ? 0.0 : __ldcg(Pv + id));
-                        x[id] = __ldcg(x + id) + alpha * pv;
-                        rn[cc] = r - alpha * sv;
-                        zn[cc] = rn[cc] * dinv;
-                        Pv[id] = pv;
-                        Sn[id] = sv;
-                        Rn[id] = rn[cc];
-                        su[(le * NC + cc) * Q + node] = zn[cc];
-                        acc_g += rn[cc] * zn[cc];
+                        x[id] = __ldcg(x + id) + alpha * __ldcg(pcur + id);
+                        const double rr = __ldcg(a.r + id) - alpha * __ldcg(AP + id);
+                        a.r[id] = rr;
+                        acc += rr * (rr * dinv);
                     }
                 }
-                __syncthreads();
-                faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) {
-                    const long long id = cc * N + en * Q + nd;
-                    const double sv = snew(__ldcg(Wc + id), beta, beta == 0.0 ? 0.0 : __ldcg(Sc + id));
-                    return (__ldcg(Rc + id) - alpha * sv) * sdinv[nd];
-                });
-                __syncthreads();
-                if (act) {
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) {
-                        const double wv = mass * zn[cc] + c * opA64(le, cc);
-                        Wn[vidx(cc, e)] = wv;
-                        acc_d += zn[cc] * wv;
-                    }
-                }
-                __syncthreads();
             });
-            put_partial(ps, acc_g);
-            put_partial(ps + G, acc_d);
+            put_partial(part + 3 * G, acc);
             if (!bar()) return false;
-            const double rzn = total(ps);
-            delta = total(ps + G);
+            const double rzn = total(part + 3 * G);
             beta = rzn / rz;
             rz = rzn;
             ++it;
-            cb ^= 1;
-            fin = isfinite(rz) && isfinite(delta);
+            par ^= 1;
+            fin = isfinite(rz);
         }
         if (logit) {
             tiles([&](const long long e0, const int nle) {
