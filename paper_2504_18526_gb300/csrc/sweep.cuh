@@ -468,6 +468,7 @@ struct Sweeper {
                     faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) { return __ldcg(xs + cc * N + en * Q + nd); });
                 __syncthreads();
                 if (act) {
+                    RT loc32 = RT(0);
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
                         const long long id = vidx(cc, e);
@@ -489,8 +490,9 @@ struct Sweeper {
                         acc64 += r64 * (r64 * dinv);
                         const RT r32 = (RT)r64;
                         RF[id] = r32;
-                        acc32 += (double)r32 * (double)(r32 * dinvr);
+                        loc32 += r32 * (r32 * dinvr);
                     }
+                    acc32 += (double)loc32;
                 }
                 __syncthreads();
             });
@@ -538,12 +540,16 @@ struct Sweeper {
                     });
                     __syncthreads();
                     if (act) {
+                        // the thread's products in FP32, one conversion, FP64 accumulation
+                        // over threads and blocks (FP32<->FP64 conversions use the FP64 pipe)
+                        RT loc = RT(0);
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) {
                             const RT Apv = massr * pn[cc] + cr * opAR(le, cc);
                             AP[vidx(cc, e)] = Apv;
-                            acc += (double)pn[cc] * (double)Apv;
+                            loc += pn[cc] * Apv;
                         }
+                        acc += (double)loc;
                     }
                     __syncthreads();
                 });
@@ -555,14 +561,16 @@ struct Sweeper {
                 tiles([&](const long long e0, const int nle) {
                     if (le < nle) {
                         const long long e = e0 + le;
+                        RT loc = RT(0);
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) {
                             const long long id = vidx(cc, e);
                             x[id] = __ldcg(x + id) + alpha * (double)__ldcg(pcur + id);
                             const RT rr = __ldcg(RF + id) - alphar * __ldcg(AP + id);
                             RF[id] = rr;
-                            acc += (double)rr * (double)(rr * dinvr);
+                            loc += rr * (rr * dinvr);
                         }
+                        acc += (double)loc;
                     }
                 });
                 put_partial(part + 4 * G, acc);
