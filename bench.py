@@ -267,6 +267,24 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x 
 SWEEP_TRAFFIC_BYTES = {("burgers2d", "fp64"): 22.431488e6 + 16.843264e6}
 
 
+# ---------------------------------------------------------------------------
+# replicas (one process per GPU, no data-path collective): timing bookkeeping
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms, dist=None, device=None):
+    """The largest per-rank time (ms) of the timed region; identity on one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_step_per_rank, steps, world, ms):
+    """Units processed by all ranks per second (weak scaling: fixed work per rank)."""
+    return world * units_per_step_per_rank * steps / (ms * 1e-3)
+
+
 def make_ctx(S, w, stream, prec, rtol, use_graph):
     return S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=rtol, cg_maxit=1000,
                      use_graph=use_graph)
@@ -343,11 +361,8 @@ def main_arm(args):
     S.sisdc_sync(ctx.ctx)
     ms = sum(a.elapsed_time(b) for a, b in evs)
     stats = S.sisdc_get_stats(ctx.ctx)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * dofs_per_step * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, dev)
+    value = whole_job_value(dofs_per_step, args.steps, world, ms)
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region --
     h_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
