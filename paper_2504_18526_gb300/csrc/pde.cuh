@@ -7,11 +7,14 @@
 
 namespace sisdc {
 
-// Parameters the fluxes need (a subset of each kernel's arguments).
-struct PdeParams {
-    double gamma;
-    double ax, ay;
+// Parameters the fluxes need (a subset of each kernel's arguments), in the
+// arithmetic type R of the flux evaluation (converted once per kernel).
+template <class R>
+struct PdeParamsT {
+    R gamma;
+    R ax, ay;
 };
+using PdeParams = PdeParamsT<double>;
 
 template <int PDE>
 struct Pde;
@@ -20,53 +23,53 @@ template <>
 struct Pde<0> {   // scalar convection-diffusion, F = a u
     static constexpr int NC = 1;
     static constexpr bool VISC = false;
-    template <class T> __device__ static void fx(const PdeParams& a, const T* u, T* f) { f[0] = T(a.ax) * u[0]; }
-    template <class T> __device__ static void fy(const PdeParams& a, const T* u, T* f) { f[0] = T(a.ay) * u[0]; }
-    template <class T> __device__ static T rx(const PdeParams& a, const T*) { return fabs(T(a.ax)); }
-    template <class T> __device__ static T ry(const PdeParams& a, const T*) { return fabs(T(a.ay)); }
+    template <class T, class PP> __device__ static void fx(const PP& a, const T* u, T* f) { f[0] = T(a.ax) * u[0]; }
+    template <class T, class PP> __device__ static void fy(const PP& a, const T* u, T* f) { f[0] = T(a.ay) * u[0]; }
+    template <class T, class PP> __device__ static T rx(const PP& a, const T*) { return fabs(T(a.ax)); }
+    template <class T, class PP> __device__ static T ry(const PP& a, const T*) { return fabs(T(a.ay)); }
 };
 
 template <>
 struct Pde<1> {   // two-component Burgers, F = u (x) u
     static constexpr int NC = 2;
     static constexpr bool VISC = false;
-    template <class T> __device__ static void fx(const PdeParams&, const T* u, T* f) {
+    template <class T, class PP> __device__ static void fx(const PP&, const T* u, T* f) {
         f[0] = u[0] * u[0];
         f[1] = u[0] * u[1];
     }
-    template <class T> __device__ static void fy(const PdeParams&, const T* u, T* f) {
+    template <class T, class PP> __device__ static void fy(const PP&, const T* u, T* f) {
         f[0] = u[0] * u[1];
         f[1] = u[1] * u[1];
     }
-    template <class T> __device__ static T rx(const PdeParams&, const T* u) { return T(2) * fabs(u[0]); }
-    template <class T> __device__ static T ry(const PdeParams&, const T* u) { return T(2) * fabs(u[1]); }
+    template <class T, class PP> __device__ static T rx(const PP&, const T* u) { return T(2) * fabs(u[0]); }
+    template <class T, class PP> __device__ static T ry(const PP&, const T* u) { return T(2) * fabs(u[1]); }
 };
 
 template <>
 struct Pde<2> {   // 2D compressible Euler, perfect gas
     static constexpr int NC = 4;
     static constexpr bool VISC = false;
-    template <class T> __device__ static T pres(const PdeParams& a, const T* u) {
+    template <class T, class PP> __device__ static T pres(const PP& a, const T* u) {
         return (T(a.gamma) - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
     }
-    template <class T> __device__ static void fx(const PdeParams& a, const T* u, T* f) {
+    template <class T, class PP> __device__ static void fx(const PP& a, const T* u, T* f) {
         const T p = pres(a, u), vx = u[1] / u[0];
         f[0] = u[1];
         f[1] = u[1] * vx + p;
         f[2] = u[2] * vx;
         f[3] = (u[3] + p) * vx;
     }
-    template <class T> __device__ static void fy(const PdeParams& a, const T* u, T* f) {
+    template <class T, class PP> __device__ static void fy(const PP& a, const T* u, T* f) {
         const T p = pres(a, u), vy = u[2] / u[0];
         f[0] = u[2];
         f[1] = u[1] * vy;
         f[2] = u[2] * vy + p;
         f[3] = (u[3] + p) * vy;
     }
-    template <class T> __device__ static T rx(const PdeParams& a, const T* u) {
+    template <class T, class PP> __device__ static T rx(const PP& a, const T* u) {
         return fabs(u[1] / u[0]) + sqrt(T(a.gamma) * pres(a, u) / u[0]);
     }
-    template <class T> __device__ static T ry(const PdeParams& a, const T* u) {
+    template <class T, class PP> __device__ static T ry(const PP& a, const T* u) {
         return fabs(u[2] / u[0]) + sqrt(T(a.gamma) * pres(a, u) / u[0]);
     }
 };
@@ -77,7 +80,7 @@ struct Pde<2> {   // 2D compressible Euler, perfect gas
 template <>
 struct Pde<3> : Pde<2> {
     static constexpr bool VISC = true;
-    template <class T> __device__ static void primitive(const PdeParams& a, const T* u, T* w) {
+    template <class T, class PP> __device__ static void primitive(const PP& a, const T* u, T* w) {
         const T ir = T(1) / u[0];
         w[0] = u[1] * ir;
         w[1] = u[2] * ir;
@@ -101,8 +104,8 @@ struct Pde<3> : Pde<2> {
 };
 
 // Rusanov flux between a left/lower state uL and right/upper state uR.
-template <int PDE, bool XDIR, class T>
-__device__ __forceinline__ void rusanov(const PdeParams& a, const T* uL, const T* uR, T* Fs) {
+template <int PDE, bool XDIR, class T, class PP>
+__device__ __forceinline__ void rusanov(const PP& a, const T* uL, const T* uR, T* Fs) {
     using P = Pde<PDE>;
     T FL[P::NC], FR[P::NC];
     T lL, lR;

@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "ops.h"
+#include "ds.cuh"
 #include "pde.cuh"
 #include "sipg.cuh"
 
@@ -46,6 +47,16 @@ struct Sweeper {
     static constexpr int Q = NQ * NQY;
     static constexpr int NF = 2 * DIM;
     static constexpr int TRS = NF * 2 * NQ;
+    // arithmetic of the explicit operator evaluations (c(u), L u): FP64, or
+    // double-single on the FP32 pipe in the mixed form of the scalar
+    // convection-diffusion and Burgers PDEs
+    static constexpr bool EXDS = MIX && (PDE == 0 || PDE == 1);
+    using EX = typename std::conditional<EXDS, dsf, double>::type;
+
+    // geometry factors in the arithmetic of the double-single evaluations
+    struct GeoDS {
+        dsf sx, sy, ihx, ihy, taux, tauy, hx, hy, liftLx, liftRx, liftLy, liftRy;
+    };
 
     static size_t smem_bytes(int epb) {
         const size_t d = 2 * NQ * NQ + 3 * NQ + 32 + 2 * (MMAX + 1) + Q      // tables, scratch, lam, dinv
@@ -54,12 +65,17 @@ struct Sweeper {
         size_t r = MIX ? (2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q + (size_t)epb * NC * TRS +
                           (size_t)epb * 2 * NC * Q)                            // RT tables, tile, faces, fluxes
                        : 0;
-        return d2 * sizeof(double) + r * sizeof(RT) + 16;
+        const size_t x = EXDS ? (2 * NQ * NQ + NQ + 16 + 4) : 0;          // double-single tables, geometry, params
+        return d2 * sizeof(double) + r * sizeof(RT) + x * sizeof(dsf) + 16;
     }
 
     const SweepArgs& a;
     const Geo& g;
     PdeParams pp;
+    PdeParamsT<dsf>* xpp;          // flux parameters in double-single (shared memory)
+    GeoDS* xg;                     // geometry factors in double-single (shared memory)
+    dsf *xD, *xK, *xw;             // D, K, w in double-single (shared memory)
+    dsf imass_ds;                  // 1 / mass of the thread's node
     double *sD, *sK, *sw, *sdx, *sdy, *scratch, *slam_old, *slam_new, *sdinv, *su, *sf, *sF64;
     RT *rD, *rK, *rw, *rdx, *rdy, *rdinv, *ru, *rf, *sFR;
     int epb, le, node, i, j, G;
@@ -121,12 +137,30 @@ struct Sweeper {
             rf = reinterpret_cast<RT*>(sf);
             sFR = reinterpret_cast<RT*>(sF64);
         }
+        if constexpr (EXDS) {
+            const size_t rcount = 2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q + (size_t)epb * NC * TRS +
+                                  (size_t)epb * 2 * NC * Q;
+            xD = reinterpret_cast<dsf*>(rbase + ((rcount + 1) & ~size_t(1)));
+            xK = xD + NQ * NQ;
+            xw = xK + NQ * NQ;
+            xg = reinterpret_cast<GeoDS*>(xw + NQ);
+            xpp = reinterpret_cast<PdeParamsT<dsf>*>(xg + 1);
+            if (threadIdx.x == 0) {
+                *xg = GeoDS{dsf(g.sx), dsf(g.sy), dsf(g.ihx), dsf(g.ihy), dsf(g.taux), dsf(g.tauy),
+                            dsf(g.hx), dsf(g.hy), dsf(g.liftLx), dsf(g.liftRx), dsf(g.liftLy), dsf(g.liftRy)};
+                *xpp = PdeParamsT<dsf>{dsf(a.gamma), dsf(a.ax), dsf(a.ay)};
+            }
+        }
         for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) {
             sD[t] = g.D[t];
             sK[t] = g.K[t];
             if (MIX) {
                 rD[t] = (RT)g.D[t];
                 rK[t] = (RT)g.K[t];
+            }
+            if constexpr (EXDS) {
+                xD[t] = dsf(g.D[t]);
+                xK[t] = dsf(g.K[t]);
             }
         }
         for (int t = threadIdx.x; t < NQ; t += blockDim.x) {
@@ -138,6 +172,7 @@ struct Sweeper {
                 rdx[t] = (RT)g.dline_x[t];
                 rdy[t] = (RT)g.dline_y[t];
             }
+            if constexpr (EXDS) xw[t] = dsf(g.w[t]);
         }
         for (int t = threadIdx.x; t <= MMAX; t += blockDim.x) {
             slam_old[t] = __ldcg(a.lam + t);
@@ -156,6 +191,51 @@ struct Sweeper {
         log_n = 0;
         __syncthreads();
         mass_diag(i, j, mass, diagA);
+        if constexpr (EXDS) imass_ds = dsf(1.0 / mass);
+    }
+
+    // geometry factors, flux parameters and operator tables in arithmetic V
+    template <class V>
+    __device__ const auto& geo() const {
+        if constexpr (std::is_same<V, dsf>::value) return *xg;
+        else return g;
+    }
+    template <class V>
+    __device__ const auto& par() const {
+        if constexpr (std::is_same<V, dsf>::value) return *xpp;
+        else return pp;
+    }
+    template <class V>
+    __device__ const V* tab_D() const {
+        if constexpr (std::is_same<V, double>::value) return sD;
+        else if constexpr (std::is_same<V, dsf>::value) return xD;
+        else return reinterpret_cast<const V*>(rD);
+    }
+    template <class V>
+    __device__ const V* tab_K() const {
+        if constexpr (std::is_same<V, double>::value) return sK;
+        else if constexpr (std::is_same<V, dsf>::value) return xK;
+        else return reinterpret_cast<const V*>(rK);
+    }
+    template <class V>
+    __device__ const V* tab_w() const {
+        if constexpr (std::is_same<V, double>::value) return sw;
+        else if constexpr (std::is_same<V, dsf>::value) return xw;
+        else return reinterpret_cast<const V*>(rw);
+    }
+    // tile, face and flux buffers: the FP32 ones for V = float, else the
+    // 8-byte ones (double and double-single have the same size)
+    template <class V>
+    __device__ V* buf_tile() const {
+        return std::is_same<V, float>::value ? reinterpret_cast<V*>(ru) : reinterpret_cast<V*>(su);
+    }
+    template <class V>
+    __device__ V* buf_face() const {
+        return std::is_same<V, float>::value ? reinterpret_cast<V*>(rf) : reinterpret_cast<V*>(sf);
+    }
+    template <class V>
+    __device__ V* buf_flux() const {
+        return std::is_same<V, float>::value ? reinterpret_cast<V*>(sFR) : reinterpret_cast<V*>(sF64);
     }
 
     // GLL mass and diagonal of A at node (ii, jj) of an element
@@ -239,7 +319,7 @@ struct Sweeper {
                 vn[q] = getv(c, en, line_node(f ^ 1, k, q));
             }
             V jump, avg;
-            sipg_face<NQ>(g, vo, vn, f, Dt, jump, avg);
+            sipg_face<NQ>(geo<V>(), vo, vn, f, Dt, jump, avg);
             V* o = tf + ((l * NC + c) * NF + f) * 2 * NQ;
             o[k] = jump;
             o[NQ + k] = avg;
@@ -249,7 +329,7 @@ struct Sweeper {
     // (A u)(i, j) for component c of local element l
     template <class V>
     __device__ V opA(int l, int c, const V* tu, const V* tf, const V* Dt, const V* Kt, const V* wt) const {
-        return sipg_opA<NQ, DIM, V>(g, i, j, tu + (l * NC + c) * Q, tf + (l * NC + c) * TRS, Dt, Kt, wt);
+        return sipg_opA<NQ, DIM, V>(geo<V>(), i, j, tu + (l * NC + c) * Q, tf + (l * NC + c) * TRS, Dt, Kt, wt);
     }
     __device__ double opA64(int l, int c) const { return opA<double>(l, c, su, sf, sD, sK, sw); }
     __device__ RT opAR(int l, int c) const { return opA<RT>(l, c, ru, rf, rD, rK, rw); }
@@ -605,8 +685,10 @@ struct Sweeper {
     // viscous flux from them, into a.FV; its divergence is added to f by lap().
     template <class V>
     __device__ void conv(const double* X, int mode, CT* out, double* f64, double* lamslot) {
-        V* sFv = std::is_same<V, double>::value ? reinterpret_cast<V*>(sF64) : reinterpret_cast<V*>(sFR);
-        const V* Dv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sD) : reinterpret_cast<const V*>(rD);
+        V* sFv = buf_flux<V>();
+        const V* Dv = tab_D<V>();
+        const auto& gv = geo<V>();
+        const auto& pv = par<V>();
         const bool visc = PD::VISC && f64 != nullptr;
         double lmax = 0.0;
         tiles([&](const long long e0, const int nle) {
@@ -622,18 +704,18 @@ struct Sweeper {
                 for (int cc = 0; cc < NC; ++cc) u[cc] = (V)__ldcg(X + vidx(cc, e));
                 if constexpr (PD::VISC) {
                     if (visc) {
-                        PD::primitive(pp, u, w);
+                        PD::primitive(pv, u, w);
 #pragma unroll
                         for (int k = 0; k < 3; ++k) sW[k * Q + node] = w[k];
                     }
                 }
-                PD::fx(pp, u, Fx);
-                lmax = fmax(lmax, (double)PD::rx(pp, u));
+                PD::fx(pv, u, Fx);
+                lmax = fmax(lmax, static_cast<double>(PD::rx(pv, u)));
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) sFx[cc * Q + node] = Fx[cc];
                 if (DIM == 2) {
-                    PD::fy(pp, u, Fy);
-                    lmax = fmax(lmax, (double)PD::ry(pp, u));
+                    PD::fy(pv, u, Fy);
+                    lmax = fmax(lmax, static_cast<double>(PD::ry(pv, u)));
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) sFy[cc * Q + node] = Fy[cc];
                 }
@@ -646,7 +728,7 @@ struct Sweeper {
                     V s = V(0);
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) s += Dv[i * NQ + k] * sFx[cc * Q + j * NQ + k];
-                    cv[cc] = -V(g.sx) * s;
+                    cv[cc] = -V(gv.sx) * s;
                 }
                 if (DIM == 2) {
 #pragma unroll
@@ -654,7 +736,7 @@ struct Sweeper {
                         V s = V(0);
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) s += Dv[j * NQ + k] * sFy[cc * Q + k * NQ + i];
-                        cv[cc] -= V(g.sy) * s;
+                        cv[cc] -= V(gv.sy) * s;
                     }
                 }
                 if constexpr (PD::VISC) {
@@ -667,8 +749,8 @@ struct Sweeper {
                                 s += Dv[i * NQ + k] * sW[q * Q + j * NQ + k];
                                 t += Dv[j * NQ + k] * sW[q * Q + k * NQ + i];
                             }
-                            gx[q] = V(g.sx) * s;
-                            gy[q] = V(g.sy) * t;
+                            gx[q] = V(gv.sx) * s;
+                            gy[q] = V(gv.sy) * t;
                         }
                     }
                 }
@@ -677,7 +759,7 @@ struct Sweeper {
                 auto lift_w = [&](const V* un_, V* gd, V lift) {
                     if constexpr (PD::VISC) {
                         V wn[3];
-                        PD::primitive(pp, un_, wn);
+                        PD::primitive(pv, un_, wn);
 #pragma unroll
                         for (int q = 0; q < 3; ++q) gd[q] += lift * (V(0.5) * (w[q] + wn[q]) - w[q]);
                     }
@@ -687,38 +769,38 @@ struct Sweeper {
                     const long long en = neighbour(e, 1);
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + j * NQ);
-                    rusanov<PDE, true>(pp, u, un, Fs);
+                    rusanov<PDE, true>(pv, u, un, Fs);
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(g.liftRx) * (Fs[cc] - Fx[cc]);
-                    if (visc) lift_w(un, gx, V(g.liftRx));
+                    for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(gv.liftRx) * (Fs[cc] - Fx[cc]);
+                    if (visc) lift_w(un, gx, V(gv.liftRx));
                 }
                 if (i == 0) {
                     const long long en = neighbour(e, 0);
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + j * NQ + NQ - 1);
-                    rusanov<PDE, true>(pp, un, u, Fs);
+                    rusanov<PDE, true>(pv, un, u, Fs);
 #pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) cv[cc] += V(g.liftLx) * (Fs[cc] - Fx[cc]);
-                    if (visc) lift_w(un, gx, -V(g.liftLx));
+                    for (int cc = 0; cc < NC; ++cc) cv[cc] += V(gv.liftLx) * (Fs[cc] - Fx[cc]);
+                    if (visc) lift_w(un, gx, -V(gv.liftLx));
                 }
                 if (DIM == 2) {
                     if (j == NQ - 1) {
                         const long long en = neighbour(e, 3);
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + i);
-                        rusanov<PDE, false>(pp, u, un, Fs);
+                        rusanov<PDE, false>(pv, u, un, Fs);
 #pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(g.liftRy) * (Fs[cc] - Fy[cc]);
-                        if (visc) lift_w(un, gy, V(g.liftRy));
+                        for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(gv.liftRy) * (Fs[cc] - Fy[cc]);
+                        if (visc) lift_w(un, gy, V(gv.liftRy));
                     }
                     if (j == 0) {
                         const long long en = neighbour(e, 2);
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + (NQ - 1) * NQ + i);
-                        rusanov<PDE, false>(pp, un, u, Fs);
+                        rusanov<PDE, false>(pv, un, u, Fs);
 #pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) cv[cc] += V(g.liftLy) * (Fs[cc] - Fy[cc]);
-                        if (visc) lift_w(un, gy, -V(g.liftLy));
+                        for (int cc = 0; cc < NC; ++cc) cv[cc] += V(gv.liftLy) * (Fs[cc] - Fy[cc]);
+                        if (visc) lift_w(un, gy, -V(gv.liftLy));
                     }
                 }
                 if constexpr (PD::VISC) {
@@ -750,12 +832,11 @@ struct Sweeper {
     // from the conv phase of the same block (neighbours' X must be final)
     template <class V>
     __device__ void lap(const double* X, CT* LUm, double* Fm) {
-        V* tu = std::is_same<V, double>::value ? reinterpret_cast<V*>(su) : reinterpret_cast<V*>(ru);
-        V* tf = std::is_same<V, double>::value ? reinterpret_cast<V*>(sf) : reinterpret_cast<V*>(rf);
-        const V* Dv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sD) : reinterpret_cast<const V*>(rD);
-        const V* Kv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sK) : reinterpret_cast<const V*>(rK);
-        const V* wv = std::is_same<V, double>::value ? reinterpret_cast<const V*>(sw) : reinterpret_cast<const V*>(rw);
-        const V massv = (V)mass;
+        V* tu = buf_tile<V>();
+        V* tf = buf_face<V>();
+        const V* Dv = tab_D<V>();
+        const V* Kv = tab_K<V>();
+        const V* wv = tab_w<V>();
         tiles([&](const long long e0, const int nle) {
             const bool act = le < nle;
             const long long e = e0 + le;
@@ -774,7 +855,9 @@ struct Sweeper {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
                     const long long id = vidx(cc, e);
-                    const V lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) / massv;
+                    V lu;
+                    if constexpr (std::is_same<V, dsf>::value) lu = -(opA<V>(le, cc, tu, tf, Dv, Kv, wv) * imass_ds);
+                    else lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) / (V)mass;
                     LUm[id] = (CT)lu;
                     Fm[id] = __ldcg(Fm + id) + a.nu * (double)lu;
                 }
@@ -872,18 +955,18 @@ struct Sweeper {
     __device__ bool visc_bar() { return PD::VISC ? bar() : true; }
 
     __device__ bool feval() {
-        conv<double>(a.u0, CONV_OUT, C(a.tmpc), a.fout, nullptr);
+        conv<EX>(a.u0, CONV_OUT, C(a.tmpc), a.fout, nullptr);
         if (!visc_bar()) return false;
-        lap<double>(a.u0, C(a.dC), a.fout);
+        lap<EX>(a.u0, C(a.dC), a.fout);
         return true;
     }
 
     __device__ bool refresh() {
-        conv<double>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
+        conv<EX>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
         for (int m = 0; m < a.M; ++m) {
-            conv<double>(Um(a.U, m), CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+            conv<EX>(Um(a.U, m), CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
             if (!visc_bar()) return false;
-            lap<double>(Um(a.U, m), Cm(a.LU, m), Um(a.F, m));
+            lap<EX>(Um(a.U, m), Cm(a.LU, m), Um(a.F, m));
             if (!visc_bar()) return false;
         }
         if (!bar()) return false;
@@ -897,7 +980,7 @@ struct Sweeper {
     }
 
     __device__ bool predict() {
-        conv<double>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
+        conv<EX>(a.u0, CONV_OUT, C(a.c0), nullptr, a.partmax);
         if (!bar()) return false;
         double lam = total_max(a.partmax);
         if (threadIdx.x == 0) slam_new[0] = lam;
@@ -913,7 +996,7 @@ struct Sweeper {
                 t1.add(cp, dtm);
                 if (!solve(um, up, t1, cimp, m ? Cm(a.LU, m - 1) : nullptr)) return false;   // warm start u_{m-1}
                 if (a.stages == 2) {
-                    conv<double>(um, CONV_OUT, C(a.tmpc), nullptr, nullptr);
+                    conv<EX>(um, CONV_OUT, C(a.tmpc), nullptr, nullptr);
                     Terms t2{};
                     t2.add(up, 1.0);
                     t2.add((const CT*)C(a.tmpc), dtm);
@@ -925,9 +1008,9 @@ struct Sweeper {
                 lin(um, t0);                               // Lobatto t_1 = t_0
                 if (!bar()) return false;
             }
-            conv<double>(um, CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+            conv<EX>(um, CONV_OUT, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
             if (!visc_bar()) return false;
-            lap<double>(um, Cm(a.LU, m), Um(a.F, m));
+            lap<EX>(um, Cm(a.LU, m), Um(a.F, m));
             if (!bar()) return false;
             lam = total_max(a.partmax + (size_t)(m + 1) * G);
             if (threadIdx.x == 0) slam_new[m + 1] = lam;
@@ -964,15 +1047,15 @@ struct Sweeper {
                     if (m > 0) t1.add((const CT*)C(a.dC), dtm);          // c(u^k_{m-1}) - c(u^{k-1}_{m-1})
                     if (!solve(um, um, t1, dtm * nu_new, Cm(a.LU, m))) return false;
                     if (a.stages == 2) {
-                        conv<double>(um, CONV_OUT, C(a.tmpc), nullptr, nullptr);
+                        conv<EX>(um, CONV_OUT, C(a.tmpc), nullptr, nullptr);
                         t2.add((const CT*)C(a.tmpc), dtm);               // c(u^(1))
                         t2.add((const CT*)Cm(a.CC, m), -dtm);            // c(u^{k-1}_m)
                         if (!solve(um, um, t2, dtm * nu_new)) return false;
                     }
                 }
-                conv<double>(um, CONV_DELTA, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
+                conv<EX>(um, CONV_DELTA, Cm(a.CC, m), Um(a.F, m), a.partmax + (size_t)(m + 1) * G);
                 if (!visc_bar()) return false;
-                lap<double>(um, Cm(a.LU, m), Um(a.F, m));
+                lap<EX>(um, Cm(a.LU, m), Um(a.F, m));
                 if (!bar()) return false;
                 lam = total_max(a.partmax + (size_t)(m + 1) * G);
                 if (threadIdx.x == 0) slam_new[m + 1] = lam;
