@@ -517,7 +517,7 @@ struct EnsSweeper {
                     acc[1] += r64 * (r64 * dinv);
                     const RT r32 = (RT)r64;
                     RF[id] = r32;
-                    acc[2] += (double)r32 * (double)(r32 * dinvr);
+                    acc[2] += (double)(r32 * (r32 * dinvr));   // FP32 term, FP64 sum
                 }
             });
             if (!bar()) return false;
@@ -571,7 +571,7 @@ struct EnsSweeper {
                         mass_diag(I, i, j, ms, dg);
                         const RT Apv = (RT)ms * pn + cr * opA<RT>(I, ru, rf, rD, rK, rw);
                         AP[id] = Apv;
-                        acc[0] += (double)pn * (double)Apv;
+                        acc[0] += (double)(pn * Apv);
                     }
                 });
                 if (!bar()) return false;
@@ -587,7 +587,7 @@ struct EnsSweeper {
                         x[id] = __ldcg(x + id) + alpha * (double)__ldcg(pcur + id);
                         const RT rr = __ldcg(RF + id) - alphar * __ldcg(AP + id);
                         RF[id] = rr;
-                        acc[0] += (double)rr * (double)(rr * dinvr);
+                        acc[0] += (double)(rr * (rr * dinvr));
                     }
                 });
                 if (!bar()) return false;
