@@ -112,3 +112,29 @@ def test_space_transfers(Pf, Pc):
     for deg in range(Pc + 1):
         assert np.allclose(Ix @ xc ** deg, xf ** deg, atol=1e-13)
     assert np.allclose(Rx @ np.ones(Pf + 1), 1.0, atol=1e-13)
+
+
+def test_level_cost_model_matches_printed_table():
+    """The per-level costs of the paper's runtime table are DOF x M ratios of
+    its discretization (the accounting of the DOF-sweep metric): 1D levels
+    36 % and 11 %, 3D (h-coarsened by 2 per direction) 9 % and 0.6 %, and
+    1 + N_c (0.36 + 0.11) = 1.94 fine-grid operations for N_c = 2."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "level_costs.txt")
+    rows = {}
+    for ln in open(path):
+        if ln.strip() and not ln.startswith("#"):
+            f = ln.split()
+            rows[f[0]] = f[1:]
+    levels = [(16, 15, 3), (32, 15, 5), (64, 15, 7)]          # (N_e, P, M), coarse to fine
+    dof_m = [ne * (P + 1) * M for ne, P, M in levels]
+    c2, c1 = dof_m[1] / dof_m[2], dof_m[0] / dof_m[2]
+    assert round(100 * c2) == int(rows["1D_MLSDC_3_5_7"][0]) == int(rows["1D_MLSDC_5_7"][0])
+    assert round(100 * c1) == int(rows["1D_MLSDC_3_5_7"][1])
+    c2_3d, c1_3d = (1 / 8) * 5 / 7, (1 / 64) * 3 / 7
+    assert round(100 * c2_3d) == int(rows["3D_MLSDC_3_5_7"][0]) == int(rows["3D_MLSDC_5_7"][0])
+    assert math.floor(1000 * c1_3d) / 10 == float(rows["3D_MLSDC_3_5_7"][1])   # 0.67 % printed as 0.6
+    Nc = 2
+    printed = float(rows["three_level_1D_Nc2_fine_ops"][0])
+    assert abs(1 + Nc * (0.36 + 0.11) - printed) < 1e-12
+    assert abs(1 + Nc * (c2 + c1) - printed) < 0.02
