@@ -93,7 +93,8 @@ typedef enum {
 
 /* One space-time level Q_l = Omega_l x T_l (Sec. 6.1): a periodic box
  * [lo, hi] split into nel[0] x nel[1] equal elements (nel[1] = 1 in 1D) of
- * degree P (1..8) and M collocation nodes (1..8; >= 2 for Lobatto). */
+ * degree P (1..8; 1..15 for 1D convection-diffusion in SISDC_FP64) and M
+ * collocation nodes (1..8; >= 2 for Lobatto). */
 typedef struct {
     int dim;
     int nel[2];

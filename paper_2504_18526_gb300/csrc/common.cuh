@@ -5,7 +5,7 @@
 
 namespace sisdc {
 
-constexpr int NQMAX = 9;      // P <= 8
+constexpr int NQMAX = 16;     // nodes per direction: P <= 8 in 2D, P <= 15 in 1D
 constexpr int MMAX = 8;       // collocation nodes per level
 constexpr int MAXTERMS = 8;   // terms of a fused linear combination
 

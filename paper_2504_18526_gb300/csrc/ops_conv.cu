@@ -158,8 +158,22 @@ static cudaError_t conv_nq(const ConvArgs& a, cudaStream_t s) {
     }
 }
 
+// degrees 9..15: 1D convection-diffusion only
+template <int NQ>
+static cudaError_t conv_1d(const ConvArgs& a, cudaStream_t s) {
+    if (a.g.dim == 1 && a.pde == 0) return conv_impl<NQ, 1, 0>(a, s);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
     switch (a.g.nq) {
+        case 10: return conv_1d<10>(a, s);
+        case 11: return conv_1d<11>(a, s);
+        case 12: return conv_1d<12>(a, s);
+        case 13: return conv_1d<13>(a, s);
+        case 14: return conv_1d<14>(a, s);
+        case 15: return conv_1d<15>(a, s);
+        case 16: return conv_1d<16>(a, s);
         case 2: return conv_nq<2>(a, s);
         case 3: return conv_nq<3>(a, s);
         case 4: return conv_nq<4>(a, s);

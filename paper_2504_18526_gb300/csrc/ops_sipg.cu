@@ -407,6 +407,8 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
 // Host launchers
 // ---------------------------------------------------------------------------
 #define SISDC_NQ_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9)
+// degrees 9..15: 1D levels only
+#define SISDC_NQ1D_CASES(X) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
 template <int NQ, int DIM>
 static cudaError_t traces_impl(const Geo& g, const double* u, double* tr, cudaStream_t s) {
@@ -421,7 +423,9 @@ static cudaError_t traces_impl(const Geo& g, const double* u, double* tr, cudaSt
 
 cudaError_t launch_traces(const Geo& g, const double* u, double* tr, cudaStream_t s) {
 #define X(n) case n: return g.dim == 1 ? traces_impl<n, 1>(g, u, tr, s) : traces_impl<n, 2>(g, u, tr, s);
-    switch (g.nq) { SISDC_NQ_CASES(X) default: return cudaErrorInvalidValue; }
+#define X1(n) case n: return g.dim == 1 ? traces_impl<n, 1>(g, u, tr, s) : cudaErrorInvalidValue;
+    switch (g.nq) { SISDC_NQ_CASES(X) SISDC_NQ1D_CASES(X1) default: return cudaErrorInvalidValue; }
+#undef X1
 #undef X
 }
 
@@ -438,7 +442,9 @@ static cudaError_t apply_impl(const ApplyArgs& a, cudaStream_t s) {
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
 #define X(n) case n: return a.g.dim == 1 ? apply_impl<n, 1>(a, s) : apply_impl<n, 2>(a, s);
-    switch (a.g.nq) { SISDC_NQ_CASES(X) default: return cudaErrorInvalidValue; }
+#define X1(n) case n: return a.g.dim == 1 ? apply_impl<n, 1>(a, s) : cudaErrorInvalidValue;
+    switch (a.g.nq) { SISDC_NQ_CASES(X) SISDC_NQ1D_CASES(X1) default: return cudaErrorInvalidValue; }
+#undef X1
 #undef X
 }
 
@@ -471,7 +477,9 @@ static int pcg_grid_impl(const Geo& g, int* block) {
 
 int pcg_grid(const Geo& g, int* block) {
 #define X(n) case n: return g.dim == 1 ? pcg_grid_impl<n, 1>(g, block) : pcg_grid_impl<n, 2>(g, block);
-    switch (g.nq) { SISDC_NQ_CASES(X) default: return 0; }
+#define X1(n) case n: return g.dim == 1 ? pcg_grid_impl<n, 1>(g, block) : 0;
+    switch (g.nq) { SISDC_NQ_CASES(X) SISDC_NQ1D_CASES(X1) default: return 0; }
+#undef X1
 #undef X
 }
 
@@ -494,7 +502,9 @@ static cudaError_t pcg_impl(const PCGArgs& a, int grid, int block, cudaStream_t 
 
 cudaError_t launch_pcg(const PCGArgs& a, int grid, int block, cudaStream_t s) {
 #define X(n) case n: return a.g.dim == 1 ? pcg_impl<n, 1>(a, grid, block, s) : pcg_impl<n, 2>(a, grid, block, s);
-    switch (a.g.nq) { SISDC_NQ_CASES(X) default: return cudaErrorInvalidValue; }
+#define X1(n) case n: return a.g.dim == 1 ? pcg_impl<n, 1>(a, grid, block, s) : cudaErrorInvalidValue;
+    switch (a.g.nq) { SISDC_NQ_CASES(X) SISDC_NQ1D_CASES(X1) default: return cudaErrorInvalidValue; }
+#undef X1
 #undef X
 }
 

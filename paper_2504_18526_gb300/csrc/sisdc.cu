@@ -543,7 +543,9 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     if (d->dim != 1 && d->dim != 2) return fail(c, SISDC_E_ARG, "dim must be 1 or 2");
     if (d->dim == 1 && c->prob.pde != SISDC_PDE_CONVDIFF) return fail(c, SISDC_E_ARG, "1D supports convection-diffusion only");
     if ((long long)d->nel[0] * (d->dim == 2 ? d->nel[1] : 1) > (1LL << 30)) return fail(c, SISDC_E_ARG, "too many elements");
-    if (d->P < 1 || d->P > 8) return fail(c, SISDC_E_ARG, "P must be in 1..8");
+    // degrees up to 15 for 1D convection-diffusion in FP64, up to 8 otherwise
+    const int pmax = (d->dim == 1 && c->prob.pde == SISDC_PDE_CONVDIFF && c->prob.precision == SISDC_FP64) ? 15 : 8;
+    if (d->P < 1 || d->P > pmax) return fail(c, SISDC_E_ARG, "P must be in 1..8 (1..15 for 1D convection-diffusion in FP64)");
     if (d->M < 1 || d->M > MMAX) return fail(c, SISDC_E_ARG, "M must be in 1..8");
     if (d->nodes != SISDC_RADAU_RIGHT && d->nodes != SISDC_LOBATTO) return fail(c, SISDC_E_ARG, "bad node kind");
     if (d->nodes == SISDC_LOBATTO && d->M < 2) return fail(c, SISDC_E_ARG, "Lobatto needs M >= 2");

@@ -127,7 +127,7 @@ std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std:
 }
 
 bool build_level_tables(int P, int M, int lobatto, LevelTables* t) {
-    if (P < 1 || P > 8 || M < 1 || M > 8 || (lobatto && M < 2)) return false;
+    if (P < 1 || P > 15 || M < 1 || M > 8 || (lobatto && M < 2)) return false;
     const int nq = P + 1;
     std::vector<ld> x, w;
     gll_ld(P, &x, &w);

@@ -50,3 +50,29 @@ def random_state(w, shape, seed):
     if w["pde"] in ("euler", "ns"):
         return physical_euler_state(shape, rng)
     return rng.standard_normal(shape)
+
+
+def wave_packet_fixture():
+    """Coefficients (kappa, a, s) and the printed iteration counts of the
+    paper's preliminary 1D studies (tests/golden/wave_packet_iterations.txt)."""
+    import math
+    import os
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden", "wave_packet_iterations.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    coef = [(float(r[0]) * math.pi, float(r[1]), float(r[2])) for r in rows if not r[0].startswith("test")]
+    tests = {r[0]: (tuple(int(m) for m in r[1].split(",")), int(r[2]), int(r[3])) for r in rows if r[0].startswith("test")}
+    return coef, tests
+
+
+def wave_packet_exact(coef, X, t, nu=2e-2, v=1.0):
+    """u = sum_i a_i sin(kappa_i (x - s_i - v t)) exp(-kappa_i^2 nu t)."""
+    import math
+    return sum(a * np.sin(k * (X - s - v * t)) * math.exp(-k * k * nu * t) for k, a, s in coef)[None]
+
+
+def converged_at(errs):
+    """First iteration whose L2 error differs from the previous one by less than 10 %."""
+    for k in range(1, len(errs)):
+        if abs(errs[k] - errs[k - 1]) <= 0.1 * abs(errs[k - 1]):
+            return k
+    return None

@@ -207,34 +207,18 @@ def test_ns_step_conserves_mass_momentum_energy():
     assert np.max(np.abs(u1 - u0)) > 1e-6
 
 
-def _wave_packet_fixture():
-    import os
-    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden", "wave_packet_iterations.txt"))
-            if ln.strip() and not ln.startswith("#")]
-    coef = [(float(r[0]) * math.pi, float(r[1]), float(r[2])) for r in rows if not r[0].startswith("test")]
-    tests = {r[0]: (tuple(int(m) for m in r[1].split(",")), int(r[2]), int(r[3])) for r in rows if r[0].startswith("test")}
-    return coef, tests
-
-
-def _converged_at(errs):
-    """First iteration whose L2 error differs from the previous one by less than 10 %."""
-    for k in range(1, len(errs)):
-        if abs(errs[k] - errs[k - 1]) <= 0.1 * abs(errs[k - 1]):
-            return k
-    return None
-
-
 @pytest.mark.parametrize("test", ["test1", "test2"])
 def test_paper_wave_packet_iteration_counts(test):
     """The paper's preliminary 1D studies: single-level SDC and the three-level
     V-cycle reach convergence after the printed numbers of sweeps / cycles
     (test 1 exactly; test 2 within one cycle for MLSDC)."""
-    coef, tests = _wave_packet_fixture()
+    from tests.helpers import wave_packet_fixture, wave_packet_exact, converged_at
+    coef, tests = wave_packet_fixture()
     Ms, sdc_sweeps, ml_cycles = tests[test]
     nu, v, dt = 2e-2, 1.0, 1e-2
 
     def exact(X, t):
-        return sum(a * np.sin(k * (X - s - v * t)) * math.exp(-k * k * nu * t) for k, a, s in coef)[None]
+        return wave_packet_exact(coef, X, t, nu, v)
 
     mk = lambda: DGSpace(1, (32,), 15, (0.0, 0.0), (1.0, 0.0), ConvDiff((v, 0.0), nu), cg_rtol=1e-14,
                          cg_maxit=10000)
@@ -248,7 +232,7 @@ def test_paper_wave_packet_iteration_counts(test):
     for _ in range(sdc_sweeps + 4):
         U = S.corrector(levels[-1], u0, U, None, dt, 2, 1)
         errs.append(fine.l2(U[-1] - ue))
-    assert _converged_at(errs) + 1 == sdc_sweeps
+    assert converged_at(errs) + 1 == sdc_sweeps
     ml = MLSDC(levels, stages=2, Nc=2)
     u0s = ml.initial_values(u0)
     Us = ml.start(u0s, dt, "predictor")
@@ -256,7 +240,7 @@ def test_paper_wave_packet_iteration_counts(test):
     for _ in range(ml_cycles + 4):
         Us = ml.vcycle(u0s, Us, dt)
         errm.append(fine.l2(Us[-1][-1] - ue))
-    got = _converged_at(errm)
+    got = converged_at(errm)
     if test == "test1":
         assert got == ml_cycles
     else:
