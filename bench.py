@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="8x8 elements (profiling case)")
     ap.add_argument("--ninst", type=int, default=0, help="ensemble: first N instances only (profiling case)")
-    ap.add_argument("--no-autotune", action="store_true", help="ensemble: default tile shapes")
+    ap.add_argument("--no-autotune", action="store_true", help="default tile shapes (no sisdc_autotune)")
     ap.add_argument("--per-instance", type=int, default=0,
                     help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -290,6 +290,13 @@ def make_ctx(S, w, stream, prec, rtol, use_graph):
                      use_graph=use_graph)
 
 
+def tune(S, args, ctx, du, dt, nlevels):
+    """Tile shapes from the library's autotuner (setup, outside every timed region)."""
+    if args.no_autotune:
+        return [list(S.sisdc_level_config(lv)) for lv in ctx.levels]
+    return S.sisdc_autotune(ctx.ctx, du, dt, nlevels).tolist()
+
+
 def run_steps(S, ctx, du, dt, ncyc, start, nsteps):
     for _ in range(nsteps):
         S.sisdc_step(ctx.ctx, du, 0.0, dt, ncyc, start, 1)
@@ -336,6 +343,8 @@ def main_arm(args):
     du = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     torch.cuda.synchronize()
+    nlev = len(w["levels"])
+    tiles = tune(S, args, ctx, du, dt, nlev)
 
     run_steps(S, ctx, du, dt, ncyc, start, args.warmup)
     S.sisdc_sync(ctx.ctx)
@@ -391,6 +400,7 @@ def main_arm(args):
     # ---- dominant kernel: live CUDA-event timing of the fine-level sweeps ----
     kctx = make_ctx(S, w, stream, prec, args.cg_rtol, 0)
     dk = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+    tune(S, args, kctx, dk, dt, nlev)
     run_steps(S, kctx, dk, dt, ncyc, start, 2)
     S.sisdc_sync(kctx.ctx)
     S.sisdc_reset_stats(kctx.ctx)
@@ -423,6 +433,7 @@ def main_arm(args):
     for pf, name in ((S.SISDC_FP64, "fp64_plain"), (S.SISDC_MIXED, "mixed_tuned")):
         fctx = make_ctx(S, w, stream, pf, args.cg_rtol, 1)
         uf = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+        tune(S, args, fctx, uf, dt, nlev)
         run_steps(S, fctx, uf, dt, ncyc, start, 2)                 # capture + warm
         S.sisdc_sync(fctx.ctx)                                     # the reset must follow them
         uf.copy_(torch.from_numpy(np.ascontiguousarray(u0)))
@@ -466,6 +477,8 @@ def main_arm(args):
                    "fine_dofs": nv, "levels": w["levels"], "nodes": w["nodes"], "dt": dt,
                    "ncycles": ncyc, "fine_sweeps_per_step": ncyc + 1, "start": w["start"],
                    "si_stages": 2, "cg_rtol": args.cg_rtol, "cuda_graph": bool(use_graph),
+                   "tiles": {"per_level_coarse_to_fine": tiles, "autotuned": not args.no_autotune,
+                             "fields": "elements per tile, blocks, threads per block"},
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "k_sweep correction launches, fine level",

@@ -263,6 +263,19 @@ sisdc_status sisdc_norms(sisdc_level lv, const double* d_u, const double* d_ref,
  * TIMEOUT, NONFINITE) recorded since the previous sisdc_sync and clear them. */
 sisdc_status sisdc_sync(sisdc_ctx ctx);
 
+/* Tile-shape autotuner of the persistent sweep kernel (not in the paper).
+ * For every level, candidate shapes (elements per tile -> a block of
+ * (P+1)^dim threads per element, and the number of persistent blocks) each run
+ * one cache refresh and `reps` timed correction sweeps from the state d_u
+ * (the fine-level state [ncomp][nel][Q]; projected to coarser levels and
+ * spread over the collocation nodes; d_u is not modified); the fastest shape
+ * is kept for all later launches.  h_config (nullable) receives 3 ints per
+ * level, coarse to fine: elements per tile, blocks, threads per block.
+ * Synchronous; invalidates a captured step graph; resets the counters. */
+sisdc_status sisdc_autotune(sisdc_ctx ctx, const double* d_u, double dt, int reps, int* h_config);
+/* The current shape of a level's sweep launches (any pointer may be NULL). */
+sisdc_status sisdc_level_config(sisdc_level lv, int* h_epb, int* h_grid, int* h_block);
+
 /* Counters since creation or the last reset (synchronises the stream). */
 sisdc_status sisdc_get_stats(sisdc_ctx ctx, sisdc_stats* out);
 sisdc_status sisdc_reset_stats(sisdc_ctx ctx);

@@ -115,7 +115,8 @@ struct SweepArgs {
     int log_cap;
     cudaStream_t stream;
 };
-// returns the cooperative grid (0 if unavailable); epb = elements per block
+// returns the largest cooperative grid (0 if unavailable) for tiles of *epb
+// elements per block (in: requested size, 0 = default heuristic; out: used)
 int sweep_config(const Geo& g, int pde, int mix, int* epb, int* block);
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int block);
 

@@ -921,6 +921,102 @@ sisdc_status sisdc_reset_stats(sisdc_ctx c) {
     return SISDC_OK;
 }
 
+sisdc_status sisdc_level_config(sisdc_level lv, int* h_epb, int* h_grid, int* h_block) {
+    if (!lv) return SISDC_E_ARG;
+    if (h_epb) *h_epb = lv->sw_epb;
+    if (h_grid) *h_grid = lv->sw_grid;
+    if (h_block) *h_block = lv->sw_block;
+    return SISDC_OK;
+}
+
+// Tile-shape autotuner of the persistent sweep kernel: per level, every
+// candidate (elements per tile, blocks in the grid) runs one refresh and one
+// timed correction sweep from the caller's state (projected to the level,
+// spread over its nodes); the fastest is kept.
+sisdc_status sisdc_autotune(sisdc_ctx c, const double* d_u, double dt, int reps, int* h_config) {
+    if (!c || !d_u || !(dt > 0.0) || reps < 1) return SISDC_E_ARG;
+    if (c->levels.empty()) return fail(c, SISDC_E_STATE, "no level created");
+    std::vector<sisdc_level_s*>& L = c->levels;
+    const int nl = (int)L.size();
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const bool mix = c->prob.precision == SISDC_MIXED;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+        check(c, cudaEventCreate(&e0), "event");
+        check(c, cudaEventCreate(&e1), "event");
+        copy_d2d(L[nl - 1], L[nl - 1]->u0, d_u, L[nl - 1]->NV);
+        for (int l = nl - 1; l >= 1; --l) k_transfer(L[l], T_PROJECT_SPACE, L[l]->u0, L[l - 1]->u0, 0);
+        for (int l = 0; l < nl; ++l) {
+            sisdc_level_s* lv = L[l];
+            auto spread = [&]() {
+                for (int m = 0; m < lv->M; ++m) copy_d2d(lv, Um(lv, lv->U, m), lv->u0, lv->NV);
+            };
+            const int maxepb = lv->Q >= 512 ? 1 : 512 / lv->Q;
+            std::vector<int> cand;
+            for (int e : {maxepb, (3 * maxepb) / 4, maxepb / 2, maxepb / 3, maxepb / 4, lv->sw_epb, 2, 1})
+                if (e >= 1 && e <= maxepb && std::find(cand.begin(), cand.end(), e) == cand.end()) cand.push_back(e);
+            float best = 0.0f;
+            int best_epb = lv->sw_epb, best_grid = lv->sw_grid, best_block = lv->sw_block;
+            for (int e : cand) {
+                int epb = e, block = 0;
+                const int gmax = sweep_config(lv->geo, c->prob.pde, mix ? 1 : 0, &epb, &block);
+                if (gmax < 1 || gmax > c->max_grid) continue;
+                for (int grid : {gmax, gmax / 2}) {
+                    if (grid < 1 || (grid == gmax / 2 && gmax < 2 * nsm)) continue;
+                    lv->sw_epb = epb;
+                    lv->sw_grid = grid;
+                    lv->sw_block = block;
+                    float t = 0.0f;
+                    for (int r = 0; r < reps; ++r) {
+                        spread();
+                        refresh(lv, lv->u0, lv->U);
+                        check(c, cudaEventRecord(e0, c->stream), "event");
+                        run_sweep_kernel(lv, SW_CORRECT, lv->u0, lv->U, nullptr, dt, 1);
+                        check(c, cudaEventRecord(e1, c->stream), "event");
+                        check(c, cudaEventSynchronize(e1), "event sync");
+                        float ms = 0.0f;
+                        check(c, cudaEventElapsedTime(&ms, e0, e1), "event time");
+                        t = r == 0 ? ms : std::min(t, ms);
+                    }
+                    if (best == 0.0f || t < best) {
+                        best = t;
+                        best_epb = epb;
+                        best_grid = grid;
+                        best_block = block;
+                    }
+                }
+            }
+            lv->sw_epb = best_epb;
+            lv->sw_grid = best_grid;
+            lv->sw_block = best_block;
+            lv->valid = false;
+            if (h_config) {
+                h_config[3 * l] = best_epb;
+                h_config[3 * l + 1] = best_grid;
+                h_config[3 * l + 2] = best_block;
+            }
+        }
+        check(c, cudaStreamSynchronize(c->stream), "sync");
+    } catch (const Fail& f) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return f.st;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    // the timing runs count nothing
+    cudaMemset(c->d_stats, 0, ST_N * sizeof(long long));
+    for (int l = 0; l < 8; ++l) c->sweeps[l] = 0;
+    c->launches = 0;
+    return sisdc_sync(c);
+}
+
 sisdc_status sisdc_set_kernel_timing(sisdc_ctx c, int enable, int level) {
     if (!c) return SISDC_E_ARG;
     if (enable && c->prob.use_graph) return fail(c, SISDC_E_STATE, "kernel timing needs eager mode (use_graph = 0)");

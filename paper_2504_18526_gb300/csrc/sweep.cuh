@@ -1106,10 +1106,15 @@ int sweep_config_impl(const Geo& g, int* epb_out, int* block_out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int maxepb = S::Q >= 512 ? 1 : 512 / S::Q;
-    long long want = (g.nel + nsm - 1) / nsm;      // aim at one tile per SM
-    int epb = (int)(want < 1 ? 1 : (want > maxepb ? maxepb : want));
-    const int minepb = (32 + S::Q - 1) / S::Q;     // at least one warp per block
-    if (epb < minepb) epb = minepb > maxepb ? maxepb : minepb;
+    int epb;
+    if (*epb_out > 0) {                            // requested tile size (autotuner)
+        epb = *epb_out > maxepb ? maxepb : *epb_out;
+    } else {
+        long long want = (g.nel + nsm - 1) / nsm;  // aim at one tile per SM
+        epb = (int)(want < 1 ? 1 : (want > maxepb ? maxepb : want));
+        const int minepb = (32 + S::Q - 1) / S::Q; // at least one warp per block
+        if (epb < minepb) epb = minepb > maxepb ? maxepb : minepb;
+    }
     const int bs = warp_round(epb * S::Q);
     const size_t sh = sweep_smem<NQ, DIM, PDE, MIX>(epb);
     // the attribute covers the largest tile, so that levels of the same degree

@@ -115,6 +115,8 @@ def load():
         "sisdc_solve_noalloc": (c_int, [P(sisdc_level_desc), c_int, c_double, c_void_p, c_void_p, c_double,
                                         c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
         "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll), P(c_ll)]),
+        "sisdc_autotune": (c_int, [c_void_p, c_void_p, c_double, c_int, c_void_p]),
+        "sisdc_level_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
         "sisdc_ens_create": (c_int, [P(sisdc_ens_instance), c_int, P(sisdc_ens_opts), c_void_p, P(c_void_p)]),
         "sisdc_ens_destroy": (None, [c_void_p]),
         "sisdc_ens_layout": (c_int, [c_void_p, c_void_p, P(c_ll)]),
@@ -337,6 +339,20 @@ def sisdc_get_stats(ctx):
 
 def sisdc_reset_stats(ctx):
     _check(load().sisdc_reset_stats(ctx), ctx)
+
+
+def sisdc_autotune(ctx, u, dt, nlevels, reps=2):
+    """Returns the chosen (elements per tile, blocks, threads per block) per level."""
+    import numpy as np
+    cfg = np.zeros(3 * nlevels, dtype=np.int32)
+    _check(load().sisdc_autotune(ctx, _ptr(u), dt, reps, cfg.ctypes.data), ctx)
+    return cfg.reshape(nlevels, 3)
+
+
+def sisdc_level_config(lv):
+    e, g, b = c_int(), c_int(), c_int()
+    _check(load().sisdc_level_config(lv, ctypes.byref(e), ctypes.byref(g), ctypes.byref(b)), lv=lv)
+    return e.value, g.value, b.value
 
 
 def sisdc_set_kernel_timing(ctx, enable, level=-1):

@@ -342,6 +342,32 @@ def test_ns_shear_layer_full_size(dev):
     assert rel_l2(out[S.SISDC_MIXED], out[S.SISDC_FP64]) < 1e-10
 
 
+def test_autotuned_shapes_keep_results(dev):
+    """The tile-shape autotuner changes only launch shapes: steps from an
+    autotuned context equal those of the default one (to rounding order)."""
+    w = inputs.scaled("burgers2d", nel=(8, 8))
+    sp = oracle_space(w, w["levels"][-1])
+    X, Y = sp.coords()
+    u0 = inputs.burgers2d_initial(X, Y)
+    dt = inputs.cfl_dt(0.5, 1.0 / 8, 7, inputs.max_wave_speed("burgers", u0))
+    out = []
+    for tune in (False, True):
+        ctx = make_ctx(w, use_graph=1)
+        du = T(u0, dev)
+        if tune:
+            cfg = S.sisdc_autotune(ctx.ctx, du, dt, len(w["levels"]))
+            assert np.all(cfg > 0)
+            for l, lv in enumerate(ctx.levels):
+                assert tuple(cfg[l]) == S.sisdc_level_config(lv)
+            assert rel_l2(N(du), u0) == 0.0            # the state is not modified
+        for n in range(2):
+            S.sisdc_step(ctx.ctx, du, n * dt, dt, 3, S.SISDC_START_CASCADE, 1)
+        S.sisdc_sync(ctx.ctx)
+        out.append(N(du))
+        ctx.close()
+    assert rel_l2(out[1], out[0]) < 1e-13
+
+
 def test_device_error_flags(dev):
     w = CASES["burgers"]
     ctx = make_ctx(w, rtol=1e-30, maxit=2)
