@@ -120,6 +120,11 @@ typedef struct {
     double mu;          /* dynamic viscosity 1/Re (Navier-Stokes)             */
     double Pr;          /* Prandtl number (Navier-Stokes)                     */
     double rho_ref;     /* reference density of nu_d (Navier-Stokes; > 0)     */
+    int projection;     /* solution projection in space (Sec. 4.2): 0 embedded
+                           interpolation, 1 L2 projection (I^T W I)^-1 I^T W
+                           with the fine GLL quadrature                       */
+    int fmg_cycles;     /* C_fmg: V-cycles per added level of the FMG start
+                           (Algorithm 4); 0 means 1                           */
 } sisdc_problem;
 
 typedef struct {

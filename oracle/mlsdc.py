@@ -3,13 +3,14 @@
 
 * Transfers (Sec. 4.2, Sec. 6.2): space-time tensor products of the time
   transfers I_t, P_t, R_t = I_t^T and per-direction spatial p-coarsening
-  transfers I_x, P_x (embedded interpolation) and R_x.
+  transfers I_x, P_x (embedded interpolation, or the L2 projection) and R_x.
 * FAS right-hand side (Sec. 4.1, eq. ml-cm:incremental:fas-mg:rhs):
   g_l = F_l(P u_{l+1}) + R (g_{l+1} - F_{l+1}(u_{l+1})), g_L = 0.
 * V-cycle: Algorithm 2.  Reading: after the solution restriction
   v_{l-1} = P u_l the coarse iterate is set to v_{l-1} (full approximation
   scheme), so that u_l += I(u_{l-1} - v_{l-1}) interpolates a correction.
-* Starts: Algorithm 3 (Cascade), Algorithm 4 (FMG with C_fmg = 1),
+* Starts: Algorithm 3 (Cascade), Algorithm 4 (FMG with C_fmg cycles per
+  added level, default 1),
   predictor on all levels, constant spread of u_0 (Sec. 4.7).
 * One step: start, C V-cycles, optional final fine post-sweep; the new
   value is u_{L,M} (t_M = t + dt for Radau-Right and Lobatto).
@@ -19,7 +20,7 @@
 import numpy as np
 
 from .sdc import corrector, predictor, Fnn
-from .tables import time_transfers, space_transfers
+from .tables import time_transfers, space_transfers, l2_projection
 
 
 def _apply_space(mat, u, dim):
@@ -33,7 +34,7 @@ def _apply_space(mat, u, dim):
 class Transfer:
     """Transfers between a coarse level and the next finer level."""
 
-    def __init__(self, fine, coarse):
+    def __init__(self, fine, coarse, projection="interp"):
         self.fine, self.coarse = fine, coarse
         self.It, self.Pt, self.Rt = time_transfers(fine.tau, coarse.tau)
         fs, cs = fine.space, coarse.space
@@ -41,6 +42,8 @@ class Transfer:
         if self.dg:
             self.dim = fs.dim
             self.Ix, self.Px, self.Rx = space_transfers(fs.P, cs.P)
+            if projection == "l2":           # solution projection in space: L2 instead of embedded
+                self.Px = l2_projection(fs.P, cs.P)
 
     def _space(self, which, u):
         if not self.dg:
@@ -70,12 +73,13 @@ class Transfer:
 class MLSDC:
     """Levels ordered coarse (index 0, paper l = 1) to fine (index L-1)."""
 
-    def __init__(self, levels, stages=2, Nc=2):
+    def __init__(self, levels, stages=2, Nc=2, projection="interp", fmg_cycles=1):
         self.levels = list(levels)
         self.L = len(self.levels)
         self.stages = stages
         self.Nc = Nc
-        self.T = [Transfer(self.levels[l + 1], self.levels[l]) for l in range(self.L - 1)]
+        self.fmg_cycles = fmg_cycles
+        self.T = [Transfer(self.levels[l + 1], self.levels[l], projection) for l in range(self.L - 1)]
         self.sweeps = [0] * self.L
 
     def _corr(self, l, u0s, U, g, dt, n):
@@ -121,8 +125,9 @@ class MLSDC:
             if L > 1:
                 Us[1] = self.T[0].interp(Us[0])
             for l in range(1, L - 1):
-                if kind == 'fmg1':
-                    self.vcycle(u0s, Us, dt, top=l + 1)
+                if kind == 'fmg1':                    # C_fmg V-cycles per added level
+                    for _ in range(self.fmg_cycles):
+                        self.vcycle(u0s, Us, dt, top=l + 1)
                 else:
                     Us[l] = self._corr(l, u0s, Us[l], None, dt, 1)
                 Us[l + 1] = self.T[l].interp(Us[l])

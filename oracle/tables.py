@@ -178,3 +178,17 @@ def space_transfers(P_f, P_c):
     Px = lagrange_matrix(xf, xc)
     Rx = (Ix.T * wf[None, :]) / wc[:, None]
     return Ix, Px, Rx
+
+
+def l2_projection(P_f, P_c):
+    """Per-direction L2 projection of a degree-P_f element polynomial onto
+    degree P_c (the alternative solution projection of Sec. 4.2), with the
+    inner product of the fine GLL quadrature: the coarse coefficients c
+    minimise sum_k wf_k (u_k - (I_x c)_k)^2, i.e.
+    P = (I_x^T W_f I_x)^{-1} I_x^T W_f (the coarse mass here is the consistent
+    one, exact for degree 2 P_c <= 2 P_f - 1)."""
+    xf, wf = gll(P_f)
+    xc, _ = gll(P_c)
+    Ix = lagrange_matrix(xc, xf)
+    Mc = Ix.T @ (wf[:, None] * Ix)
+    return np.linalg.solve(Mc, Ix.T * wf[None, :])

@@ -425,7 +425,8 @@ void start_strategy(sisdc_ctx_s* c, LevelPtrs& P, double dt, int start) {
             L[1]->valid = false;
         }
         for (int l = 1; l < nl - 1; ++l) {
-            if (start == SISDC_START_FMG1) vcycle(c, P, l + 1, dt, c->prob.Nc);
+            if (start == SISDC_START_FMG1)                 // C_fmg V-cycles per added level
+                for (int k = 0; k < std::max(1, c->prob.fmg_cycles); ++k) vcycle(c, P, l + 1, dt, c->prob.Nc);
             else sweep(L[l], P.u0[l], P.U[l], nullptr, dt, 1);
             k_transfer(L[l + 1], T_INTERP, P.U[l], P.U[l + 1], 0);
             L[l + 1]->valid = false;
@@ -483,6 +484,8 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (!(prob->cg_rtol > 0.0) || prob->cg_maxit < 1 || prob->Nc < 0) return SISDC_E_ARG;
     if ((prob->pde == SISDC_PDE_EULER || prob->pde == SISDC_PDE_NS) && !(prob->gamma > 1.0)) return SISDC_E_ARG;
     if (prob->pde == SISDC_PDE_NS && !(prob->mu > 0.0 && prob->Pr > 0.0 && prob->rho_ref > 0.0)) return SISDC_E_ARG;
+    if (prob->projection != 0 && prob->projection != 1) return SISDC_E_ARG;
+    if (prob->fmg_cycles < 0) return SISDC_E_ARG;
     if (prob->nu < 0.0) return SISDC_E_ARG;
     sisdc_ctx_s* c = new sisdc_ctx_s();
     c->prob = *prob;
@@ -601,7 +604,9 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         const std::vector<double>& xf = lv->tab.gll;
         const std::vector<double>& xc = cl->tab.gll;
         std::vector<double> Ix = lagrange_matrix(xc, xf);   // (nqf x nqc)
-        std::vector<double> Px = lagrange_matrix(xf, xc);   // (nqc x nqf)
+        // solution projection (nqc x nqf): embedded interpolation, or the L2 projection
+        std::vector<double> Px = c->prob.projection == 1 ? l2_projection_matrix(d->P, cl->desc.P)
+                                                         : lagrange_matrix(xf, xc);
         std::vector<double> Rx(cl->nq * nq);
         for (int a = 0; a < cl->nq; ++a)
             for (int b = 0; b < nq; ++b) Rx[a * nq + b] = Ix[b * cl->nq + a] * lv->tab.w[b] / cl->tab.w[a];

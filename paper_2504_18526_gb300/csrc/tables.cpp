@@ -126,6 +126,42 @@ std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std:
     return E;
 }
 
+std::vector<double> l2_projection_matrix(int Pf, int Pc) {
+    std::vector<ld> xf, wf, xc, wc;
+    gll_ld(Pf, &xf, &wf);
+    gll_ld(Pc, &xc, &wc);
+    const int nf = Pf + 1, nc = Pc + 1;
+    std::vector<ld> I(nf * nc);                        // I[k][a] = l^c_a(xf_k)
+    for (int k = 0; k < nf; ++k)
+        for (int a = 0; a < nc; ++a) I[k * nc + a] = lagrange(xc, a, xf[k]);
+    // A = I^T W_f I (nc x nc), B = I^T W_f (nc x nf); solve A X = B
+    std::vector<ld> A(nc * nc, 0.0L), B(nc * nf, 0.0L);
+    for (int a = 0; a < nc; ++a) {
+        for (int b = 0; b < nc; ++b)
+            for (int k = 0; k < nf; ++k) A[a * nc + b] += I[k * nc + a] * wf[k] * I[k * nc + b];
+        for (int k = 0; k < nf; ++k) B[a * nf + k] = I[k * nc + a] * wf[k];
+    }
+    for (int col = 0; col < nc; ++col) {               // Gaussian elimination, partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < nc; ++r)
+            if (fabsl(A[r * nc + col]) > fabsl(A[piv * nc + col])) piv = r;
+        if (piv != col) {
+            for (int q = 0; q < nc; ++q) std::swap(A[col * nc + q], A[piv * nc + q]);
+            for (int q = 0; q < nf; ++q) std::swap(B[col * nf + q], B[piv * nf + q]);
+        }
+        for (int r = 0; r < nc; ++r) {
+            if (r == col) continue;
+            const ld f = A[r * nc + col] / A[col * nc + col];
+            for (int q = 0; q < nc; ++q) A[r * nc + q] -= f * A[col * nc + q];
+            for (int q = 0; q < nf; ++q) B[r * nf + q] -= f * B[col * nf + q];
+        }
+    }
+    std::vector<double> P(nc * nf);
+    for (int a = 0; a < nc; ++a)
+        for (int k = 0; k < nf; ++k) P[a * nf + k] = (double)(B[a * nf + k] / A[a * nc + a]);
+    return P;
+}
+
 bool build_level_tables(int P, int M, int lobatto, LevelTables* t) {
     if (P < 1 || P > 15 || M < 1 || M > 8 || (lobatto && M < 2)) return false;
     const int nq = P + 1;

@@ -15,6 +15,10 @@ bool build_level_tables(int P, int M, int lobatto, LevelTables* t);
 // E[p][j] = l_j(pts[p]) for the Lagrange basis on `nodes`.
 std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& pts);
 
+// Per-direction L2 projection from degree Pf to Pc under the fine GLL
+// quadrature: (I^T W_f I)^{-1} I^T W_f, row-major (Pc+1) x (Pf+1).
+std::vector<double> l2_projection_matrix(int Pf, int Pc);
+
 }  // namespace sisdc
 
 namespace sisdc {

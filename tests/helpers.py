@@ -24,9 +24,9 @@ def oracle_space(w, lvl, rtol=1e-14):
                    oracle_pde(w), cg_rtol=rtol, cg_maxit=10000)
 
 
-def oracle_ml(w, stages=2, Nc=2, rtol=1e-14):
+def oracle_ml(w, stages=2, Nc=2, rtol=1e-14, **kw):
     levels = [Level(oracle_space(w, lv, rtol), w["nodes"], lv["M"]) for lv in w["levels"]]
-    return MLSDC(levels, stages=stages, Nc=Nc)
+    return MLSDC(levels, stages=stages, Nc=Nc, **kw)
 
 
 def rel_l2(a, b):

@@ -342,6 +342,27 @@ def test_ns_shear_layer_full_size(dev):
     assert rel_l2(out[S.SISDC_MIXED], out[S.SISDC_FP64]) < 1e-10
 
 
+@pytest.mark.parametrize("projection,fmg_cycles", [("l2", 1), ("interp", 2), ("l2", 2)])
+def test_method_variants_parity(dev, projection, fmg_cycles):
+    """L2 solution projection and FMG with C_fmg V-cycles per added level
+    (three-level Euler vortex): V-cycle and step parity with the oracle."""
+    w = inputs.scaled("euler_vortex", nel=(5, 5))
+    sp = oracle_space(w, w["levels"][-1])
+    X, Y = sp.coords()
+    u0 = inputs.isentropic_vortex(X, Y)
+    dt = inputs.cfl_dt(0.5, 20.0 / 5, 7, inputs.max_wave_speed("euler", u0))
+    ctx = make_ctx(w, projection=projection, fmg_cycles=fmg_cycles)
+    om = oracle_ml(w, projection=projection, fmg_cycles=fmg_cycles)
+    u = u0.copy()
+    du = T(u0, dev)
+    for n in range(2):
+        u = om.step(u, dt, 2, start="fmg1")
+        S.sisdc_step(ctx.ctx, du, n * dt, dt, 2, S.SISDC_START_FMG1, 1)
+        assert rel_l2(N(du), u) < TOL, n
+    S.sisdc_sync(ctx.ctx)
+    ctx.close()
+
+
 def test_autotuned_shapes_keep_results(dev):
     """The tile-shape autotuner changes only launch shapes: steps from an
     autotuned context equal those of the default one (to rounding order)."""

@@ -127,8 +127,10 @@ def test_pde_converges_to_collocation(kind):
         assert errs[-1] < 1e-11 and errs[0] > errs[1] > errs[2]
 
 
-def test_fas_fixed_point():
-    """A V-cycle started at the collocation solution leaves it unchanged."""
+@pytest.mark.parametrize("projection", ["interp", "l2"])
+def test_fas_fixed_point(projection):
+    """A V-cycle started at the collocation solution leaves it unchanged,
+    whichever solution projection the FAS right-hand side uses."""
     mk = _tiny_problem()
     kind = "radau_right"
     fine, coarse = mk(4), mk(2)
@@ -136,7 +138,7 @@ def test_fas_fixed_point():
     u0 = np.sin(X)[None]
     dt = 0.3
     Uc = _collocation(fine, kind, 5, u0, dt)
-    ml = MLSDC([Level(coarse, kind, 3), Level(fine, kind, 5)], stages=2)
+    ml = MLSDC([Level(coarse, kind, 3), Level(fine, kind, 5)], stages=2, projection=projection)
     u0s = ml.initial_values(u0)
     Us = [np.zeros((3,) + coarse.shape), Uc.copy()]
     ml.vcycle(u0s, Us, dt)
@@ -246,3 +248,29 @@ def test_paper_wave_packet_iteration_counts(test):
     else:
         assert abs(got - ml_cycles) <= 1
     assert errm[got] < 1e-10     # converged to the collocation error, far below the start
+
+
+@pytest.mark.parametrize("projection", ["interp", "l2"])
+def test_fmg_start_with_several_cycles_converges(projection):
+    """Three levels, FMG start with C_fmg = 2 V-cycles per added level: the
+    step converges to the fine collocation solution as cycles are added, and
+    C_fmg = 2 starts closer than C_fmg = 1."""
+    mk = _tiny_problem()
+    kind = "radau_right"
+    fine = mk(5)
+    X, _ = fine.coords()
+    u0 = np.sin(X)[None]
+    dt = 0.3
+    Uc = _collocation(fine, kind, 5, u0, dt)
+    errs = {}
+    for C in (1, 2):
+        ml = MLSDC([Level(mk(2), kind, 2), Level(mk(3), kind, 3), Level(fine, kind, 5)], stages=2,
+                   projection=projection, fmg_cycles=C)
+        u0s = ml.initial_values(u0)
+        Us = ml.start(u0s, dt, "fmg1")
+        errs[C] = [np.max(np.abs(Us[-1] - Uc))]
+        for _ in range(30):
+            Us = ml.vcycle(u0s, Us, dt)
+            errs[C].append(np.max(np.abs(Us[-1] - Uc)))
+    assert errs[2][0] < errs[1][0]
+    assert errs[1][-1] < 1e-9 and errs[2][-1] < 1e-9

@@ -138,3 +138,22 @@ def test_level_cost_model_matches_printed_table():
     printed = float(rows["three_level_1D_Nc2_fine_ops"][0])
     assert abs(1 + Nc * (0.36 + 0.11) - printed) < 1e-12
     assert abs(1 + Nc * (c2 + c1) - printed) < 0.02
+
+
+@pytest.mark.parametrize("Pf,Pc", [(7, 3), (5, 3), (4, 2), (8, 4)])
+def test_l2_projection(Pf, Pc):
+    """The L2 solution projection is a projection (P I = identity), is the
+    weighted least-squares fit under the fine GLL quadrature (checked against
+    numpy's lstsq) and conserves the integral against the consistent coarse
+    mass."""
+    from oracle.tables import l2_projection, space_transfers
+    P = l2_projection(Pf, Pc)
+    Ix, _, _ = space_transfers(Pf, Pc)
+    assert np.max(np.abs(P @ Ix - np.eye(Pc + 1))) < 1e-13
+    xf, wf = T.gll(Pf)
+    u = np.random.default_rng(Pf * 10 + Pc).standard_normal(Pf + 1)
+    sw = np.sqrt(wf)
+    c_ls = np.linalg.lstsq(sw[:, None] * Ix, sw * u, rcond=None)[0]
+    assert np.max(np.abs(P @ u - c_ls)) < 1e-12
+    ones = np.ones(Pf + 1)
+    assert abs(ones @ (wf * (Ix @ (P @ u))) - wf @ u) < 1e-13
