@@ -650,6 +650,55 @@ def ensemble_arm(args):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# stability map of the Dahlquist problem (one GPU thread per point)
+# ---------------------------------------------------------------------------
+def stability_arm(args):
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import sisdc as S
+    from paper_2504_18526_gb300.build import build
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build()
+    S.load()
+    nx = ny = 1024
+    zr = torch.linspace(-40.0, 5.0, nx, dtype=torch.float64, device=dev)
+    zi = torch.linspace(-40.0, 40.0, ny, dtype=torch.float64, device=dev)
+    z = (zr[None, :] + 1j * zi[:, None]).reshape(-1)
+    cfg = dict(Ms=[3, 5, 7], nodes="radau_right", stages=2, ncycles=3, start="fmg1")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        S.sisdc_stability(z, stream=stream.cuda_stream, **cfg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        R = S.sisdc_stability(z, stream=stream.cuda_stream, **cfg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stable = float((R.abs() <= 1.0 + 1e-12).double().mean())
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle.dahlquist import stability
+        pts = z[:: max(1, z.numel() // 400)].cpu().numpy()
+        t0 = time.perf_counter()
+        for p in pts:
+            stability(complex(p), cfg["Ms"], cfg["nodes"], cfg["stages"], cfg["ncycles"], cfg["start"])
+        el = time.perf_counter() - t0
+        cpu = {"value": len(pts) / el, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": "%d points of the same map by the numpy oracle, %.1f s" % (len(pts), el)}
+    print(json.dumps({"metric": "stability-map points/s", "value": z.numel() * args.steps / (ms * 1e-3),
+                      "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "stability_map", "grid": [nx, ny], "box": [[-40, 5], [-40, 40]],
+                                 "method": cfg, "stable_fraction": stable},
+                      "cpu_baseline": cpu}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.oracle_sample:
@@ -661,5 +710,7 @@ if __name__ == "__main__":
         reference_arm(a)
     elif a.workload == "ensemble512":
         ensemble_arm(a)
+    elif a.workload == "stability_map":
+        stability_arm(a)
     else:
         main_arm(a)

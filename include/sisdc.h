@@ -420,6 +420,29 @@ sisdc_status sisdc_ens_get_stats(sisdc_ens ens, sisdc_stats* out, long long* h_i
 sisdc_status sisdc_ens_reset_stats(sisdc_ens ens);
 const char* sisdc_ens_last_error(sisdc_ens ens);
 
+/* --- stability function on the Dahlquist problem (Sec. 5) -----------------
+ *
+ * R(z) of one SI-MLSDC step for u' = z u with the semi-implicit split of the
+ * Fourier-mode problem (Sec. 5): Im(z) convective (explicit), Re(z) diffusive
+ * (implicit, nu_d = -Re(z)), nu_tilde = -Re(z) + dt_m/2 Im(z)^2, dt = 1,
+ * u(0) = 1.  Levels coarsen in time only (node counts M[0] <= ... , coarse
+ * to fine).  One GPU thread per point. */
+typedef struct {
+    int nlevels;         /* 1..4                                               */
+    int M[4];            /* collocation nodes per level, coarse to fine        */
+    sisdc_nodes nodes;
+    int si_stages;       /* 1 or 2                                             */
+    int ncycles;         /* V-cycles (one level: correction sweeps)            */
+    int start;           /* sisdc_start                                        */
+    int post_sweep;
+    int Nc;              /* coarse sweeps per V-cycle                          */
+    int fmg_cycles;      /* C_fmg of the FMG start (0 means 1)                 */
+} sisdc_stab_opts;
+/* d_z: [n][2] (Re, Im) device array; d_R: [n][2] receives R(z).
+ * Asynchronous on `cuda_stream` (a cudaStream_t; NULL = legacy stream). */
+sisdc_status sisdc_stability(const sisdc_stab_opts* opts, const double* d_z, double* d_R, long long n,
+                             void* cuda_stream);
+
 /* Message of the last failing call on this context ("" if none). */
 const char* sisdc_last_error(sisdc_ctx ctx);
 

@@ -37,10 +37,10 @@ class DahlquistSpace:
 
 
 def stability(z, Ms, node_kind='radau_right', stages=2, ncycles=1, start='predictor',
-              post_sweep=True, Nc=2):
+              post_sweep=True, Nc=2, fmg_cycles=1):
     """R(z) of one SI-MLSDC step (levels with node counts Ms, coarse first)."""
     sp = DahlquistSpace(z)
     levels = [Level(sp, node_kind, M) for M in Ms]
-    ml = MLSDC(levels, stages=stages, Nc=Nc)
+    ml = MLSDC(levels, stages=stages, Nc=Nc, fmg_cycles=fmg_cycles)
     u1 = ml.step(np.complex128(1.0), 1.0, ncycles, start=start, post_sweep=post_sweep)
     return complex(u1)

@@ -53,6 +53,11 @@ class sisdc_ens_opts(ctypes.Structure):
                 ("post_sweep", c_int), ("use_graph", c_int)]
 
 
+class sisdc_stab_opts(ctypes.Structure):
+    _fields_ = [("nlevels", c_int), ("M", c_int * 4), ("nodes", c_int), ("si_stages", c_int), ("ncycles", c_int),
+                ("start", c_int), ("post_sweep", c_int), ("Nc", c_int), ("fmg_cycles", c_int)]
+
+
 class SisdcError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -117,6 +122,7 @@ def load():
                                         c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
         "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll), P(c_ll)]),
         "sisdc_autotune": (c_int, [c_void_p, c_void_p, c_double, c_int, c_void_p]),
+        "sisdc_stability": (c_int, [P(sisdc_stab_opts), c_void_p, c_void_p, c_ll, c_void_p]),
         "sisdc_level_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
         "sisdc_ens_create": (c_int, [P(sisdc_ens_instance), c_int, P(sisdc_ens_opts), c_void_p, P(c_void_p)]),
         "sisdc_ens_destroy": (None, [c_void_p]),
@@ -348,6 +354,25 @@ def sisdc_autotune(ctx, u, dt, nlevels, reps=2):
     cfg = np.zeros(3 * nlevels, dtype=np.int32)
     _check(load().sisdc_autotune(ctx, _ptr(u), dt, reps, cfg.ctypes.data), ctx)
     return cfg.reshape(nlevels, 3)
+
+
+def sisdc_stability(z, Ms, nodes="radau_right", stages=2, ncycles=1, start="predictor", post_sweep=True, Nc=2,
+                    fmg_cycles=1, stream=0):
+    """R(z) of one SI-MLSDC step on the Dahlquist problem for a complex torch
+    tensor z (on the GPU); returns a complex128 tensor."""
+    import torch
+    o = sisdc_stab_opts()
+    o.nlevels = len(Ms)
+    for k, M in enumerate(Ms):
+        o.M[k] = M
+    o.nodes, o.si_stages, o.ncycles = NODE_IDS[nodes], stages, ncycles
+    o.start, o.post_sweep, o.Nc, o.fmg_cycles = START_IDS[start], 1 if post_sweep else 0, Nc, fmg_cycles
+    zr = torch.view_as_real(z.to(torch.complex128).contiguous()).contiguous()
+    R = torch.empty_like(zr)
+    st = load().sisdc_stability(ctypes.byref(o), zr.data_ptr(), R.data_ptr(), zr.shape[0], c_void_p(stream))
+    if st != SISDC_OK:
+        raise SisdcError(st, "sisdc_stability")
+    return torch.view_as_complex(R)
 
 
 def sisdc_level_config(lv):

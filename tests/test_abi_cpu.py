@@ -34,11 +34,12 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sisdc.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sisdc_level_desc),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu ", sizeof(sisdc_level_desc),'
         ' sizeof(sisdc_problem), sizeof(sisdc_stats), offsetof(sisdc_level_desc, lo),'
         ' offsetof(sisdc_problem, cg_rtol), offsetof(sisdc_stats, launches),'
         ' sizeof(sisdc_ens_instance), offsetof(sisdc_ens_instance, dt), sizeof(sisdc_ens_opts),'
-        ' offsetof(sisdc_ens_opts, cg_rtol)); return 0;}\n')
+        ' offsetof(sisdc_ens_opts, cg_rtol)); printf("%zu %zu\\n", sizeof(sisdc_stab_opts),'
+        ' offsetof(sisdc_stab_opts, fmg_cycles)); return 0;}\n')
     exe = tmp_path / "layout"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
@@ -48,7 +49,8 @@ def test_struct_layouts_match_header(tmp_path):
                     ctypes.sizeof(sisdc.sisdc_stats), sisdc.sisdc_level_desc.lo.offset,
                     sisdc.sisdc_problem.cg_rtol.offset, sisdc.sisdc_stats.launches.offset,
                     ctypes.sizeof(sisdc.sisdc_ens_instance), sisdc.sisdc_ens_instance.dt.offset,
-                    ctypes.sizeof(sisdc.sisdc_ens_opts), sisdc.sisdc_ens_opts.cg_rtol.offset]
+                    ctypes.sizeof(sisdc.sisdc_ens_opts), sisdc.sisdc_ens_opts.cg_rtol.offset,
+                    ctypes.sizeof(sisdc.sisdc_stab_opts), sisdc.sisdc_stab_opts.fmg_cycles.offset]
 
 
 def test_invalid_problem_rejected_without_gpu(lib):
