@@ -125,6 +125,10 @@ typedef struct {
                            with the fine GLL quadrature                       */
     int fmg_cycles;     /* C_fmg: V-cycles per added level of the FMG start
                            (Algorithm 4); 0 means 1                           */
+    int form;           /* 0: incremental (node-to-node) MLSDC; 1: the
+                           non-incremental (zero-to-node) MLSDC of Sec. 4.5,
+                           whose FAS right-hand side is built from F^0n
+                           residuals (single-level sweeps are the same)       */
 } sisdc_problem;
 
 typedef struct {

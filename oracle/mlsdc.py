@@ -19,7 +19,7 @@
 """
 import numpy as np
 
-from .sdc import corrector, predictor, Fnn
+from .sdc import corrector, corrector_0n, predictor, Fnn, F0n
 from .tables import time_transfers, space_transfers, l2_projection
 
 
@@ -73,17 +73,21 @@ class Transfer:
 class MLSDC:
     """Levels ordered coarse (index 0, paper l = 1) to fine (index L-1)."""
 
-    def __init__(self, levels, stages=2, Nc=2, projection="interp", fmg_cycles=1):
+    def __init__(self, levels, stages=2, Nc=2, projection="interp", fmg_cycles=1, form="incremental"):
         self.levels = list(levels)
         self.L = len(self.levels)
         self.stages = stages
         self.Nc = Nc
         self.fmg_cycles = fmg_cycles
+        self.form = form            # "incremental" (node-to-node) or "zero_to_node"
+        self.F = F0n if form == "zero_to_node" else Fnn
         self.T = [Transfer(self.levels[l + 1], self.levels[l], projection) for l in range(self.L - 1)]
         self.sweeps = [0] * self.L
 
     def _corr(self, l, u0s, U, g, dt, n):
         self.sweeps[l] += n
+        if self.form == "zero_to_node":
+            return corrector_0n(self.levels[l], u0s[l], U, g, dt, self.stages, n)
         return corrector(self.levels[l], u0s[l], U, g, dt, self.stages, n)
 
     def initial_values(self, u0):
@@ -101,12 +105,12 @@ class MLSDC:
         v = [None] * top
         for l in range(top - 1, 0, -1):
             Us[l] = self._corr(l, u0s, Us[l], g[l], dt, 1)              # pre-sweep
-            r = -Fnn(self.levels[l], u0s[l], Us[l], dt)                   # residual
+            r = -self.F(self.levels[l], u0s[l], Us[l], dt)                # residual (F^nn or F^0n)
             if g[l] is not None:
                 r = r + g[l]
             T = self.T[l - 1]
             v[l - 1] = T.project(Us[l])                                   # solution restriction
-            g[l - 1] = Fnn(self.levels[l - 1], u0s[l - 1], v[l - 1], dt) + T.restrict(r)
+            g[l - 1] = self.F(self.levels[l - 1], u0s[l - 1], v[l - 1], dt) + T.restrict(r)
             Us[l - 1] = v[l - 1].copy()
         Us[0] = self._corr(0, u0s, Us[0], g[0], dt, Nc)                  # coarse solve
         for l in range(1, top):

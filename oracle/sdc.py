@@ -27,7 +27,7 @@ iterate (the CUDA path caches them, Sec. 3.3 implementation remark).
 """
 import numpy as np
 
-from .tables import collocation_nodes, wnn, substeps
+from .tables import collocation_nodes, wnn, substeps, c0n
 
 
 class Level:
@@ -37,6 +37,7 @@ class Level:
         self.node_kind = node_kind
         self.tau = collocation_nodes(node_kind, M)
         self.Wnn = wnn(self.tau)
+        self.W0n = c0n(self.M) @ self.Wnn          # zero-to-node weights (eq. 0n_weights)
         self.dtau = substeps(self.tau)
 
 
@@ -110,6 +111,58 @@ def corrector(level, u0, U, g, dt, stages, nsweeps):
                 old2 = dtm * (sp.conv(Uold[m]) + nu_old * LUold)
                 x1 = sp.solve(dtm * nu_new, base + dtm * sp.conv(x1) - old2, x1)
             Unew[m] = x1
+            unew_prev = Unew[m]
+        U = Unew
+    return U
+
+
+# --------------------------------------------------------------------------
+# Non-incremental (zero-to-node) form (Sec. 3.2 "Non-incremental SDC method",
+# Sec. 4.5 "Non-incremental multilevel SDC method")
+# --------------------------------------------------------------------------
+def F0n(level, u0, U, dt):
+    """F^0n_m(U) = U_m - u_0 - dt sum_i w^0n_{m,i} f(U_i)."""
+    sp = level.space
+    F = np.stack([f_eval(sp, U[i]) for i in range(level.M)])
+    return U - u0[None] - dt * np.tensordot(level.W0n, F, axes=(1, 0))
+
+
+def corrector_0n(level, u0, U, g, dt, stages, nsweeps):
+    """``nsweeps`` non-incremental SI sweeps: u^k_m = u_0 + dt sum_i w^0n_{m,i}
+    f(u^{k-1}_i) + g_m + sum_{i<=m} Delta H^k_i, with the same deltas as the
+    incremental sweep, summed over the current and all preceding nodes (g is
+    the zero-to-node FAS right-hand side)."""
+    sp = level.space
+    for _ in range(nsweeps):
+        Uold = np.array(U, copy=True)
+        Q0 = dt * np.tensordot(level.W0n, np.stack([f_eval(sp, Uold[i]) for i in range(level.M)]), axes=(1, 0))
+        Unew = np.empty_like(Uold)
+        dH = np.zeros_like(u0)                     # sum of the deltas of the preceding nodes
+        unew_prev = u0
+        for m in range(level.M):
+            dtm = dt * level.dtau[m]
+            uold_prev = u0 if m == 0 else Uold[m - 1]
+            base = u0 + Q0[m] + dH
+            if g is not None:
+                base = base + g[m]
+            if dtm == 0.0:
+                Unew[m] = base
+                unew_prev = Unew[m]
+                continue
+            nu_new = nutilde(sp, unew_prev, dtm)
+            nu_old = nutilde(sp, uold_prev, dtm)
+            LUold = sp.lap(Uold[m])
+            old1 = dtm * (sp.conv(uold_prev) + nu_old * LUold)
+            new_expl = dtm * sp.conv(unew_prev)
+            x1 = sp.solve(dtm * nu_new, base + new_expl - old1, Uold[m])
+            delta = new_expl + dtm * nu_new * sp.lap(x1) - old1
+            if stages == 2:
+                old2 = dtm * (sp.conv(Uold[m]) + nu_old * LUold)
+                new_expl = dtm * sp.conv(x1)
+                x1 = sp.solve(dtm * nu_new, base + new_expl - old2, x1)
+                delta = new_expl + dtm * nu_new * sp.lap(x1) - old2
+            Unew[m] = x1
+            dH = dH + delta
             unew_prev = Unew[m]
         U = Unew
     return U

@@ -486,6 +486,7 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (prob->pde == SISDC_PDE_NS && !(prob->mu > 0.0 && prob->Pr > 0.0 && prob->rho_ref > 0.0)) return SISDC_E_ARG;
     if (prob->projection != 0 && prob->projection != 1) return SISDC_E_ARG;
     if (prob->fmg_cycles < 0) return SISDC_E_ARG;
+    if (prob->form != 0 && prob->form != 1) return SISDC_E_ARG;
     if (prob->nu < 0.0) return SISDC_E_ARG;
     sisdc_ctx_s* c = new sisdc_ctx_s();
     c->prob = *prob;
@@ -615,6 +616,22 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         std::vector<double> Rt(cl->M * lv->M);
         for (int a = 0; a < cl->M; ++a)
             for (int b = 0; b < lv->M; ++b) Rt[a * lv->M + b] = It[b * cl->M + a];
+        if (c->prob.form == 1) {
+            // zero-to-node form (Sec. 4.5): the levels solve F^0n(u) = g^0n + C^0n dH with
+            // F^0n = C^0n F^nn, i.e. the incremental equations with g^nn = (C^0n)^-1 g^0n;
+            // the FAS restriction of the residual becomes (C_c^0n)^-1 R_t C_f^0n
+            const int Mf = lv->M, Mc = cl->M;
+            std::vector<double> RC(Mc * Mf);                    // R_t C_f: suffix sums over the fine index
+            for (int a = 0; a < Mc; ++a) {
+                double s = 0.0;
+                for (int b = Mf - 1; b >= 0; --b) {
+                    s += Rt[a * Mf + b];
+                    RC[a * Mf + b] = s;
+                }
+            }
+            for (int a = Mc - 1; a >= 0; --a)                   // (C_c)^-1: first differences over a
+                for (int b = 0; b < Mf; ++b) Rt[a * Mf + b] = RC[a * Mf + b] - (a > 0 ? RC[(a - 1) * Mf + b] : 0.0);
+        }
         auto push = [&](const std::vector<double>& v) { size_t o = ttab.size(); ttab.insert(ttab.end(), v.begin(), v.end()); return o; };
         off_Ix = push(Ix); off_Px = push(Px); off_Rx = push(Rx);
         off_It = push(It); off_Pt = push(Pt); off_Rt = push(Rt);

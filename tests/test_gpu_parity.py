@@ -342,17 +342,21 @@ def test_ns_shear_layer_full_size(dev):
     assert rel_l2(out[S.SISDC_MIXED], out[S.SISDC_FP64]) < 1e-10
 
 
-@pytest.mark.parametrize("projection,fmg_cycles", [("l2", 1), ("interp", 2), ("l2", 2)])
-def test_method_variants_parity(dev, projection, fmg_cycles):
-    """L2 solution projection and FMG with C_fmg V-cycles per added level
-    (three-level Euler vortex): V-cycle and step parity with the oracle."""
+@pytest.mark.parametrize("projection,fmg_cycles,form", [("l2", 1, "incremental"), ("interp", 2, "incremental"),
+                                                        ("l2", 2, "incremental"), ("interp", 1, "zero_to_node"),
+                                                        ("l2", 2, "zero_to_node")])
+def test_method_variants_parity(dev, projection, fmg_cycles, form):
+    """L2 solution projection, FMG with C_fmg V-cycles per added level and the
+    non-incremental multilevel form (three-level Euler vortex): step parity
+    with the oracle, which runs the zero-to-node sweeps and F^0n residuals
+    literally while the library uses the equivalent modified restriction."""
     w = inputs.scaled("euler_vortex", nel=(5, 5))
     sp = oracle_space(w, w["levels"][-1])
     X, Y = sp.coords()
     u0 = inputs.isentropic_vortex(X, Y)
     dt = inputs.cfl_dt(0.5, 20.0 / 5, 7, inputs.max_wave_speed("euler", u0))
-    ctx = make_ctx(w, projection=projection, fmg_cycles=fmg_cycles)
-    om = oracle_ml(w, projection=projection, fmg_cycles=fmg_cycles)
+    ctx = make_ctx(w, projection=projection, fmg_cycles=fmg_cycles, form=form)
+    om = oracle_ml(w, projection=projection, fmg_cycles=fmg_cycles, form=form)
     u = u0.copy()
     du = T(u0, dev)
     for n in range(2):

@@ -274,3 +274,42 @@ def test_fmg_start_with_several_cycles_converges(projection):
             errs[C].append(np.max(np.abs(Us[-1] - Uc)))
     assert errs[2][0] < errs[1][0]
     assert errs[1][-1] < 1e-9 and errs[2][-1] < 1e-9
+
+
+def test_non_incremental_sdc_equals_incremental_single_level():
+    """Single level: the zero-to-node sweeps give the incremental iterates
+    (the same deltas summed over the preceding nodes)."""
+    mk = _tiny_problem()
+    fine = mk(4)
+    X, _ = fine.coords()
+    u0 = np.sin(X)[None]
+    for kind in ("radau_right", "lobatto"):
+        for stages in (1, 2):
+            L = Level(fine, kind, 5)
+            U = S.predictor(L, u0, 0.3, stages)
+            a = S.corrector(L, u0, U, None, 0.3, stages, 3)
+            b = S.corrector_0n(L, u0, U, None, 0.3, stages, 3)
+            assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_non_incremental_mlsdc_converges_and_differs():
+    """Two levels: the zero-to-node MLSDC has the collocation solution as its
+    FAS fixed point and converges to it, but its iterates differ from the
+    incremental MLSDC (the forms are not equivalent, Sec. 4.6)."""
+    mk = _tiny_problem()
+    kind = "radau_right"
+    fine = mk(4)
+    X, _ = fine.coords()
+    u0 = np.sin(X)[None]
+    dt = 0.3
+    Uc = _collocation(fine, kind, 5, u0, dt)
+    ml = {f: MLSDC([Level(mk(2), kind, 3), Level(fine, kind, 5)], stages=2, form=f)
+          for f in ("incremental", "zero_to_node")}
+    u0s = ml["zero_to_node"].initial_values(u0)
+    Us = [np.zeros((3,) + mk(2).shape), Uc.copy()]
+    ml["zero_to_node"].vcycle(u0s, Us, dt)
+    assert np.max(np.abs(Us[-1] - Uc)) < 1e-13
+    one = {f: ml[f].step(u0, dt, 1, start="predictor") for f in ml}
+    assert np.max(np.abs(one["zero_to_node"] - one["incremental"])) > 1e-8
+    conv = ml["zero_to_node"].step(u0, dt, 40, start="predictor")
+    assert np.max(np.abs(conv - Uc[-1])) < 1e-10
