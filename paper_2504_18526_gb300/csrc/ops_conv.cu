@@ -81,7 +81,7 @@ __global__ void k_conv(const ConvArgs a) {
             cv[c] -= sy * s;
         }
     }
-    const int ex = (int)(e % g.nex), ey = (int)(e / g.nex);
+    const int ei = (int)e, ey = ei / g.nex, ex = ei - ey * g.nex;
     double un[NC], Fs[NC];
     if (i == NQ - 1) {         // right face: own state left, neighbour right
         const long long en = (long long)ey * g.nex + (ex + 1) % g.nex;

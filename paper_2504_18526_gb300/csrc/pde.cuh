@@ -125,4 +125,31 @@ __device__ __forceinline__ void rusanov(const PP& a, const T* uL, const T* uR, T
     for (int c = 0; c < P::NC; ++c) Fs[c] = T(0.5) * (FL[c] + FR[c]) - T(0.5) * lam * (uR[c] - uL[c]);
 }
 
+// Rusanov flux minus the normal flux of the own state, Fs - F(uo), at a face
+// node shared with the neighbour state un; own_left: the own state is the
+// left/lower one.  Same flux as rusanov(), without forming Fs itself.
+template <int PDE, bool XDIR, class T, class PP>
+__device__ __forceinline__ void rusanov_jump(const PP& a, const T* uo, const T* un, bool own_left, T* d) {
+    using P = Pde<PDE>;
+    T Fo[P::NC], Fn[P::NC];
+    T lo, ln;
+    if (XDIR) {
+        P::fx(a, uo, Fo);
+        P::fx(a, un, Fn);
+        lo = P::rx(a, uo);
+        ln = P::rx(a, un);
+    } else {
+        P::fy(a, uo, Fo);
+        P::fy(a, un, Fn);
+        lo = P::ry(a, uo);
+        ln = P::ry(a, un);
+    }
+    const T hl = T(0.5) * fmax(lo, ln);
+#pragma unroll
+    for (int c = 0; c < P::NC; ++c) {
+        const T du = own_left ? un[c] - uo[c] : uo[c] - un[c];    // uR - uL
+        d[c] = T(0.5) * (Fn[c] - Fo[c]) - hl * du;
+    }
+}
+
 }  // namespace sisdc

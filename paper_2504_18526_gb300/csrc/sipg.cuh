@@ -60,4 +60,71 @@ __device__ __forceinline__ void sipg_face(const GG& g, const V* vo, const V* vn,
     }
 }
 
+// Pre-scaled form of sipg_opA for a uniform grid.  The quadrature weights,
+// metric factors (2/h, 1/h, h/2) and penalties are folded into one
+// coefficient per product, so (A u)(i, j) is a plain sum of products with
+// no branches.  cf points at the node's first coefficient and consecutive
+// coefficients of a node lie Q apart (layout [coefficient][node]):
+//   [0, NQ)            x-direction stiffness row, against u(k, j)
+//   [NQ, 2NQ)          y-direction stiffness row, against u(i, k) (2D)
+//   DIM*NQ + [0, 4)    x faces: left jump, left average, right jump, right average
+//   DIM*NQ + [4, 8)    y faces, same order (2D)
+// sipg_opA_coeff gives the coefficient values.
+template <int NQ, int DIM, class V>
+__device__ __forceinline__ V sipg_opA_pre(int i, int j, const V* u, const V* f, const V* cf) {
+    constexpr int Q = DIM == 2 ? NQ * NQ : NQ;
+    const V* cx = cf + DIM * NQ * Q;
+    V ax = V(0);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) ax += cf[k * Q] * u[j * NQ + k];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) ax += cx[s * Q] * f[s * NQ + j];
+    if constexpr (DIM == 1) {
+        return ax;
+    } else {
+        V ay = V(0);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) ay += cf[(NQ + k) * Q] * u[k * NQ + i];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) ay += cx[(4 + s) * Q] * f[(4 + s) * NQ + i];
+        return ax + ay;
+    }
+}
+
+// coefficient k of node (i, j) of sipg_opA_pre (FP64; D, K, w as in sipg_opA)
+template <int NQ, int DIM, class GG>
+__device__ __forceinline__ double sipg_opA_coeff(const GG& g, const double* D, const double* K, const double* w,
+                                                 int k, int i, int j) {
+    const double wy = DIM == 2 ? 0.5 * g.hy * w[j] : 1.0;
+    const double wx = 0.5 * g.hx * w[i];
+    if (k < NQ) return wy * g.sx * K[i * NQ + k];
+    if (DIM == 2 && k < 2 * NQ) return wx * g.sy * K[j * NQ + (k - NQ)];
+    const int r = k - DIM * NQ;
+    const bool xd = r < 4;
+    const int a = xd ? i : j, s = r & 3;
+    const double wgt = xd ? wy : wx, ih = xd ? g.ihx : g.ihy, tau = xd ? g.taux : g.tauy;
+    if (s == 0) return wgt * (-ih * D[a] - (a == 0 ? tau : 0.0));
+    if (s == 1) return a == 0 ? wgt : 0.0;
+    if (s == 2) return wgt * (-ih * D[(NQ - 1) * NQ + a] + (a == NQ - 1 ? tau : 0.0));
+    return a == NQ - 1 ? -wgt : 0.0;
+}
+
+// sipg_face with half-scaled end rows: Dh[f][q] = (s/2) D[end(f)][q], s the
+// 2/h factor of face f's direction and end(f) the node of face f (0 or NQ-1)
+template <int NQ, class V>
+__device__ __forceinline__ void sipg_face_pre(const V* vo, const V* vn, int f, const V* Dh, V& jump, V& avg) {
+    const V* ro = Dh + f * NQ;
+    const V* rn = Dh + (f ^ 1) * NQ;
+    V od = V(0), nd = V(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        od += ro[q] * vo[q];
+        nd += rn[q] * vn[q];
+    }
+    const int end = (f & 1) ? NQ - 1 : 0;
+    const V ov = vo[end], nv = vn[NQ - 1 - end];
+    jump = (f & 1) ? ov - nv : nv - ov;
+    avg = od + nd;
+}
+
 }  // namespace sisdc

@@ -47,6 +47,8 @@ struct Sweeper {
     static constexpr int Q = NQ * NQY;
     static constexpr int NF = 2 * DIM;
     static constexpr int TRS = NF * 2 * NQ;
+    static constexpr int NCO = DIM * NQ + 4 * DIM;   // coefficients per node of the pre-scaled operator
+    static constexpr int NTAB = NCO * Q + 4 * NQ;     // pre-scaled operator and face tables
     // arithmetic of the explicit operator evaluations (c(u), L u): FP64, or
     // double-single on the FP32 pipe in the mixed form of the scalar
     // convection-diffusion and Burgers PDEs
@@ -59,11 +61,11 @@ struct Sweeper {
     };
 
     static size_t smem_bytes(int epb) {
-        const size_t d = 2 * NQ * NQ + 3 * NQ + 32 + 2 * (MMAX + 1) + Q      // tables, scratch, lam, dinv
-                         + (size_t)epb * NC * Q + (size_t)epb * NC * TRS;    // FP64 tile + faces
-        const size_t d2 = d + (size_t)epb * 2 * NC * Q;                     // FP64 fluxes
-        size_t r = MIX ? (2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q + (size_t)epb * NC * TRS +
-                          (size_t)epb * 2 * NC * Q)                            // RT tables, tile, faces, fluxes
+        const size_t d = NTAB + 2 * NQ * NQ + 3 * NQ + 32 + 2 * (MMAX + 1) + Q   // tables, scratch, lam, dinv
+                         + (size_t)epb * NC * Q + (size_t)epb * NC * TRS;         // FP64 tile + faces
+        const size_t d2 = d + (size_t)epb * 2 * NC * Q;                          // FP64 fluxes
+        size_t r = MIX ? (NTAB + 2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q + (size_t)epb * NC * TRS +
+                          (size_t)epb * 2 * NC * Q)                                 // RT tables, tile, faces, fluxes
                        : 0;
         const size_t x = EXDS ? (2 * NQ * NQ + NQ + 16 + 4) : 0;          // double-single tables, geometry, params
         return d2 * sizeof(double) + r * sizeof(RT) + x * sizeof(dsf) + 16;
@@ -76,11 +78,11 @@ struct Sweeper {
     GeoDS* xg;                     // geometry factors in double-single (shared memory)
     dsf *xD, *xK, *xw;             // D, K, w in double-single (shared memory)
     dsf imass_ds;                  // 1 / mass of the thread's node
-    double *sD, *sK, *sw, *sdx, *sdy, *scratch, *slam_old, *slam_new, *sdinv, *su, *sf, *sF64;
-    RT *rD, *rK, *rw, *rdx, *rdy, *rdinv, *ru, *rf, *sFR;
+    double *sA, *sDh, *sD, *sK, *sw, *sdx, *sdy, *scratch, *slam_old, *slam_new, *sdinv, *su, *sf, *sF64;
+    RT *rA, *rDh, *rD, *rK, *rw, *rdx, *rdy, *rdinv, *ru, *rf, *sFR;
     int epb, le, node, i, j, G;
     long long ntiles, N, NV;
-    double mass, diagA;
+    double mass, imass, diagA;
     int solve_parity;
     int log_base, log_n;                  // solve-log slot of the next solve
 
@@ -103,7 +105,9 @@ struct Sweeper {
         extern __shared__ double sm[];
         pp = PdeParams{a.gamma, a.ax, a.ay};
         epb = a.epb;
-        sD = sm;
+        sA = sm;                              // [NCO][Q] pre-scaled operator coefficients
+        sDh = sA + NCO * Q;                   // [4][NQ] half-scaled face rows
+        sD = sDh + 4 * NQ;
         sK = sD + NQ * NQ;
         sw = sK + NQ * NQ;
         sdx = sw + NQ;
@@ -117,7 +121,9 @@ struct Sweeper {
         sF64 = sf + epb * NC * TRS;           // [epb][2][NC][Q] FP64 fluxes
         RT* rbase = reinterpret_cast<RT*>(sF64 + epb * 2 * NC * Q);
         if (MIX) {
-            rD = rbase;
+            rA = rbase;
+            rDh = rA + NCO * Q;
+            rD = rDh + 4 * NQ;
             rK = rD + NQ * NQ;
             rw = rK + NQ * NQ;
             rdx = rw + NQ;
@@ -127,6 +133,8 @@ struct Sweeper {
             rf = ru + epb * NC * Q;
             sFR = rf + epb * NC * TRS;
         } else {
+            rA = reinterpret_cast<RT*>(sA);
+            rDh = reinterpret_cast<RT*>(sDh);
             rD = reinterpret_cast<RT*>(sD);
             rK = reinterpret_cast<RT*>(sK);
             rw = reinterpret_cast<RT*>(sw);
@@ -138,8 +146,8 @@ struct Sweeper {
             sFR = reinterpret_cast<RT*>(sF64);
         }
         if constexpr (EXDS) {
-            const size_t rcount = 2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q + (size_t)epb * NC * TRS +
-                                  (size_t)epb * 2 * NC * Q;
+            const size_t rcount = NTAB + 2 * NQ * NQ + 3 * NQ + Q + (size_t)epb * NC * Q +
+                                  (size_t)epb * NC * TRS + (size_t)epb * 2 * NC * Q;
             xD = reinterpret_cast<dsf*>(rbase + ((rcount + 1) & ~size_t(1)));
             xK = xD + NQ * NQ;
             xw = xK + NQ * NQ;
@@ -174,6 +182,18 @@ struct Sweeper {
             }
             if constexpr (EXDS) xw[t] = dsf(g.w[t]);
         }
+        for (int t = threadIdx.x; t < NCO * Q; t += blockDim.x) {
+            const int k = t / Q, nd = t - k * Q;
+            const double v = sipg_opA_coeff<NQ, DIM>(g, g.D, g.K, g.w, k, nd % NQ, nd / NQ);
+            sA[t] = v;
+            if (MIX) rA[t] = (RT)v;
+        }
+        for (int t = threadIdx.x; t < 4 * NQ; t += blockDim.x) {
+            const int f = t / NQ, q = t - f * NQ;
+            const double v = 0.5 * (f < 2 ? g.sx : g.sy) * g.D[((f & 1) ? NQ - 1 : 0) * NQ + q];
+            sDh[t] = v;
+            if (MIX) rDh[t] = (RT)v;
+        }
         for (int t = threadIdx.x; t <= MMAX; t += blockDim.x) {
             slam_old[t] = __ldcg(a.lam + t);
             slam_new[t] = __ldcg(a.lam + MMAX + 1 + t);
@@ -191,7 +211,8 @@ struct Sweeper {
         log_n = 0;
         __syncthreads();
         mass_diag(i, j, mass, diagA);
-        if constexpr (EXDS) imass_ds = dsf(1.0 / mass);
+        imass = 1.0 / mass;
+        if constexpr (EXDS) imass_ds = dsf(imass);
     }
 
     // geometry factors, flux parameters and operator tables in arithmetic V
@@ -210,6 +231,16 @@ struct Sweeper {
         if constexpr (std::is_same<V, double>::value) return sD;
         else if constexpr (std::is_same<V, dsf>::value) return xD;
         else return reinterpret_cast<const V*>(rD);
+    }
+    template <class V>
+    __device__ const V* tab_A() const {
+        if constexpr (std::is_same<V, double>::value) return sA;
+        else return reinterpret_cast<const V*>(rA);
+    }
+    template <class V>
+    __device__ const V* tab_Dh() const {
+        if constexpr (std::is_same<V, double>::value) return sDh;
+        else return reinterpret_cast<const V*>(rDh);
     }
     template <class V>
     __device__ const V* tab_K() const {
@@ -287,11 +318,12 @@ struct Sweeper {
     __device__ long long vidx(int c, long long e) const { return c * N + e * Q + node; }
 
     __device__ long long neighbour(long long e, int f) const {
-        const int ex = (int)(e % g.nex), ey = (int)(e / g.nex);
-        if (f == 0) return (long long)ey * g.nex + (ex + g.nex - 1) % g.nex;
-        if (f == 1) return (long long)ey * g.nex + (ex + 1) % g.nex;
-        if (f == 2) return (long long)((ey + g.ney - 1) % g.ney) * g.nex + ex;
-        return (long long)((ey + 1) % g.ney) * g.nex + ex;
+        // element counts are capped at 2^30, so 32-bit division suffices
+        const int ei = (int)e, ey = ei / g.nex, ex = ei - ey * g.nex;
+        if (f == 0) return (long long)(ei + (ex == 0 ? g.nex - 1 : -1));
+        if (f == 1) return (long long)(ei + (ex == g.nex - 1 ? 1 - g.nex : 1));
+        if (f == 2) return (long long)(ey == 0 ? ei + (g.ney - 1) * g.nex : ei - g.nex);
+        return (long long)(ey == g.ney - 1 ? ex : ei + g.nex);
     }
 
     // node of the line normal to face f through face row k, position q
@@ -319,7 +351,8 @@ struct Sweeper {
                 vn[q] = getv(c, en, line_node(f ^ 1, k, q));
             }
             V jump, avg;
-            sipg_face<NQ>(geo<V>(), vo, vn, f, Dt, jump, avg);
+            if constexpr (std::is_same<V, dsf>::value) sipg_face<NQ>(geo<V>(), vo, vn, f, Dt, jump, avg);
+            else sipg_face_pre<NQ>(vo, vn, f, tab_Dh<V>(), jump, avg);
             V* o = tf + ((l * NC + c) * NF + f) * 2 * NQ;
             o[k] = jump;
             o[NQ + k] = avg;
@@ -329,7 +362,10 @@ struct Sweeper {
     // (A u)(i, j) for component c of local element l
     template <class V>
     __device__ V opA(int l, int c, const V* tu, const V* tf, const V* Dt, const V* Kt, const V* wt) const {
-        return sipg_opA<NQ, DIM, V>(geo<V>(), i, j, tu + (l * NC + c) * Q, tf + (l * NC + c) * TRS, Dt, Kt, wt);
+        if constexpr (std::is_same<V, dsf>::value)
+            return sipg_opA<NQ, DIM, V>(geo<V>(), i, j, tu + (l * NC + c) * Q, tf + (l * NC + c) * TRS, Dt, Kt, wt);
+        else
+            return sipg_opA_pre<NQ, DIM, V>(i, j, tu + (l * NC + c) * Q, tf + (l * NC + c) * TRS, tab_A<V>() + node);
     }
     __device__ double opA64(int l, int c) const { return opA<double>(l, c, su, sf, sD, sK, sw); }
     __device__ RT opAR(int l, int c) const { return opA<RT>(l, c, ru, rf, rD, rK, rw); }
@@ -676,6 +712,45 @@ struct Sweeper {
         return solve64(x, xsrc, tm, c, Lx0);
     }
 
+    // One face node of the convective operator, for local element l, face
+    // side (0: left/lower, 1: right/upper) of direction x (XD) or y, face row
+    // k: stores the lifted difference between the Rusanov flux and the own
+    // normal flux, the correction of c(u) at the own end node, in the face
+    // buffer tf ([l][c][f][k]); Navier-Stokes with visc: also the BR1
+    // correction of the gradient of w = (v_x, v_y, T) at that node, lift
+    // times ({w} - w) with the central trace {w} ([l][q][NF + f][k]).
+    template <class V, bool XD>
+    __device__ void conv_face(const double* X, int l, long long e0, int side, int k, bool visc, V* tf) const {
+        const auto& gv = geo<V>();
+        const auto& pv = par<V>();
+        const int f = (XD ? 0 : 2) + side;
+        const int io = side ? NQ - 1 : 0, in = NQ - 1 - io;
+        const int nd = XD ? k * NQ + io : io * NQ + k;
+        const int ndn = XD ? k * NQ + in : in * NQ + k;
+        const long long e = e0 + l, en = neighbour(e, f);
+        V uo[NC], un[NC], d[NC];
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            uo[cc] = (V)__ldcg(X + cc * N + e * Q + nd);
+            un[cc] = (V)__ldcg(X + cc * N + en * Q + ndn);
+        }
+        rusanov_jump<PDE, XD>(pv, uo, un, side == 1, d);
+        // c(u) gains +liftL (Fs - F) at a left end node, -liftR (Fs - F) at a right one
+        const V lift = XD ? (side ? -V(gv.liftRx) : V(gv.liftLx)) : (side ? -V(gv.liftRy) : V(gv.liftLy));
+        V* o = tf + (size_t)l * NC * TRS + f * NQ + k;
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) o[cc * TRS] = lift * d[cc];
+        if constexpr (PD::VISC) {
+            if (visc) {
+                V wo[3], wn[3];
+                PD::primitive(pv, uo, wo);
+                PD::primitive(pv, un, wn);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) o[q * TRS + NF * NQ] = -lift * (V(0.5) * (wo[q] + wn[q]) - wo[q]);
+            }
+        }
+    }
+
     // ---- convective operator phase (arithmetic V) ------------------------------
     // c(X) for the block's elements into out (CT); mode CONV_DELTA also
     // writes dC = c - out_old; f64 (optional) receives c in FP64 (the start of
@@ -686,6 +761,7 @@ struct Sweeper {
     template <class V>
     __device__ void conv(const double* X, int mode, CT* out, double* f64, double* lamslot) {
         V* sFv = buf_flux<V>();
+        V* tf = buf_face<V>();
         const V* Dv = tab_D<V>();
         const auto& gv = geo<V>();
         const auto& pv = par<V>();
@@ -718,6 +794,21 @@ struct Sweeper {
                     lmax = fmax(lmax, static_cast<double>(PD::ry(pv, u)));
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) sFy[cc * Q + node] = Fy[cc];
+                }
+            }
+            // face tasks, one per face node, x faces first (padded to whole
+            // warps so that each warp evaluates one flux direction)
+            {
+                const int nx = nle * 2 * NQY, xr = (nx + 31) & ~31;
+                const int ny = DIM == 2 ? nle * 2 * NQ : 0;
+                for (int t = threadIdx.x; t < xr + ny; t += blockDim.x) {
+                    if (t < nx) {
+                        const int l = t / (2 * NQY), r = t - l * 2 * NQY;
+                        conv_face<V, true>(X, l, e0, r / NQY, r % NQY, visc, tf);
+                    } else if (t >= xr) {
+                        const int ty = t - xr, l = ty / (2 * NQ), r = ty - l * 2 * NQ;
+                        conv_face<V, false>(X, l, e0, r / NQ, r % NQ, visc, tf);
+                    }
                 }
             }
             __syncthreads();
@@ -754,54 +845,24 @@ struct Sweeper {
                         }
                     }
                 }
-                // BR1 face correction of the gradient: +- lift ({w} - w) at the
-                // end nodes, from the neighbour's trace value at the same face node
-                auto lift_w = [&](const V* un_, V* gd, V lift) {
-                    if constexpr (PD::VISC) {
-                        V wn[3];
-                        PD::primitive(pv, un_, wn);
+                // face corrections of the end nodes (conv_face)
+                const V* fc = tf + (size_t)le * NC * TRS;
+                auto add_face = [&](int f, int k) {
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) gd[q] += lift * (V(0.5) * (w[q] + wn[q]) - w[q]);
+                    for (int cc = 0; cc < NC; ++cc) cv[cc] += fc[cc * TRS + f * NQ + k];
+                    if constexpr (PD::VISC) {
+                        if (visc) {
+                            V* gd = f < 2 ? gx : gy;
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) gd[q] += fc[q * TRS + NF * NQ + f * NQ + k];
+                        }
                     }
                 };
-                V un[NC], Fs[NC];
-                if (i == NQ - 1) {
-                    const long long en = neighbour(e, 1);
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + j * NQ);
-                    rusanov<PDE, true>(pv, u, un, Fs);
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(gv.liftRx) * (Fs[cc] - Fx[cc]);
-                    if (visc) lift_w(un, gx, V(gv.liftRx));
-                }
-                if (i == 0) {
-                    const long long en = neighbour(e, 0);
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + j * NQ + NQ - 1);
-                    rusanov<PDE, true>(pv, un, u, Fs);
-#pragma unroll
-                    for (int cc = 0; cc < NC; ++cc) cv[cc] += V(gv.liftLx) * (Fs[cc] - Fx[cc]);
-                    if (visc) lift_w(un, gx, -V(gv.liftLx));
-                }
+                if (i == 0) add_face(0, j);
+                if (i == NQ - 1) add_face(1, j);
                 if (DIM == 2) {
-                    if (j == NQ - 1) {
-                        const long long en = neighbour(e, 3);
-#pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + i);
-                        rusanov<PDE, false>(pv, u, un, Fs);
-#pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) cv[cc] -= V(gv.liftRy) * (Fs[cc] - Fy[cc]);
-                        if (visc) lift_w(un, gy, V(gv.liftRy));
-                    }
-                    if (j == 0) {
-                        const long long en = neighbour(e, 2);
-#pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) un[cc] = (V)__ldcg(X + cc * N + en * Q + (NQ - 1) * NQ + i);
-                        rusanov<PDE, false>(pv, un, u, Fs);
-#pragma unroll
-                        for (int cc = 0; cc < NC; ++cc) cv[cc] += V(gv.liftLy) * (Fs[cc] - Fy[cc]);
-                        if (visc) lift_w(un, gy, -V(gv.liftLy));
-                    }
+                    if (j == 0) add_face(2, i);
+                    if (j == NQ - 1) add_face(3, i);
                 }
                 if constexpr (PD::VISC) {
                     if (visc) {
@@ -857,7 +918,7 @@ struct Sweeper {
                     const long long id = vidx(cc, e);
                     V lu;
                     if constexpr (std::is_same<V, dsf>::value) lu = -(opA<V>(le, cc, tu, tf, Dv, Kv, wv) * imass_ds);
-                    else lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) / (V)mass;
+                    else lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) * (V)imass;
                     LUm[id] = (CT)lu;
                     Fm[id] = __ldcg(Fm + id) + a.nu * (double)lu;
                 }
