@@ -52,11 +52,13 @@ struct EnsSweeper {
     static constexpr int Q = NQ * NQ;
     static constexpr int TRS = 4 * 2 * NQ;
     static constexpr int NSLOT = 4;          // partial-sum slots per set (two sets alternate)
+    static constexpr int NCO = 2 * NQ + 8;   // coefficients per node of the pre-scaled operator
+    static constexpr int NTAB = NCO * Q + 4 * NQ;
 
     static size_t smem_bytes(int epb) {
-        const size_t d = 2 * NQ * NQ + 2 * NQ + 32 + 2 * 3 * 32 + (size_t)epb * Q + (size_t)epb * TRS +
-                         (size_t)epb * 2 * Q;
-        const size_t r = MIX ? (2 * NQ * NQ + NQ + (size_t)epb * Q + (size_t)epb * TRS) : 0;
+        const size_t d = NTAB + 2 * Q + 2 * NQ * NQ + 2 * NQ + 32 + 2 * 3 * 32 + (size_t)epb * Q +
+                         (size_t)epb * TRS + (size_t)epb * 2 * Q;
+        const size_t r = MIX ? (NTAB + 2 * NQ * NQ + NQ + (size_t)epb * Q + (size_t)epb * TRS) : 0;
         return ENS_LSMEM * sizeof(EnsInst) + d * sizeof(double) + r * sizeof(RT) + 16;
     }
 
@@ -64,8 +66,8 @@ struct EnsSweeper {
     EnsInst* sI;          // the block's instances (shared memory): all of them when
                           // nloc <= ENS_LSMEM (pre), else the current tile's in slot 0
     bool pre;
-    double *sD, *sK, *sw, *sdl, *scratch, *wsum, *su, *sf, *sF;
-    RT *rD, *rK, *rw, *ru, *rf;
+    double *sA, *sDh, *sWW, *sIWW, *sD, *sK, *sw, *sdl, *scratch, *wsum, *su, *sf, *sF;
+    RT *rA, *rDh, *rD, *rK, *rw, *ru, *rf;
     int le, node, i, j, G;
     int solve_parity;
     EnsLocal* L;          // this block's per-instance state [nloc]
@@ -76,7 +78,11 @@ struct EnsSweeper {
     __device__ EnsSweeper(const EnsArgs& args) : a(args) {
         extern __shared__ double sm[];
         sI = reinterpret_cast<EnsInst*>(sm);
-        sD = sm + ENS_LSMEM * sizeof(EnsInst) / sizeof(double);
+        sA = sm + ENS_LSMEM * sizeof(EnsInst) / sizeof(double);   // [NCO][Q] unit-element operator
+        sDh = sA + NCO * Q;                                        // [4][NQ] unit-element face rows
+        sWW = sDh + 4 * NQ;                                        // [Q] w_i w_j
+        sIWW = sWW + Q;                                            // [Q] 1 / (w_i w_j)
+        sD = sIWW + Q;
         sK = sD + NQ * NQ;
         sw = sK + NQ * NQ;
         sdl = sw + NQ;
@@ -87,12 +93,16 @@ struct EnsSweeper {
         sF = sf + a.epb * TRS;
         RT* rb = reinterpret_cast<RT*>(sF + a.epb * 2 * Q);
         if (MIX) {
-            rD = rb;
+            rA = rb;
+            rDh = rA + NCO * Q;
+            rD = rDh + 4 * NQ;
             rK = rD + NQ * NQ;
             rw = rK + NQ * NQ;
             ru = rw + NQ;
             rf = ru + a.epb * Q;
         } else {
+            rA = reinterpret_cast<RT*>(sA);
+            rDh = reinterpret_cast<RT*>(sDh);
             rD = reinterpret_cast<RT*>(sD);
             rK = reinterpret_cast<RT*>(sK);
             rw = reinterpret_cast<RT*>(sw);
@@ -111,6 +121,25 @@ struct EnsSweeper {
             sw[t] = a.w[t];
             sdl[t] = a.dl[t];
             if (MIX) rw[t] = (RT)a.w[t];
+        }
+        {
+            const UnitElementGeo ug(NQ);
+            for (int t = threadIdx.x; t < NCO * Q; t += blockDim.x) {
+                const int k = t / Q, nd = t - k * Q;
+                const double v = sipg_opA_coeff<NQ, 2>(ug, a.D, a.K, a.w, k, nd % NQ, nd / NQ);
+                sA[t] = v;
+                if (MIX) rA[t] = (RT)v;
+            }
+            for (int t = threadIdx.x; t < 4 * NQ; t += blockDim.x) {
+                const int f = t / NQ, q = t - f * NQ;
+                const double v = 0.5 * a.D[((f & 1) ? NQ - 1 : 0) * NQ + q];
+                sDh[t] = v;
+                if (MIX) rDh[t] = (RT)v;
+            }
+            for (int t = threadIdx.x; t < Q; t += blockDim.x) {
+                sWW[t] = a.w[t % NQ] * a.w[t / NQ];
+                sIWW[t] = 1.0 / sWW[t];
+            }
         }
         le = threadIdx.x / Q;
         node = threadIdx.x - le * Q;
@@ -159,15 +188,17 @@ struct EnsSweeper {
     __device__ static double nut(const EnsInst& I, double dtm) { return I.nu + 0.5 * dtm * I.lam * I.lam; }
 
     __device__ long long neighbour(const EnsInst& I, long long e, int f) const {
-        const long long el = e - I.e0;
-        const int ex = (int)(el % I.nex), ey = (int)(el / I.nex);
-        long long n;
-        if (f == 0) n = (long long)ey * I.nex + (ex + I.nex - 1) % I.nex;
-        else if (f == 1) n = (long long)ey * I.nex + (ex + 1) % I.nex;
-        else if (f == 2) n = (long long)((ey + I.ney - 1) % I.ney) * I.nex + ex;
-        else n = (long long)((ey + 1) % I.ney) * I.nex + ex;
+        const int el = (int)(e - I.e0), ey = el / I.nex, ex = el - ey * I.nex;   // instances hold < 2^31 elements
+        int n;
+        if (f == 0) n = el + (ex == 0 ? I.nex - 1 : -1);
+        else if (f == 1) n = el + (ex == I.nex - 1 ? 1 - I.nex : 1);
+        else if (f == 2) n = ey == 0 ? el + (I.ney - 1) * I.nex : el - I.nex;
+        else n = ey == I.ney - 1 ? ex : el + I.nex;
         return I.e0 + n;
     }
+
+    // mass of the thread's node in instance I (diagonal GLL mass)
+    __device__ double mass_of(const EnsInst& I) const { return I.mq * sWW[node]; }
 
     __device__ static int line_node(int f, int k, int q) { return f < 2 ? k * NQ + q : q * NQ + k; }
 
@@ -258,7 +289,7 @@ struct EnsSweeper {
 
     // ---- SIPG faces of a tile ----------------------------------------------------
     template <class V, class GetV>
-    __device__ void faces(const EnsInst& I, int nle, long long e0, const V* tu, V* tf, const V* Dt, GetV getv) {
+    __device__ void faces(const EnsInst& I, int nle, long long e0, const V* tu, V* tf, const V* Dh, GetV getv) {
         const int per = 4 * NQ;
         for (int t = threadIdx.x; t < nle * per; t += blockDim.x) {
             const int l = t / per;
@@ -272,17 +303,20 @@ struct EnsSweeper {
                 vo[q] = u[line_node(f, k, q)];
                 vn[q] = getv(en, line_node(f ^ 1, k, q));
             }
-            V jump, avg;
-            sipg_face<NQ>(I, vo, vn, f, Dt, jump, avg);
+            V jump, avg;     // avg: the unscaled derivative average of the unit element
+            sipg_face_pre<NQ>(vo, vn, f, Dh, jump, avg);
             V* o = tf + (l * 4 + f) * 2 * NQ;
             o[k] = jump;
             o[NQ + k] = avg;
         }
     }
 
+    // (A u) of the thread's node: unit-element sums scaled by the instance's aspect ratio
     template <class V>
-    __device__ V opA(const EnsInst& I, const V* tu, const V* tf, const V* Dt, const V* Kt, const V* wt) const {
-        return sipg_opA<NQ, 2, V>(I, i, j, tu + le * Q, tf + le * TRS, Dt, Kt, wt);
+    __device__ V opA(const EnsInst& I, const V* tu, const V* tf, const V* cf) const {
+        V X, Y;
+        sipg_opA_pre_xy<NQ>(i, j, tu + le * Q, tf + le * TRS, cf + node, X, Y);
+        return V(I.rho) * X + V(I.irho) * Y;
     }
 
     template <class V>
@@ -389,15 +423,14 @@ struct EnsSweeper {
                 if (xsrc != x) x[id] = xv;
             }
             __syncthreads();
-            if (!Lx0) faces<double>(I, nle, e0, su, sf, sD, [&](long long en, int nd) { return __ldcg(xsrc + en * Q + nd); });
+            if (!Lx0) faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) { return __ldcg(xsrc + en * Q + nd); });
             __syncthreads();
             if (act) {
-                double ms, dg;
-                mass_diag(I, i, j, ms, dg);
+                const double ms = mass_of(I);
                 const double dtm = I.dt * a.dtau[m];
                 const double mb = ms * rhs_at(R, id, dtm, nut(I, dtm));
                 const double xv = su[le * Q + node];
-                const double Ax = Lx0 ? -ms * __ldcg(Lx0 + id) : opA<double>(I, su, sf, sD, sK, sw);
+                const double Ax = Lx0 ? -ms * __ldcg(Lx0 + id) : opA<double>(I, su, sf, sA);
                 const double rr = mb - (ms * xv + c * Ax);
                 a.r[id] = rr;
                 acc[0] += mb * mb * dinv;
@@ -431,15 +464,13 @@ struct EnsSweeper {
                     su[le * Q + node] = pn;
                 }
                 __syncthreads();
-                faces<double>(I, nle, e0, su, sf, sD, [&](long long en, int nd) {
+                faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) {
                     const long long idn = en * Q + nd;
                     return pnew<double>(__ldcg(a.r + idn), dv[nd], beta, beta == 0.0 ? 0.0 : __ldcg(pold + idn));
                 });
                 __syncthreads();
                 if (act) {
-                    double ms, dg;
-                    mass_diag(I, i, j, ms, dg);
-                    const double Apv = ms * pn + c * opA<double>(I, su, sf, sD, sK, sw);
+                    const double Apv = mass_of(I) * pn + c * opA<double>(I, su, sf, sA);
                     AP[id] = Apv;
                     acc[0] += pn * Apv;
                 }
@@ -497,11 +528,10 @@ struct EnsSweeper {
                 }
                 __syncthreads();
                 if (!(ir == 0 && Lx0))
-                    faces<double>(I, nle, e0, su, sf, sD, [&](long long en, int nd) { return __ldcg(xs + en * Q + nd); });
+                    faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) { return __ldcg(xs + en * Q + nd); });
                 __syncthreads();
                 if (act) {
-                    double ms, dg;
-                    mass_diag(I, i, j, ms, dg);
+                    const double ms = mass_of(I);
                     double mb;
                     if (ir == 0) {
                         const double dtm = I.dt * a.dtau[m];
@@ -512,7 +542,7 @@ struct EnsSweeper {
                         mb = __ldcg(a.r + id);
                     }
                     const double xv = su[le * Q + node];
-                    const double Ax = (ir == 0 && Lx0) ? -ms * __ldcg(Lx0 + id) : opA<double>(I, su, sf, sD, sK, sw);
+                    const double Ax = (ir == 0 && Lx0) ? -ms * __ldcg(Lx0 + id) : opA<double>(I, su, sf, sA);
                     const double r64 = mb - (ms * xv + c * Ax);
                     acc[1] += r64 * (r64 * dinv);
                     const RT r32 = (RT)r64;
@@ -561,15 +591,13 @@ struct EnsSweeper {
                         ru[le * Q + node] = pn;
                     }
                     __syncthreads();
-                    faces<RT>(I, nle, e0, ru, rf, rD, [&](long long en, int nd) {
+                    faces<RT>(I, nle, e0, ru, rf, rDh, [&](long long en, int nd) {
                         const long long idn = en * Q + nd;
                         return pnew<RT>(__ldcg(RF + idn), (RT)dv[nd], betar, betar == RT(0) ? RT(0) : __ldcg(pold + idn));
                     });
                     __syncthreads();
                     if (act) {
-                        double ms, dg;
-                        mass_diag(I, i, j, ms, dg);
-                        const RT Apv = (RT)ms * pn + cr * opA<RT>(I, ru, rf, rD, rK, rw);
+                        const RT Apv = (RT)mass_of(I) * pn + cr * opA<RT>(I, ru, rf, rA);
                         AP[id] = Apv;
                         acc[0] += (double)(pn * Apv);
                     }
@@ -608,6 +636,25 @@ struct EnsSweeper {
     // ---- explicit operators ------------------------------------------------------
     // c(X) into out; CONV_DELTA also writes dC = c - out_old; f64 (optional)
     // receives c (the start of the cached f)
+    // One face node of c(u) (local element l, side 0/1 of direction x (XD)
+    // or y, face row k): the lifted Rusanov-minus-own flux difference, the
+    // correction of c(u) at the own end node, into the face buffer [l][f][k]
+    template <bool XD>
+    __device__ void conv_face(const EnsInst& I, const PdeParams& pp, const double* X, long long e0, int l, int side,
+                              int k) const {
+        const int f = (XD ? 0 : 2) + side;
+        const int io = side ? NQ - 1 : 0, in = NQ - 1 - io;
+        const int nd = XD ? k * NQ + io : io * NQ + k;
+        const int ndn = XD ? k * NQ + in : in * NQ + k;
+        const long long e = e0 + l;
+        const double uo = __ldcg(X + e * Q + nd);
+        const double un = __ldcg(X + neighbour(I, e, f) * Q + ndn);
+        double d;
+        rusanov_jump<0, XD>(pp, &uo, &un, side == 1, &d);
+        const double lift = XD ? (side ? -I.liftRx : I.liftLx) : (side ? -I.liftRy : I.liftLy);
+        sf[(size_t)l * TRS + f * NQ + k] = lift * d;
+    }
+
     __device__ void conv(const double* X, int mode, double* out, double* f64) {
         tiles<0>(nullptr, 0, [&](const EnsInst& I, long long e0, int nle, int, double*) {
             const bool act = le < nle;
@@ -615,13 +662,26 @@ struct EnsSweeper {
             const PdeParams pp{0.0, I.ax, I.ay};
             double* sFx = sF + (size_t)le * 2 * Q;
             double* sFy = sFx + Q;
-            double u = 0.0, Fx = 0.0, Fy = 0.0;
             if (act) {
-                u = __ldcg(X + id);
+                const double u = __ldcg(X + id);
+                double Fx, Fy;
                 Pde<0>::fx(pp, &u, &Fx);
                 Pde<0>::fy(pp, &u, &Fy);
                 sFx[node] = Fx;
                 sFy[node] = Fy;
+            }
+            // face tasks, one per face node: x faces, then y faces from the next whole warp
+            {
+                const int nx = nle * 2 * NQ, xr = (nx + 31) & ~31;
+                for (int t = threadIdx.x; t < xr + nx; t += blockDim.x) {
+                    if (t < nx) {
+                        const int l = t / (2 * NQ), r = t - l * 2 * NQ;
+                        conv_face<true>(I, pp, X, e0, l, r / NQ, r % NQ);
+                    } else if (t >= xr) {
+                        const int ty = t - xr, l = ty / (2 * NQ), r = ty - l * 2 * NQ;
+                        conv_face<false>(I, pp, X, e0, l, r / NQ, r % NQ);
+                    }
+                }
             }
             __syncthreads();
             if (act) {
@@ -633,27 +693,11 @@ struct EnsSweeper {
 #pragma unroll
                 for (int k = 0; k < NQ; ++k) s += sD[j * NQ + k] * sFy[k * NQ + i];
                 cv -= I.sy * s;
-                double un, Fs;
-                if (i == NQ - 1) {
-                    un = __ldcg(X + neighbour(I, e, 1) * Q + j * NQ);
-                    rusanov<0, true>(pp, &u, &un, &Fs);
-                    cv -= I.liftRx * (Fs - Fx);
-                }
-                if (i == 0) {
-                    un = __ldcg(X + neighbour(I, e, 0) * Q + j * NQ + NQ - 1);
-                    rusanov<0, true>(pp, &un, &u, &Fs);
-                    cv += I.liftLx * (Fs - Fx);
-                }
-                if (j == NQ - 1) {
-                    un = __ldcg(X + neighbour(I, e, 3) * Q + i);
-                    rusanov<0, false>(pp, &u, &un, &Fs);
-                    cv -= I.liftRy * (Fs - Fy);
-                }
-                if (j == 0) {
-                    un = __ldcg(X + neighbour(I, e, 2) * Q + (NQ - 1) * NQ + i);
-                    rusanov<0, false>(pp, &un, &u, &Fs);
-                    cv += I.liftLy * (Fs - Fy);
-                }
+                const double* fc = sf + (size_t)le * TRS;
+                if (i == 0) cv += fc[j];
+                if (i == NQ - 1) cv += fc[NQ + j];
+                if (j == 0) cv += fc[2 * NQ + i];
+                if (j == NQ - 1) cv += fc[3 * NQ + i];
                 if (mode == CONV_DELTA) a.dC[id] = cv - __ldcg(out + id);
                 out[id] = cv;
                 if (f64) f64[id] = cv;
@@ -668,12 +712,10 @@ struct EnsSweeper {
             const long long id = (e0 + le) * Q + node;
             if (act) su[le * Q + node] = __ldcg(X + id);
             __syncthreads();
-            faces<double>(I, nle, e0, su, sf, sD, [&](long long en, int nd) { return __ldcg(X + en * Q + nd); });
+            faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) { return __ldcg(X + en * Q + nd); });
             __syncthreads();
             if (act) {
-                double ms, dg;
-                mass_diag(I, i, j, ms, dg);
-                const double lu = -opA<double>(I, su, sf, sD, sK, sw) / ms;
+                const double lu = -opA<double>(I, su, sf, sA) * (I.imq * sIWW[node]);
                 LUm[id] = lu;
                 Fm[id] = __ldcg(Fm + id) + I.nu * lu;
             }

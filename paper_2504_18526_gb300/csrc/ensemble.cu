@@ -208,6 +208,10 @@ EnsInst make_inst(const sisdc_ens_instance& s, int nq, const LevelTables& tab, l
     I.nu = s.nu;
     I.lam = std::max(std::fabs(s.adv[0]), std::fabs(s.adv[1]));
     I.dt = s.dt;
+    I.rho = I.hy / I.hx;
+    I.irho = I.hx / I.hy;
+    I.mq = 0.25 * I.hx * I.hy;
+    I.imq = 1.0 / I.mq;
     return I;
 }
 

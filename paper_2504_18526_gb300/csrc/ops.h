@@ -172,6 +172,8 @@ struct EnsInst {
     double ax, ay, nu;
     double lam;                              // max(|a_x|, |a_y|)
     double dt;                               // the instance's time step
+    double rho, irho;                        // h_y / h_x, h_x / h_y
+    double mq, imq;                          // h_x h_y / 4 and its inverse (mass = mq w_i w_j)
 };
 
 // instance records a block keeps in shared memory for the whole launch

@@ -91,6 +91,37 @@ __device__ __forceinline__ V sipg_opA_pre(int i, int j, const V* u, const V* f, 
     }
 }
 
+// 2D sipg_opA_pre with coefficients of the unit element (h_x = h_y = 2) and
+// the x and y parts returned separately: for an element of sides h_x, h_y,
+// (A u)(i, j) = (h_y / h_x) X + (h_x / h_y) Y when the face averages hold
+// the unscaled derivatives (face rows D/2, as sipg_face_pre with the unit
+// element's half rows gives them).
+template <int NQ, class V>
+__device__ __forceinline__ void sipg_opA_pre_xy(int i, int j, const V* u, const V* f, const V* cf, V& X, V& Y) {
+    constexpr int Q = NQ * NQ;
+    const V* cx = cf + 2 * NQ * Q;
+    V ax = V(0), ay = V(0);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        ax += cf[k * Q] * u[j * NQ + k];
+        ay += cf[(NQ + k) * Q] * u[k * NQ + i];
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        ax += cx[s * Q] * f[s * NQ + j];
+        ay += cx[(4 + s) * Q] * f[(4 + s) * NQ + i];
+    }
+    X = ax;
+    Y = ay;
+}
+
+// geometry of the unit element h_x = h_y = 2 (penalty 2 NQ^2 / h)
+struct UnitElementGeo {
+    double hx, hy, sx, sy, ihx, ihy, taux, tauy;
+    __host__ __device__ constexpr explicit UnitElementGeo(int nq)
+        : hx(2.0), hy(2.0), sx(1.0), sy(1.0), ihx(0.5), ihy(0.5), taux(double(nq) * nq), tauy(double(nq) * nq) {}
+};
+
 // coefficient k of node (i, j) of sipg_opA_pre (FP64; D, K, w as in sipg_opA)
 template <int NQ, int DIM, class GG>
 __device__ __forceinline__ double sipg_opA_coeff(const GG& g, const double* D, const double* K, const double* w,
