@@ -285,9 +285,9 @@ def whole_job_value(units_per_step_per_rank, steps, world, ms):
     return world * units_per_step_per_rank * steps / (ms * 1e-3)
 
 
-def make_ctx(S, w, stream, prec, rtol, use_graph):
+def make_ctx(S, w, stream, prec, rtol, use_graph, mixed_levels=0):
     return S.Context(w, stream=stream.cuda_stream, precision=prec, cg_rtol=rtol, cg_maxit=1000,
-                     use_graph=use_graph)
+                     use_graph=use_graph, mixed_levels=mixed_levels)
 
 
 def tune(S, args, ctx, du, dt, nlevels):
@@ -430,8 +430,11 @@ def main_arm(args):
     run_steps(S, ref_ctx, ur, dt / 4, 6, start, 4 * win)
     S.sisdc_sync(ref_ctx.ctx)
     ref_ctx.close()
-    for pf, name in ((S.SISDC_FP64, "fp64_plain"), (S.SISDC_MIXED, "mixed_tuned")):
-        fctx = make_ctx(S, w, stream, pf, args.cg_rtol, 1)
+    # mixed form on every level, and on the finest level only (the coarse
+    # level's sweeps are barrier-latency bound, where FP64 solves are faster)
+    for pf, name, mask in ((S.SISDC_FP64, "fp64_plain", 0), (S.SISDC_MIXED, "mixed_all_levels", 0),
+                           (S.SISDC_MIXED, "mixed_fine_level", 1 << (nlev - 1))):
+        fctx = make_ctx(S, w, stream, pf, args.cg_rtol, 1, mask)
         uf = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
         tune(S, args, fctx, uf, dt, nlev)
         run_steps(S, fctx, uf, dt, ncyc, start, 2)                 # capture + warm
@@ -446,8 +449,10 @@ def main_arm(args):
         tms = a0.elapsed_time(a1)
         err = float(torch.linalg.vector_norm(uf - ur) / torch.linalg.vector_norm(ur))
         forms[name] = {"ms_per_step": tms / win, "dof_sweeps_per_s": dofs_per_step * win / (tms * 1e-3),
-                       "time_to_solution_ms": tms, "rel_l2_error_vs_reference": err}
+                       "time_to_solution_ms": tms, "rel_l2_error_vs_reference": err, "mixed_levels": mask}
         fctx.close()
+    best = min(("mixed_all_levels", "mixed_fine_level"), key=lambda k: forms[k]["time_to_solution_ms"])
+    forms["mixed_tuned"] = dict(forms[best], variant=best)
     tts = {"window_steps": win, "reference": "FP64 GPU path at dt/4 with 6 V-cycles per step",
            "error_ratio_tuned_over_plain": forms["mixed_tuned"]["rel_l2_error_vs_reference"] /
            max(1e-300, forms["fp64_plain"]["rel_l2_error_vs_reference"]),

@@ -129,6 +129,11 @@ typedef struct {
                            non-incremental (zero-to-node) MLSDC of Sec. 4.5,
                            whose FAS right-hand side is built from F^0n
                            residuals (single-level sweeps are the same)       */
+    int mixed_levels;   /* SISDC_MIXED only: bit l set = level l (creation
+                           order, 0 = first created) uses the mixed form, the
+                           others run in FP64; 0 = every level.  Levels whose
+                           sweeps are barrier-latency bound (small coarse
+                           levels) are often faster in FP64                    */
 } sisdc_problem;
 
 typedef struct {

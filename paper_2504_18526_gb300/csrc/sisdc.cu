@@ -29,6 +29,7 @@ using namespace sisdc;
 struct sisdc_level_s {
     sisdc_ctx_s* ctx = nullptr;
     int index = 0;
+    bool mix = false;            // this level runs the mixed-precision form
     sisdc_level_desc desc{};
     LevelTables tab;
     Geo geo{};
@@ -283,7 +284,7 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.u0 = u0;
     a.U = U;
     a.G = G;
-    a.mix = c->prob.precision == SISDC_MIXED ? 1 : 0;
+    a.mix = lv->mix ? 1 : 0;
     a.F = lv->F; a.CC = lv->CC; a.LU = lv->LU; a.Qb = lv->Qb;
     a.c0 = lv->c0; a.dC = lv->dC; a.tmpc = lv->tmpc;
     a.r = lv->cg_r; a.p = lv->cg_p; a.p2 = lv->cg_p2; a.Ap = lv->cg_Ap; a.rf = lv->cg_rf;
@@ -299,7 +300,7 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.epb = lv->sw_epb;
     a.stream = c->stream;
     a.iters_out = nullptr;
-    if (c->log_r && lv->index == c->log_level && c->prob.precision == SISDC_FP64) {
+    if (c->log_r && lv->index == c->log_level && !lv->mix) {
         a.log_r = c->log_r;
         a.log_dx = c->log_dx;
         a.log_c = c->log_c;
@@ -481,6 +482,7 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (nc_expect < 0 || prob->ncomp != nc_expect) return SISDC_E_ARG;
     if (prob->si_stages != 1 && prob->si_stages != 2) return SISDC_E_ARG;
     if (prob->precision != SISDC_FP64 && prob->precision != SISDC_MIXED) return SISDC_E_ARG;
+    if (prob->mixed_levels < 0) return SISDC_E_ARG;
     if (!(prob->cg_rtol > 0.0) || prob->cg_maxit < 1 || prob->Nc < 0) return SISDC_E_ARG;
     if ((prob->pde == SISDC_PDE_EULER || prob->pde == SISDC_PDE_NS) && !(prob->gamma > 1.0)) return SISDC_E_ARG;
     if (prob->pde == SISDC_PDE_NS && !(prob->mu > 0.0 && prob->Pr > 0.0 && prob->rho_ref > 0.0)) return SISDC_E_ARG;
@@ -547,8 +549,11 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     if (d->dim != 1 && d->dim != 2) return fail(c, SISDC_E_ARG, "dim must be 1 or 2");
     if (d->dim == 1 && c->prob.pde != SISDC_PDE_CONVDIFF) return fail(c, SISDC_E_ARG, "1D supports convection-diffusion only");
     if ((long long)d->nel[0] * (d->dim == 2 ? d->nel[1] : 1) > (1LL << 30)) return fail(c, SISDC_E_ARG, "too many elements");
+    const int lidx = (int)c->levels.size();
+    const bool lmix = c->prob.precision == SISDC_MIXED &&
+                      (c->prob.mixed_levels == 0 || (lidx < 31 && ((c->prob.mixed_levels >> lidx) & 1)));
     // degrees up to 15 for 1D convection-diffusion in FP64, up to 8 otherwise
-    const int pmax = (d->dim == 1 && c->prob.pde == SISDC_PDE_CONVDIFF && c->prob.precision == SISDC_FP64) ? 15 : 8;
+    const int pmax = (d->dim == 1 && c->prob.pde == SISDC_PDE_CONVDIFF && !lmix) ? 15 : 8;
     if (d->P < 1 || d->P > pmax) return fail(c, SISDC_E_ARG, "P must be in 1..8 (1..15 for 1D convection-diffusion in FP64)");
     if (d->M < 1 || d->M > MMAX) return fail(c, SISDC_E_ARG, "M must be in 1..8");
     if (d->nodes != SISDC_RADAU_RIGHT && d->nodes != SISDC_LOBATTO) return fail(c, SISDC_E_ARG, "bad node kind");
@@ -557,7 +562,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     if (d->nel[0] < 1 || ney < 1) return fail(c, SISDC_E_ARG, "nel must be >= 1");
     if (!(d->hi[0] > d->lo[0]) || (d->dim == 2 && !(d->hi[1] > d->lo[1]))) return fail(c, SISDC_E_ARG, "empty box");
     if ((int)c->levels.size() >= 8) return fail(c, SISDC_E_ARG, "at most 8 levels");
-    if (c->prob.precision == SISDC_MIXED && (d->dim != 2 || d->P < 3))
+    if (lmix && (d->dim != 2 || d->P < 3))
         return fail(c, SISDC_E_ARG, "mixed precision supports 2D levels with P >= 3");
     if (!c->levels.empty()) {
         const sisdc_level_desc& p = c->levels.back()->desc;
@@ -569,7 +574,8 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     }
     sisdc_level_s* lv = new sisdc_level_s();
     lv->ctx = c;
-    lv->index = (int)c->levels.size();
+    lv->index = lidx;
+    lv->mix = lmix;
     lv->desc = *d;
     if (d->dim == 1) { lv->desc.nel[1] = 1; lv->desc.lo[1] = 0.0; lv->desc.hi[1] = 1.0; }
     if (!build_level_tables(d->P, d->M, d->nodes == SISDC_LOBATTO, &lv->tab)) {
@@ -681,7 +687,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     g.liftLx = g.sx / lv->tab.w[0]; g.liftRx = g.sx / lv->tab.w[nq - 1];
     g.liftLy = g.sy / lv->tab.w[0]; g.liftRy = g.sy / lv->tab.w[nq - 1];
     lv->pcg_grid = pcg_grid(g, &lv->pcg_block);
-    lv->sw_grid = sweep_config(g, c->prob.pde, c->prob.precision == SISDC_MIXED, &lv->sw_epb, &lv->sw_block);
+    lv->sw_grid = sweep_config(g, c->prob.pde, lv->mix, &lv->sw_epb, &lv->sw_block);
     if (lv->pcg_grid < 1 || lv->pcg_grid > c->max_grid || lv->sw_grid < 1 || lv->sw_grid > c->max_grid) {
         cudaFree(lv->d_tab);
         cudaFree(lv->d_mem);
@@ -963,7 +969,6 @@ sisdc_status sisdc_autotune(sisdc_ctx c, const double* d_u, double dt, int reps,
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const bool mix = c->prob.precision == SISDC_MIXED;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     try {
         check(c, cudaEventCreate(&e0), "event");
@@ -983,7 +988,7 @@ sisdc_status sisdc_autotune(sisdc_ctx c, const double* d_u, double dt, int reps,
             int best_epb = lv->sw_epb, best_grid = lv->sw_grid, best_block = lv->sw_block;
             for (int e : cand) {
                 int epb = e, block = 0;
-                const int gmax = sweep_config(lv->geo, c->prob.pde, mix ? 1 : 0, &epb, &block);
+                const int gmax = sweep_config(lv->geo, c->prob.pde, lv->mix ? 1 : 0, &epb, &block);
                 if (gmax < 1 || gmax > c->max_grid) continue;
                 for (int grid : {gmax, gmax / 2}) {
                     if (grid < 1 || (grid == gmax / 2 && gmax < 2 * nsm)) continue;

@@ -35,7 +35,7 @@ class sisdc_problem(ctypes.Structure):
                 ("adv", c_double * 2), ("precision", c_int), ("si_stages", c_int),
                 ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("use_graph", c_int),
                 ("mu", c_double), ("Pr", c_double), ("rho_ref", c_double), ("projection", c_int),
-                ("fmg_cycles", c_int), ("form", c_int)]
+                ("fmg_cycles", c_int), ("form", c_int), ("mixed_levels", c_int)]
 
 
 class sisdc_stats(ctypes.Structure):
@@ -526,7 +526,8 @@ START_IDS = {"spread": SISDC_START_SPREAD, "predictor": SISDC_START_PREDICTOR,
 
 
 def make_problem(w, precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12, cg_maxit=1000, Nc=2,
-                 use_graph=0, projection="interp", fmg_cycles=1, form="incremental"):
+                 use_graph=0, projection="interp", fmg_cycles=1, form="incremental",
+                 mixed_levels=0):
     p = sisdc_problem()
     p.pde = PDE_IDS[w["pde"]]
     p.ncomp = w["ncomp"]
@@ -543,6 +544,7 @@ def make_problem(w, precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12, cg_maxit=1
     p.projection = {"interp": 0, "l2": 1}[projection]
     p.fmg_cycles = fmg_cycles
     p.form = {"incremental": 0, "zero_to_node": 1}[form]
+    p.mixed_levels = mixed_levels
     if w["pde"] == "ns":
         p.mu = 1.0 / w["Re"]
         p.Pr = w["Pr"]
