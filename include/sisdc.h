@@ -452,6 +452,23 @@ typedef struct {
 sisdc_status sisdc_stability(const sisdc_stab_opts* opts, const double* d_z, double* d_R, long long n,
                              void* cuda_stream);
 
+/* --- number-format conversions of the mixed-precision kernels ------------
+ *
+ * The mixed form's FP32 <-> FP64 and FP64 -> double-single conversions are
+ * built from the IEEE-754 bit patterns with integer instructions (on GB300
+ * the hardware conversions issue on the FP64 unit).  This entry applies them
+ * elementwise so that they can be checked against the hardware conversions:
+ *   kind 0: d_in double[n] -> d_out float[n], rounded to nearest (ties even)
+ *   kind 1: d_in float[n]  -> d_out double[n], exact
+ *   kind 2: d_in double[n] -> d_out float[2n], (hi, lo) double-single pairs:
+ *           hi = the input truncated to 24 significand bits, lo = the
+ *           remainder truncated to 24 bits (2^-74 <= |x| < 2^128; other
+ *           inputs: hi = the rounded float, lo = the rounded remainder)
+ *   kind 3: d_in float[2n] (hi, lo) -> d_out double[n] = hi + lo rounded
+ * Device pointers, n >= 0, asynchronous on `cuda_stream`; SISDC_E_ARG for an
+ * unknown kind, n < 0 or a null pointer with n > 0. */
+sisdc_status sisdc_convert(int kind, const void* d_in, long long n, void* d_out, void* cuda_stream);
+
 /* Message of the last failing call on this context ("" if none). */
 const char* sisdc_last_error(sisdc_ctx ctx);
 

@@ -26,6 +26,7 @@
 #pragma once
 #include <type_traits>
 
+#include "ds.cuh"
 #include "ops.h"
 #include "pde.cuh"
 #include "sipg.cuh"
@@ -520,7 +521,7 @@ struct EnsSweeper {
                 const bool act = le < nle;
                 const long long id = (e0 + le) * Q + node;
                 const double c = L[li].c, dinv = dinv_tab[(size_t)li * Q + node];
-                const RT dinvr = (RT)dinv;
+                const RT dinvr = to_v<RT>(dinv);
                 if (act) {
                     const double xv = __ldcg(xs + id);
                     su[le * Q + node] = xv;
@@ -545,9 +546,9 @@ struct EnsSweeper {
                     const double Ax = (ir == 0 && Lx0) ? -ms * __ldcg(Lx0 + id) : opA<double>(I, su, sf, sA);
                     const double r64 = mb - (ms * xv + c * Ax);
                     acc[1] += r64 * (r64 * dinv);
-                    const RT r32 = (RT)r64;
+                    const RT r32 = to_v<RT>(r64);
                     RF[id] = r32;
-                    acc[2] += (double)(r32 * (r32 * dinvr));   // FP32 term, FP64 sum
+                    acc[2] += to_f64(r32 * (r32 * dinvr));   // FP32 term, FP64 sum
                 }
             });
             if (!bar()) return false;
@@ -586,20 +587,20 @@ struct EnsSweeper {
                     const double* dv = dinv_tab + (size_t)li * Q;
                     RT pn = RT(0);
                     if (act) {
-                        pn = pnew<RT>(__ldcg(RF + id), (RT)dv[node], betar, betar == RT(0) ? RT(0) : __ldcg(pold + id));
+                        pn = pnew<RT>(__ldcg(RF + id), to_v<RT>(dv[node]), betar, betar == RT(0) ? RT(0) : __ldcg(pold + id));
                         pcur[id] = pn;
                         ru[le * Q + node] = pn;
                     }
                     __syncthreads();
                     faces<RT>(I, nle, e0, ru, rf, rDh, [&](long long en, int nd) {
                         const long long idn = en * Q + nd;
-                        return pnew<RT>(__ldcg(RF + idn), (RT)dv[nd], betar, betar == RT(0) ? RT(0) : __ldcg(pold + idn));
+                        return pnew<RT>(__ldcg(RF + idn), to_v<RT>(dv[nd]), betar, betar == RT(0) ? RT(0) : __ldcg(pold + idn));
                     });
                     __syncthreads();
                     if (act) {
-                        const RT Apv = (RT)mass_of(I) * pn + cr * opA<RT>(I, ru, rf, rA);
+                        const RT Apv = to_v<RT>(mass_of(I)) * pn + cr * opA<RT>(I, ru, rf, rA);
                         AP[id] = Apv;
-                        acc[0] += (double)(pn * Apv);
+                        acc[0] += to_f64(pn * Apv);
                     }
                 });
                 if (!bar()) return false;
@@ -611,11 +612,11 @@ struct EnsSweeper {
                     if (le < nle) {
                         const long long id = (e0 + le) * Q + node;
                         const double alpha = L[li].alpha;
-                        const RT alphar = (RT)alpha, dinvr = (RT)dinv_tab[(size_t)li * Q + node];
-                        x[id] = __ldcg(x + id) + alpha * (double)__ldcg(pcur + id);
+                        const RT alphar = (RT)alpha, dinvr = to_v<RT>(dinv_tab[(size_t)li * Q + node]);
+                        x[id] = __ldcg(x + id) + alpha * to_f64(__ldcg(pcur + id));
                         const RT rr = __ldcg(RF + id) - alphar * __ldcg(AP + id);
                         RF[id] = rr;
-                        acc[0] += (double)(rr * (rr * dinvr));
+                        acc[0] += to_f64(rr * (rr * dinvr));
                     }
                 });
                 if (!bar()) return false;

@@ -7,9 +7,28 @@
 //            FAS residual r = g - F^nn(U) (eq. MLSDC:incremental:residual).
 // * transfer: I, P, R = I^T as (space (x) space) (x) time tensor products
 //            applied per element (Sec. 4.2, Sec. 6.2).
+#include "sisdc.h"
+#include "ds.cuh"
 #include "ops.h"
 
 namespace sisdc {
+
+__global__ void k_convert(int kind, const void* in, long long n, void* out) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        if (kind == 0) {
+            static_cast<float*>(out)[t] = d2f_int(static_cast<const double*>(in)[t]);
+        } else if (kind == 1) {
+            static_cast<double*>(out)[t] = f2d_int(static_cast<const float*>(in)[t]);
+        } else if (kind == 2) {
+            const dsf v = ds_from_double_int(static_cast<const double*>(in)[t]);
+            static_cast<float*>(out)[2 * t] = v.hi;
+            static_cast<float*>(out)[2 * t + 1] = v.lo;
+        } else {
+            const float* p = static_cast<const float*>(in) + 2 * t;
+            static_cast<double*>(out)[t] = ds_to_double_int(dsf(p[0], p[1]));
+        }
+    }
+}
 
 static inline unsigned ew_grid(long long n, int bs) {
     long long g = (n + bs - 1) / bs;
@@ -246,3 +265,11 @@ cudaError_t launch_norms(const Geo& g, const double* u, const double* ref, doubl
 }
 
 }  // namespace sisdc
+
+extern "C" sisdc_status sisdc_convert(int kind, const void* d_in, long long n, void* d_out, void* cuda_stream) {
+    using namespace sisdc;
+    if (kind < 0 || kind > 3 || n < 0 || (n > 0 && (!d_in || !d_out))) return SISDC_E_ARG;
+    if (n == 0) return SISDC_OK;
+    k_convert<<<ew_grid(n, 256), 256, 0, (cudaStream_t)cuda_stream>>>(kind, d_in, n, d_out);
+    return cudaGetLastError() == cudaSuccess ? SISDC_OK : SISDC_E_CUDA;
+}

@@ -604,11 +604,11 @@ struct Sweeper {
                         const double Ax = (ir == 0 && Lx0) ? -mass * __ldcg(Lx0 + id) : opA64(le, cc);
                         const double r64 = mb - (mass * xv + c * Ax);
                         acc64 += r64 * (r64 * dinv);
-                        const RT r32 = (RT)r64;
+                        const RT r32 = to_v<RT>(r64);
                         RF[id] = r32;
                         loc32 += r32 * (r32 * dinvr);
                     }
-                    acc32 += (double)loc32;
+                    acc32 += to_f64(loc32);
                 }
                 __syncthreads();
             });
@@ -665,7 +665,7 @@ struct Sweeper {
                             AP[vidx(cc, e)] = Apv;
                             loc += pn[cc] * Apv;
                         }
-                        acc += (double)loc;
+                        acc += to_f64(loc);
                     }
                     __syncthreads();
                 });
@@ -681,12 +681,12 @@ struct Sweeper {
 #pragma unroll
                         for (int cc = 0; cc < NC; ++cc) {
                             const long long id = vidx(cc, e);
-                            x[id] = __ldcg(x + id) + alpha * (double)__ldcg(pcur + id);
+                            x[id] = __ldcg(x + id) + alpha * to_f64(__ldcg(pcur + id));
                             const RT rr = __ldcg(RF + id) - alphar * __ldcg(AP + id);
                             RF[id] = rr;
                             loc += rr * (rr * dinvr);
                         }
-                        acc += (double)loc;
+                        acc += to_f64(loc);
                     }
                 });
                 put_partial(part + 4 * G, acc);
@@ -731,8 +731,8 @@ struct Sweeper {
         V uo[NC], un[NC], d[NC];
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) {
-            uo[cc] = (V)__ldcg(X + cc * N + e * Q + nd);
-            un[cc] = (V)__ldcg(X + cc * N + en * Q + ndn);
+            uo[cc] = to_v<V>(__ldcg(X + cc * N + e * Q + nd));
+            un[cc] = to_v<V>(__ldcg(X + cc * N + en * Q + ndn));
         }
         rusanov_jump<PDE, XD>(pv, uo, un, side == 1, d);
         // c(u) gains +liftL (Fs - F) at a left end node, -liftR (Fs - F) at a right one
@@ -777,7 +777,7 @@ struct Sweeper {
             V* sW = reinterpret_cast<V*>(su) + (size_t)le * NC * Q;    // primitive values (tile buffer is free here)
             if (act) {
 #pragma unroll
-                for (int cc = 0; cc < NC; ++cc) u[cc] = (V)__ldcg(X + vidx(cc, e));
+                for (int cc = 0; cc < NC; ++cc) u[cc] = to_v<V>(__ldcg(X + vidx(cc, e)));
                 if constexpr (PD::VISC) {
                     if (visc) {
                         PD::primitive(pv, u, w);
@@ -786,12 +786,12 @@ struct Sweeper {
                     }
                 }
                 PD::fx(pv, u, Fx);
-                lmax = fmax(lmax, static_cast<double>(PD::rx(pv, u)));
+                lmax = fmax(lmax, to_f64(PD::rx(pv, u)));
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) sFx[cc * Q + node] = Fx[cc];
                 if (DIM == 2) {
                     PD::fy(pv, u, Fy);
-                    lmax = fmax(lmax, static_cast<double>(PD::ry(pv, u)));
+                    lmax = fmax(lmax, to_f64(PD::ry(pv, u)));
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) sFy[cc * Q + node] = Fy[cc];
                 }
@@ -879,9 +879,10 @@ struct Sweeper {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
                     const long long id = vidx(cc, e);
-                    if (mode == CONV_DELTA) C(a.dC)[id] = (CT)((double)cv[cc] - (double)__ldcg(out + id));
-                    out[id] = (CT)cv[cc];
-                    if (f64) f64[id] = (double)cv[cc];
+                    const double cvd = to_f64(cv[cc]);
+                    if (mode == CONV_DELTA) C(a.dC)[id] = cvd - __ldcg(out + id);
+                    out[id] = cvd;
+                    if (f64) f64[id] = cvd;
                 }
             }
             __syncthreads();
@@ -904,13 +905,13 @@ struct Sweeper {
             double* sV = sF64 + (size_t)le * 6 * Q;     // own viscous fluxes (Navier-Stokes)
             if (act) {
 #pragma unroll
-                for (int cc = 0; cc < NC; ++cc) tu[(le * NC + cc) * Q + node] = (V)__ldcg(X + vidx(cc, e));
+                for (int cc = 0; cc < NC; ++cc) tu[(le * NC + cc) * Q + node] = to_v<V>(__ldcg(X + vidx(cc, e)));
                 if constexpr (PD::VISC)
 #pragma unroll
                     for (int q = 0; q < 6; ++q) sV[q * Q + node] = __ldcg(a.FV + q * N + e * Q + node);
             }
             __syncthreads();
-            faces<V>(nle, e0, tu, tf, Dv, [&](int cc, long long en, int nd) { return (V)__ldcg(X + cc * N + en * Q + nd); });
+            faces<V>(nle, e0, tu, tf, Dv, [&](int cc, long long en, int nd) { return to_v<V>(__ldcg(X + cc * N + en * Q + nd)); });
             __syncthreads();
             if (act) {
 #pragma unroll
@@ -919,8 +920,9 @@ struct Sweeper {
                     V lu;
                     if constexpr (std::is_same<V, dsf>::value) lu = -(opA<V>(le, cc, tu, tf, Dv, Kv, wv) * imass_ds);
                     else lu = -opA<V>(le, cc, tu, tf, Dv, Kv, wv) * (V)imass;
-                    LUm[id] = (CT)lu;
-                    Fm[id] = __ldcg(Fm + id) + a.nu * (double)lu;
+                    const double lud = to_f64(lu);
+                    LUm[id] = lud;
+                    Fm[id] = __ldcg(Fm + id) + a.nu * lud;
                 }
                 if constexpr (PD::VISC) {
                     // div F_v with central face fluxes: (2/h) D F_v plus

@@ -123,6 +123,7 @@ def load():
         "sisdc_get_kernel_timing": (c_int, [c_void_p, P(c_double), P(c_ll), P(c_ll), P(c_ll), P(c_ll)]),
         "sisdc_autotune": (c_int, [c_void_p, c_void_p, c_double, c_int, c_void_p]),
         "sisdc_stability": (c_int, [P(sisdc_stab_opts), c_void_p, c_void_p, c_ll, c_void_p]),
+        "sisdc_convert": (c_int, [c_int, c_void_p, c_ll, c_void_p, c_void_p]),
         "sisdc_level_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
         "sisdc_ens_create": (c_int, [P(sisdc_ens_instance), c_int, P(sisdc_ens_opts), c_void_p, P(c_void_p)]),
         "sisdc_ens_destroy": (None, [c_void_p]),
@@ -373,6 +374,23 @@ def sisdc_stability(z, Ms, nodes="radau_right", stages=2, ncycles=1, start="pred
     if st != SISDC_OK:
         raise SisdcError(st, "sisdc_stability")
     return torch.view_as_complex(R)
+
+
+def sisdc_convert(kind, x, stream=0):
+    """The mixed-precision kernels' integer-pipe format conversions applied to
+    a CUDA tensor x: kind 0 float64 -> float32, 1 float32 -> float64, 2
+    float64 -> [n, 2] float32 double-single pairs, 3 [n, 2] float32 pairs ->
+    float64."""
+    import torch
+    x = x.contiguous()
+    n = x.shape[0]
+    out_shape, out_dtype = {0: ((n,), torch.float32), 1: ((n,), torch.float64),
+                            2: ((n, 2), torch.float32), 3: ((n,), torch.float64)}[kind]
+    out = torch.empty(out_shape, dtype=out_dtype, device=x.device)
+    st = load().sisdc_convert(kind, x.data_ptr(), n, out.data_ptr(), c_void_p(stream))
+    if st != SISDC_OK:
+        raise SisdcError(st, "sisdc_convert")
+    return out
 
 
 def sisdc_level_config(lv):
