@@ -178,6 +178,24 @@ def ensemble_oracle_sample(args):
                       "finite": True}))
 
 
+def mlp_oracle_sample(args):
+    """FP64 numpy loss and gradients of the oracle MLP (325 -> 112 -> 112 -> 36)
+    over 4096 patch rows, repeated for about 10 s."""
+    import numpy as np
+    from oracle import mlp as omlp
+    rows, n_in, H, q = 4096, 9 * 36 + 1, 112, 36
+    rng = np.random.default_rng(3)
+    p = omlp.init_params(n_in, H, q, 1)
+    X = rng.standard_normal((rows, n_in))
+    T = rng.standard_normal((rows, q))
+    t0 = time.perf_counter()
+    reps = 0
+    while reps == 0 or time.perf_counter() - t0 < 10.0:
+        omlp.loss_and_grads(p, X, T)
+        reps += 1
+    print(json.dumps({"seconds": time.perf_counter() - t0, "rows": rows * reps, "passes": reps}))
+
+
 def run_oracle_child(args, steps):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -704,10 +722,109 @@ def stability_arm(args):
                       "cpu_baseline": cpu}))
 
 
+def mlp_flops(rows, n_in, H, q):
+    """GEMM flops of one inference (forward) and one training step (forward,
+    the five backward products) of the n_in -> H -> H -> q network."""
+    fwd = 2.0 * rows * (n_in * H + H * H + H * q)
+    bwd = 2.0 * rows * (n_in * H + 2 * H * H + 2 * H * q)
+    return fwd, fwd + bwd
+
+
+def mlp_arm(args):
+    """The learned part on the Navier-Stokes level (128^2 elements, P = 5,
+    four components: 65 536 patch rows, 325 -> 112 -> 112 -> 36): training
+    steps (loss, gradients, Adam) on synthetic logged solves, and inference
+    (gather, three layers, scatter), BF16 tensor-core mode against the FP32
+    SIMT mode."""
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import inputs, sisdc as S
+    from paper_2504_18526_gb300.build import build
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build()
+    S.load()
+    stream = torch.cuda.current_stream()
+    w = inputs.WORKLOADS["ns_shear"]
+    ctx = S.Context(w, stream=stream.cuda_stream)
+    lv = ctx.levels[-1]
+    nc, n, M = ctx.info(-1)
+    nv = nc * n
+    K = max(args.steps, 1)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2504185260 + 7)
+    r = torch.randn((K, nv), dtype=torch.float64, device=dev, generator=gen)
+    dx = r + 0.1 * torch.randn((K, nv), dtype=torch.float64, device=dev, generator=gen)
+    cs = np.full(K, 3e-3)
+    hidden = 112
+    res = {}
+    clk = ClockSampler(dev.index or 0)
+    for mode, name in ((1, "bf16_tensor_core"), (0, "fp32_simt")):
+        m = S.sisdc_mlp_create(lv, hidden, seed=1, bf16=mode)
+        n_in, H, q, npar = S.sisdc_mlp_info(m)
+        rows = nv // q
+        S.sisdc_mlp_train(m, r, dx, cs, min(K, max(args.warmup, 1)), 1, 1e-3)
+        z = torch.zeros(nv, dtype=torch.float64, device=dev)
+        for _ in range(max(args.warmup, 1)):
+            S.sisdc_mlp_apply(m, r[0], 3e-3, z)
+        torch.cuda.synchronize()
+        if mode == 1:
+            clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.sisdc_mlp_train(m, r, dx, cs, K, 1, 1e-3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_train = e0.elapsed_time(e1) / K
+        e0.record(stream)
+        for k in range(K):
+            S.sisdc_mlp_apply(m, r[k], 3e-3, z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_inf = e0.elapsed_time(e1) / K
+        if mode == 1:
+            clocks = clk.stop()
+        f_inf, f_train = mlp_flops(rows, n_in, H, q)
+        res[name] = {"train_ms_per_step": t_train, "train_rows_per_s": rows / (t_train * 1e-3),
+                     "infer_ms": t_inf, "infer_rows_per_s": rows / (t_inf * 1e-3),
+                     "train_gemm_tflops": f_train / (t_train * 1e-3) / 1e12,
+                     "infer_gemm_tflops": f_inf / (t_inf * 1e-3) / 1e12}
+        S.sisdc_mlp_destroy(m)
+    ctx.close()
+    peak = 1940.5
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, pkind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, pkind = 1900.0, "fallback"
+    tc = res["bf16_tensor_core"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        o = run_oracle_child(args, 1)
+        cpu = {"value": o["rows"] / o["seconds"], "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": "%d FP64 numpy loss+gradient passes of the oracle MLP over 4096 rows (single-threaded "
+                         "BLAS), %.1f s" % (o["passes"], o["seconds"])}
+    print(json.dumps({
+        "metric": "MLP training rows/s", "value": tc["train_rows_per_s"], "unit": "rows/s", "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": tc["train_ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": "mlp_ns_level", "rows": rows, "layers": [n_in, H, H, q],
+                   "step": "one training step (loss, gradients, Adam) on one logged solve of the level",
+                   "l2": "weights L2-resident; each step reads a new 19 MB residual and correction pair"},
+        "roofline": {"bound": "tensor", "kernel": "k_gemm_tc (all GEMMs of a training step, with the step's other kernels in the time)",
+                     "achieved": tc["train_gemm_tflops"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": tc["train_gemm_tflops"] / peak, "traffic": None, "peak_kind": pkind + " bf16 dense"},
+        "forms": res, "cpu_baseline": cpu, "clocks": clocks,
+        "gpu_launches": None}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.oracle_sample:
-        if a.workload == "ensemble512":
+        if a.workload == "mlp_ns_level":
+            mlp_oracle_sample(a)
+        elif a.workload == "ensemble512":
             ensemble_oracle_sample(a)
         else:
             oracle_sample(a)
@@ -717,5 +834,7 @@ if __name__ == "__main__":
         ensemble_arm(a)
     elif a.workload == "stability_map":
         stability_arm(a)
+    elif a.workload == "mlp_ns_level":
+        mlp_arm(a)
     else:
         main_arm(a)

@@ -12,8 +12,13 @@ when c -> 0), scaled back by s:
 Loss: mean over samples of 0.5 * mean_q (MLP(x) - t)^2 with
 t = (dx - r_centre) / s.
 
+The optional round_op is applied to both operands of every matrix product
+(the BF16 mode of the CUDA kernels rounds them to bfloat16 as it stages them
+for the tensor cores; sums, biases and tanh stay in full precision).
+
 Pins (tests/test_oracle_mlp.py): gradients against central finite
-differences; patch gathering against direct indexing on a small mesh.
+differences; patch gathering against direct indexing on a small mesh;
+bf16_round against closed-form ties and the bfloat16 conversion of PyTorch.
 """
 import numpy as np
 
@@ -27,25 +32,40 @@ def init_params(n_in, hidden, n_out, seed):
             "W3": W3, "b3": np.zeros(n_out)}
 
 
-def forward(p, X):
-    h1 = np.tanh(X @ p["W1"] + p["b1"])
-    h2 = np.tanh(h1 @ p["W2"] + p["b2"])
-    y = h2 @ p["W3"] + p["b3"]
+def bf16_round(a):
+    """Nearest bfloat16 value (8 significand bits, ties to even) of a, taken
+    through its float32 bit pattern: add 0x7FFF plus the lowest kept bit to
+    the pattern, then clear the 16 dropped bits."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
+def forward(p, X, round_op=None):
+    R = round_op or _ident
+    h1 = np.tanh(R(X) @ R(p["W1"]) + p["b1"])
+    h2 = np.tanh(R(h1) @ R(p["W2"]) + p["b2"])
+    y = R(h2) @ R(p["W3"]) + p["b3"]
     return y, (X, h1, h2)
 
 
-def loss_and_grads(p, X, T):
+def loss_and_grads(p, X, T, round_op=None):
     """0.5 * mean over samples and outputs of (y - t)^2, and its gradients."""
-    y, (X, h1, h2) = forward(p, X)
+    R = round_op or _ident
+    y, (X, h1, h2) = forward(p, X, round_op)
     n, q = T.shape
     d = (y - T) / (n * q)
     loss = 0.5 * np.sum((y - T) ** 2) / (n * q)
-    g = {"W3": h2.T @ d, "b3": d.sum(axis=0)}
-    dh2 = (d @ p["W3"].T) * (1.0 - h2 * h2)
-    g["W2"] = h1.T @ dh2
+    g = {"W3": R(h2).T @ R(d), "b3": d.sum(axis=0)}
+    dh2 = (R(d) @ R(p["W3"]).T) * (1.0 - h2 * h2)
+    g["W2"] = R(h1).T @ R(dh2)
     g["b2"] = dh2.sum(axis=0)
-    dh1 = (dh2 @ p["W2"].T) * (1.0 - h1 * h1)
-    g["W1"] = X.T @ dh1
+    dh1 = (R(dh2) @ R(p["W2"]).T) * (1.0 - h1 * h1)
+    g["W1"] = R(X).T @ R(dh1)
     g["b1"] = dh1.sum(axis=0)
     return loss, g
 
@@ -70,8 +90,8 @@ def targets(field, dx, s, q):
     return (np.asarray(dx).reshape(-1, q) - np.asarray(field).reshape(-1, q)) / s[:, None]
 
 
-def apply(p, field, nex, ney, q, c, h):
+def apply(p, field, nex, ney, q, c, h, round_op=None):
     """z = r_centre + s * MLP(patch / s) for every element and component."""
     X, s = patches(field, nex, ney, q, c, h)
-    y, _ = forward(p, X)
+    y, _ = forward(p, X, round_op)
     return (np.asarray(field).reshape(-1, q) + y * s[:, None]).reshape(np.shape(field))

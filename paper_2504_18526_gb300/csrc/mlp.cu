@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -24,41 +25,60 @@ namespace sisdc {
 
 // ---- kernels ---------------------------------------------------------------
 
-// one block per row (element-component): gather, RMS scale, feature
-__global__ void k_mlp_patches(const double* __restrict__ f, int nc, int nex, int ney, int q, float feat,
-                              float* __restrict__ X, float* __restrict__ s, int n_in) {
-    __shared__ double scratch[32];
-    const long long row = blockIdx.x;
+// patch gathering in three elementwise passes (rows = element-components):
+// sum of squares of each row's q values; the patch scale s = RMS over the 3x3
+// patch from the nine neighbours' sums; then every input X[row][t] (the
+// patch values scaled by 1/s, and the feature) by one thread
+__global__ void k_mlp_elem_ss(const double* __restrict__ f, long long rows, int q, double* __restrict__ ss) {
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (long long)gridDim.x * blockDim.x) {
+        const double* v = f + row * q;
+        double a = 0.0;
+        for (int k = 0; k < q; ++k) a += v[k] * v[k];
+        ss[row] = a;
+    }
+}
+
+__global__ void k_mlp_scale(const double* __restrict__ ss, int nex, int ney, int q, long long rows,
+                            float* __restrict__ s, double* __restrict__ sinv) {
     const int nel = nex * ney;
-    const int c = (int)(row / nel);
-    const int e = (int)(row - (long long)c * nel);
-    const int ex = e % nex, ey = e / nex;
-    const long long N = (long long)nel * q;
-    double acc = 0.0;
-    for (int t = threadIdx.x; t < 9 * q; t += blockDim.x) {
-        const int k = t / q, node = t - k * q;
-        const int dy = k / 3 - 1, dx = k % 3 - 1;
-        const int en = ((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex;
-        const double v = f[c * N + (long long)en * q + node];
-        acc += v * v;
-    }
-    const double tot = block_sum(acc, scratch);
-    __shared__ double s_scale;
-    if (threadIdx.x == 0) {
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(row / nel), e = (int)(row - (long long)c * nel);
+        const int ex = e % nex, ey = e / nex;
+        double tot = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            const int dy = k / 3 - 1, dx = k % 3 - 1;
+            tot += ss[(long long)c * nel + ((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex];
+        }
         double sc = sqrt(tot / (9.0 * q));
-        s_scale = sc > 0.0 ? sc : 1.0;
-        s[row] = (float)s_scale;
+        sc = sc > 0.0 ? sc : 1.0;
+        s[row] = (float)sc;
+        sinv[row] = 1.0 / sc;
     }
-    __syncthreads();
-    const double inv = 1.0 / s_scale;
-    float* xr = X + row * n_in;
-    for (int t = threadIdx.x; t < 9 * q; t += blockDim.x) {
-        const int k = t / q, node = t - k * q;
-        const int dy = k / 3 - 1, dx = k % 3 - 1;
-        const int en = ((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex;
-        xr[t] = (float)(f[c * N + (long long)en * q + node] * inv);
+}
+
+__global__ void k_mlp_fill(const double* __restrict__ f, const double* __restrict__ sinv, int nex, int ney, int q,
+                           long long rows, int n_in, float feat, float* __restrict__ X) {
+    const int nel = nex * ney;
+    const long long N = (long long)nel * q;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int c = (int)(row / nel), e = (int)(row - (long long)c * nel);
+        const int ex = e % nex, ey = e / nex;
+        const double si = sinv[row];
+        const double* fc = f + c * N;
+        float* xr = X + row * n_in;
+        for (int t = threadIdx.x; t < n_in; t += blockDim.x) {
+            if (t == 9 * q) {
+                xr[t] = feat;
+                continue;
+            }
+            const int k = t / q, node = t - k * q;
+            const int dy = k / 3 - 1, dx = k % 3 - 1;
+            const int en = ((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex;
+            xr[t] = (float)(fc[(long long)en * q + node] * si);
+        }
     }
-    if (threadIdx.x == 0) xr[9 * q] = feat;
 }
 
 // targets t = (dx - r_centre) / s
@@ -142,6 +162,110 @@ __global__ void k_gemm(const TA* __restrict__ A, const TB* __restrict__ B, float
         }
 }
 
+// Tensor-core form of k_gemm for the BF16 mode: both operands are rounded to
+// BF16 while they are staged in shared memory and multiplied by warp-level
+// mma.sync m16n8k16 (BF16 x BF16 -> FP32 accumulate).  Block tile 64x64,
+// K slices of 32, 4 warps each owning a 32x32 sub-tile (2 x 4 MMA tiles).
+// kz > 1 (split-K): block z covers K slices [z * kchunk, (z+1) * kchunk) and
+// writes its partial product to C + z * M * N (row-major M x N, no epilogue);
+// k_splitk_sum adds the partials in a fixed order.
+constexpr int TC_BM = 64, TC_BN = 64, TC_BK = 32, TC_PAD = 8;
+
+__device__ __forceinline__ void mma_bf16_16816(float* d, const unsigned* a, const unsigned* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <class TA, class TB>
+__global__ void __launch_bounds__(128) k_gemm_tc(const TA* __restrict__ A, const TB* __restrict__ B,
+                                                 float* __restrict__ C, const float* bias, int M, int N, int K,
+                                                 int lda, int ldb, int ldc, int ta, int tb, int epi, int kchunk) {
+    __shared__ __align__(16) __nv_bfloat16 As[TC_BM][TC_BK + TC_PAD];   // [m][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[TC_BN][TC_BK + TC_PAD];   // [n][k]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    float acc[2][4][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
+        // stage op(A)[m0.., k0..] and op(B)[k0.., n0..]; consecutive threads
+        // walk the operand's contiguous index
+        for (int t = threadIdx.x; t < TC_BM * TC_BK; t += blockDim.x) {
+            int mm, kk;
+            if (ta) { kk = t / TC_BM; mm = t - kk * TC_BM; } else { mm = t / TC_BK; kk = t - mm * TC_BK; }
+            const int m = m0 + mm, k = k0 + kk;
+            float v = 0.f;
+            if (m < M && k < kend) v = ld_as_float<TA>(A, ta ? (long long)k * lda + m : (long long)m * lda + k);
+            As[mm][kk] = __float2bfloat16_rn(v);
+        }
+        for (int t = threadIdx.x; t < TC_BN * TC_BK; t += blockDim.x) {
+            int nn, kk;
+            if (tb) { nn = t / TC_BK; kk = t - nn * TC_BK; } else { kk = t / TC_BN; nn = t - kk * TC_BN; }
+            const int n = n0 + nn, k = k0 + kk;
+            float v = 0.f;
+            if (n < N && k < kend) v = ld_as_float<TB>(B, tb ? (long long)n * ldb + k : (long long)k * ldb + n);
+            Bs[nn][kk] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TC_BK; kk += 16) {
+            unsigned af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + g;
+                af[i][0] = *reinterpret_cast<const unsigned*>(&As[r][kk + 2 * t4]);
+                af[i][1] = *reinterpret_cast<const unsigned*>(&As[r + 8][kk + 2 * t4]);
+                af[i][2] = *reinterpret_cast<const unsigned*>(&As[r][kk + 2 * t4 + 8]);
+                af[i][3] = *reinterpret_cast<const unsigned*>(&As[r + 8][kk + 2 * t4 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + g;
+                bfr[j][0] = *reinterpret_cast<const unsigned*>(&Bs[c][kk + 2 * t4]);
+                bfr[j][1] = *reinterpret_cast<const unsigned*>(&Bs[c][kk + 2 * t4 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    float* Cz = gridDim.z > 1 ? C + (size_t)blockIdx.z * M * N : C;
+    const int ldz = gridDim.z > 1 ? N : ldc;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int m = m0 + wm + i * 16 + g + (h >> 1) * 8;
+                const int n = n0 + wn + j * 8 + 2 * t4 + (h & 1);
+                if (m < M && n < N) {
+                    float v = acc[i][j][h];
+                    if (gridDim.z == 1) {
+                        if (epi >= EPI_BIAS) v += bias[n];
+                        if (epi == EPI_BIAS_TANH) v = tanhf(v);
+                    }
+                    Cz[(long long)m * ldz + n] = v;
+                }
+            }
+}
+
+// C[m][n] = sum over z of the split-K partials P[z][m][n] (fixed order)
+__global__ void k_splitk_sum(const float* __restrict__ P, int nz, int M, int N, float* __restrict__ C, int ldc) {
+    const long long mn = (long long)M * N;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < mn; t += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < nz; ++z) v += P[z * mn + t];
+        C[(t / N) * ldc + t % N] = v;
+    }
+}
+
 // dY = (Y - T) / (rows * q); loss partials
 __global__ void k_mlp_loss(const float* __restrict__ Y, const float* __restrict__ T, long long n, float scale,
                            float* __restrict__ dY, double* __restrict__ partial) {
@@ -156,6 +280,15 @@ __global__ void k_mlp_loss(const float* __restrict__ Y, const float* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// *acc += scale * (sum of the n partials, in order)
+__global__ void k_loss_acc(const double* __restrict__ partial, int n, double scale, double* __restrict__ acc) {
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += partial[b];
+        *acc += scale * s;
+    }
+}
+
 // dH *= (1 - H^2) (tanh derivative)
 __global__ void k_tanh_back(const float* __restrict__ H, float* __restrict__ dH, long long n) {
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
@@ -163,12 +296,33 @@ __global__ void k_tanh_back(const float* __restrict__ H, float* __restrict__ dH,
 }
 
 // column sums (bias gradients), one thread per column, fixed order
-__global__ void k_colsum(const float* __restrict__ D, int rows, int cols, float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+// column sums of D[rows][cols] in two deterministic passes: block (x, y)
+// sums rows [y*chunk, (y+1)*chunk) of 32 columns with 8 row lanes (coalesced
+// 32-column rows), partial[y][col]; then out[col] = sum over y in order
+constexpr int COLSUM_CHUNKS = 64;
+
+__global__ void k_colsum_part(const float* __restrict__ D, int rows, int cols, int chunk, float* __restrict__ part) {
+    __shared__ float sh[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
     float s = 0.f;
-    for (int i = 0; i < rows; ++i) s += D[(long long)i * cols + j];
-    out[j] = s;
+    if (c < cols)
+        for (int i = r0 + threadIdx.y; i < r1; i += 8) s += D[(long long)i * cols + c];
+    sh[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
+        part[(long long)blockIdx.y * cols + c] = t;
+    }
+}
+
+__global__ void k_colsum_fin(const float* __restrict__ part, int nchunk, int cols, float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int k = 0; k < nchunk; ++k) s += part[(long long)k * cols + c];
+    out[c] = s;
 }
 
 // Adam step on FP32 master weights; refresh the BF16 copy
@@ -212,6 +366,9 @@ struct sisdc_mlp_s {
     float *X = nullptr, *H1 = nullptr, *H2 = nullptr, *Y = nullptr, *T = nullptr, *dY = nullptr, *dH = nullptr,
           *s = nullptr;
     double* part = nullptr;
+    float* ws = nullptr;            // split-K partials of the tensor-core GEMMs
+    double *ss = nullptr, *sinv = nullptr;   // per-row sums of squares, 1 / patch scale
+    double* lacc = nullptr;                  // loss accumulator of a training epoch
     long long adam_t = 0;
     std::string err;
     // offsets
@@ -231,12 +388,49 @@ void mck(sisdc_mlp_s* p, cudaError_t e, const char* what) {
     }
 }
 
+// split-K workspace limit (floats)
+constexpr long long MLP_SPLITK_WS = 1ll << 22;
+
+// C = op(A) op(B) (+ bias, tanh): tensor cores in the BF16 mode (split-K when
+// the output has too few tiles for the GPU and K is long, as for the weight
+// gradients whose reduction runs over all rows), FP32 SIMT otherwise
 template <class TB>
 void gemm(sisdc_mlp_s* p, const float* A, const TB* B, float* C, const float* bias, int M, int N, int K, int lda,
           int ldb, int ldc, int ta, int tb, int epi) {
     dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<float, TB><<<grid, 256, 0, p->stream>>>(A, B, C, bias, M, N, K, lda, ldb, ldc, ta, tb, epi);
-    mck(p, cudaGetLastError(), "gemm");
+    if (!p->bf16) {
+        k_gemm<float, TB><<<grid, 256, 0, p->stream>>>(A, B, C, bias, M, N, K, lda, ldb, ldc, ta, tb, epi);
+        mck(p, cudaGetLastError(), "gemm");
+        return;
+    }
+    const long long tiles = (long long)grid.x * grid.y;
+    int kz = 1;
+    if (epi == EPI_NONE && tiles < 152 && K >= 8 * TC_BK) {
+        kz = (int)std::min<long long>((2 * 152 + tiles - 1) / tiles, K / (4 * TC_BK));
+        kz = (int)std::min<long long>(kz, MLP_SPLITK_WS / ((long long)M * N));
+        if (kz < 1) kz = 1;
+    }
+    int kchunk = (K + kz - 1) / kz;
+    kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
+    kz = (K + kchunk - 1) / kchunk;
+    grid.z = (unsigned)kz;
+    k_gemm_tc<float, TB><<<grid, 128, 0, p->stream>>>(A, B, kz > 1 ? p->ws : C, bias, M, N, K, lda, ldb, ldc, ta,
+                                                     tb, epi, kchunk);
+    mck(p, cudaGetLastError(), "gemm_tc");
+    if (kz > 1) {
+        k_splitk_sum<<<ew((long long)M * N), 256, 0, p->stream>>>(p->ws, kz, M, N, C, ldc);
+        mck(p, cudaGetLastError(), "splitk_sum");
+    }
+}
+
+// out[c] = sum over rows of D[row][c] (bias gradients); the split-K
+// workspace holds the partial sums
+void colsum(sisdc_mlp_s* p, const float* D, int rows, int cols, float* out) {
+    const int chunk = (rows + COLSUM_CHUNKS - 1) / COLSUM_CHUNKS;
+    const int nchunk = (rows + chunk - 1) / chunk;
+    k_colsum_part<<<dim3((cols + 31) / 32, nchunk), dim3(32, 8), 0, p->stream>>>(D, rows, cols, chunk, p->ws);
+    k_colsum_fin<<<(cols + 127) / 128, 128, 0, p->stream>>>(p->ws, nchunk, cols, out);
+    mck(p, cudaGetLastError(), "colsum");
 }
 
 // forward on p->X (rows) -> p->Y; hidden activations kept for backward
@@ -261,25 +455,29 @@ void forward(sisdc_mlp_s* p) {
 
 void gather(sisdc_mlp_s* p, const double* field, double c) {
     const float feat = (float)(0.1 * std::log(c / (p->h * p->h)));
-    k_mlp_patches<<<(unsigned)p->rows, 128, 0, p->stream>>>(field, p->nc, p->nex, p->ney, p->q, feat, p->X, p->s,
-                                                            p->n_in);
+    k_mlp_elem_ss<<<ew(p->rows), 256, 0, p->stream>>>(field, p->rows, p->q, p->ss);
+    k_mlp_scale<<<ew(p->rows), 256, 0, p->stream>>>(p->ss, p->nex, p->ney, p->q, p->rows, p->s, p->sinv);
+    const unsigned fb = (unsigned)std::min<long long>(p->rows, 152LL * 16);
+    k_mlp_fill<<<fb, 128, 0, p->stream>>>(field, p->sinv, p->nex, p->ney, p->q, p->rows, p->n_in, feat, p->X);
     mck(p, cudaGetLastError(), "patches");
 }
 
-// loss and gradients (into p->grad) for inputs gathered from r and targets dx/s
-double loss_grad(sisdc_mlp_s* p, const double* r, const double* dx, double c) {
+// loss partials (p->part) and gradients (into p->grad) for inputs gathered
+// from r and targets dx/s; asynchronous
+constexpr int LOSS_NB = 256;
+void loss_grad_dev(sisdc_mlp_s* p, const double* r, const double* dx, double c) {
     gather(p, r, c);
     const long long nq = p->rows * p->q;
     k_mlp_targets<<<ew(nq), 256, 0, p->stream>>>(dx, r, p->s, p->q, p->rows, p->T);
     forward(p);
-    const int nb = 256;
+    const int nb = LOSS_NB;
     k_mlp_loss<<<nb, 256, 0, p->stream>>>(p->Y, p->T, nq, 1.f / (float)nq, p->dY, p->part);
     mck(p, cudaGetLastError(), "loss");
     const int R = (int)p->rows;
     float* g = p->grad;
     // layer 3: dW3 = H2^T dY, db3 = colsum dY, dH2 = dY W3^T
     gemm<float>(p, p->H2, p->dY, g + p->oW3, nullptr, p->H, p->q, R, p->H, p->q, p->q, 1, 0, EPI_NONE);
-    k_colsum<<<(p->q + 127) / 128, 128, 0, p->stream>>>(p->dY, R, p->q, g + p->ob3);
+    colsum(p, p->dY, R, p->q, g + p->ob3);
     if (p->bf16)
         gemm<__nv_bfloat16>(p, p->dY, p->theta_b + p->oW3, p->dH, nullptr, R, p->H, p->q, p->q, p->q, p->H, 0, 1,
                             EPI_NONE);
@@ -288,7 +486,7 @@ double loss_grad(sisdc_mlp_s* p, const double* r, const double* dx, double c) {
     k_tanh_back<<<ew((long long)R * p->H), 256, 0, p->stream>>>(p->H2, p->dH, (long long)R * p->H);
     // layer 2
     gemm<float>(p, p->H1, p->dH, g + p->oW2, nullptr, p->H, p->H, R, p->H, p->H, p->H, 1, 0, EPI_NONE);
-    k_colsum<<<(p->H + 127) / 128, 128, 0, p->stream>>>(p->dH, R, p->H, g + p->ob2);
+    colsum(p, p->dH, R, p->H, g + p->ob2);
     // dH1 = dH2 W2^T (reuse H2 as scratch for dH1: H2 no longer needed)
     if (p->bf16)
         gemm<__nv_bfloat16>(p, p->dH, p->theta_b + p->oW2, p->H2, nullptr, R, p->H, p->H, p->H, p->H, p->H, 0, 1,
@@ -298,14 +496,19 @@ double loss_grad(sisdc_mlp_s* p, const double* r, const double* dx, double c) {
     k_tanh_back<<<ew((long long)R * p->H), 256, 0, p->stream>>>(p->H1, p->H2, (long long)R * p->H);
     // layer 1
     gemm<float>(p, p->X, p->H2, g + p->oW1, nullptr, p->n_in, p->H, R, p->n_in, p->H, p->H, 1, 0, EPI_NONE);
-    k_colsum<<<(p->H + 127) / 128, 128, 0, p->stream>>>(p->H2, R, p->H, g + p->ob1);
+    colsum(p, p->H2, R, p->H, g + p->ob1);
     mck(p, cudaGetLastError(), "backward");
-    std::vector<double> hp(nb);
-    mck(p, cudaMemcpyAsync(hp.data(), p->part, nb * sizeof(double), cudaMemcpyDeviceToHost, p->stream), "copy");
+}
+
+// loss of one sample set, read back (synchronous)
+double loss_grad(sisdc_mlp_s* p, const double* r, const double* dx, double c) {
+    loss_grad_dev(p, r, dx, c);
+    std::vector<double> hp(LOSS_NB);
+    mck(p, cudaMemcpyAsync(hp.data(), p->part, LOSS_NB * sizeof(double), cudaMemcpyDeviceToHost, p->stream), "copy");
     mck(p, cudaStreamSynchronize(p->stream), "sync");
     double l = 0.0;
-    for (int b = 0; b < nb; ++b) l += hp[b];
-    return 0.5 * l / (double)nq;
+    for (int b = 0; b < LOSS_NB; ++b) l += hp[b];
+    return 0.5 * l / (double)(p->rows * p->q);
 }
 
 }  // namespace
@@ -381,6 +584,10 @@ sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long see
     al((void**)&p->dY, R * p->q * sizeof(float));
     al((void**)&p->s, R * sizeof(float));
     al((void**)&p->part, 256 * sizeof(double));
+    al((void**)&p->ws, MLP_SPLITK_WS * sizeof(float));
+    al((void**)&p->ss, R * sizeof(double));
+    al((void**)&p->sinv, R * sizeof(double));
+    al((void**)&p->lacc, sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(p->theta, w.data(), p->nparam * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->m, 0, p->nparam * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(p->v, 0, p->nparam * sizeof(float));
@@ -401,7 +608,8 @@ void sisdc_mlp_destroy(sisdc_mlp p) {
     cudaDeviceSynchronize();
     cudaFree(p->theta); cudaFree(p->grad); cudaFree(p->m); cudaFree(p->v); cudaFree(p->theta_b);
     cudaFree(p->X); cudaFree(p->H1); cudaFree(p->H2); cudaFree(p->dH); cudaFree(p->Y); cudaFree(p->T);
-    cudaFree(p->dY); cudaFree(p->s); cudaFree(p->part);
+    cudaFree(p->dY); cudaFree(p->s); cudaFree(p->part); cudaFree(p->ws);
+    cudaFree(p->ss); cudaFree(p->sinv); cudaFree(p->lacc);
     delete p;
 }
 
@@ -448,10 +656,12 @@ sisdc_status sisdc_mlp_train(sisdc_mlp p, const double* d_r, const double* d_dx,
     try {
         double last = 0.0;
         for (int ep = 0; ep < epochs; ++ep) {
-            double sum = 0.0;
+            // the epoch's losses are summed on the device (fixed order) and read once
+            mck(p, cudaMemsetAsync(p->lacc, 0, sizeof(double), p->stream), "memset");
             for (int k = 0; k < nsolves; ++k) {
                 if (!(h_c[k] > 0.0)) continue;
-                sum += loss_grad(p, d_r + (long long)k * nv, d_dx + (long long)k * nv, h_c[k]);
+                loss_grad_dev(p, d_r + (long long)k * nv, d_dx + (long long)k * nv, h_c[k]);
+                k_loss_acc<<<1, 32, 0, p->stream>>>(p->part, LOSS_NB, 0.5 / (double)(p->rows * p->q), p->lacc);
                 ++p->adam_t;
                 const float b1 = 0.9f, b2 = 0.999f;
                 const float c1 = 1.f - std::pow(b1, (float)p->adam_t), c2 = 1.f - std::pow(b2, (float)p->adam_t);
@@ -459,6 +669,9 @@ sisdc_status sisdc_mlp_train(sisdc_mlp p, const double* d_r, const double* d_dx,
                                                               (float)lr, b1, b2, 1e-8f, c1, c2);
                 mck(p, cudaGetLastError(), "adam");
             }
+            double sum = 0.0;
+            mck(p, cudaMemcpyAsync(&sum, p->lacc, sizeof(double), cudaMemcpyDeviceToHost, p->stream), "copy");
+            mck(p, cudaStreamSynchronize(p->stream), "sync");
             last = sum / nsolves;
         }
         mck(p, cudaStreamSynchronize(p->stream), "sync");

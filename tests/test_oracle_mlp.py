@@ -1,6 +1,8 @@
 """Pins for the oracle's element-patch MLP (CPU only): gradients against
-central finite differences, patch gathering against direct indexing."""
+central finite differences, patch gathering against direct indexing,
+the bfloat16 rounding of the BF16 mode against closed forms and PyTorch."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 
@@ -59,3 +61,38 @@ def test_training_reduces_loss_on_a_linear_target():
             p[k] -= 0.5 * g[k]
     l1, _ = mlp.loss_and_grads(p, X, T)
     assert l1 < 0.2 * l0
+
+
+def test_bf16_round_closed_forms_and_library():
+    """bf16_round: ties to even at closed-form halfway points, exact on values
+    that fit 8 bits, overflow to infinity, and the same bits as PyTorch's
+    bfloat16 conversion on random float32 values."""
+    from oracle.mlp import bf16_round
+    assert bf16_round(1.0 + 2.0 ** -8) == 1.0                       # tie, even neighbour 1.0
+    assert bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6       # tie, rounds up to even
+    assert bf16_round(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert bf16_round(-(1.0 + 2.0 ** -9)) == -1.0
+    assert bf16_round(1.5) == 1.5 and bf16_round(0.0) == 0.0 and bf16_round(-3.0 * 2.0 ** -100) == -3.0 * 2.0 ** -100
+    assert np.isinf(bf16_round(3.4e38))
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal(100000) * np.exp(rng.uniform(-30, 30, 100000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(bf16_round(x), ref)
+
+
+def test_round_op_identity_is_the_plain_network():
+    """With round_op = None the forward pass and gradients are the plain FP64
+    network (the form pinned by finite differences above), and rounding every
+    operand to bfloat16 moves them by the size of one bfloat16 rounding."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(9)
+    p = M.init_params(12, 8, 4, 3)
+    X = rng.standard_normal((20, 12))
+    T = rng.standard_normal((20, 4))
+    l0, g0 = M.loss_and_grads(p, X, T)
+    l1, g1 = M.loss_and_grads(p, X, T, round_op=lambda a: a)
+    assert l0 == l1 and all(np.array_equal(g0[k], g1[k]) for k in g0)
+    lb, gb = M.loss_and_grads(p, X, T, round_op=M.bf16_round)
+    rel = np.linalg.norm(gb["W1"] - g0["W1"]) / np.linalg.norm(g0["W1"])
+    assert 1e-5 < rel < 3e-2 and abs(lb - l0) < 3e-2 * abs(l0)
