@@ -469,6 +469,20 @@ sisdc_status sisdc_stability(const sisdc_stab_opts* opts, const double* d_z, dou
  * unknown kind, n < 0 or a null pointer with n > 0. */
 sisdc_status sisdc_convert(int kind, const void* d_in, long long n, void* d_out, void* cuda_stream);
 
+/* --- failure detection of the bounded grid barrier -------------------------
+ *
+ * Every persistent kernel synchronises its blocks with a grid barrier whose
+ * wait is bounded (2 s of the global timer, or 2^24 polls); a block whose
+ * wait runs out records SISDC_E_TIMEOUT for sisdc_sync and leaves the
+ * kernel, so the context stays usable.  This entry exercises that path:
+ * it launches a cooperative kernel of `nblocks` blocks (1..number of SMs)
+ * that meet at one barrier, except block `absent` (absent < 0: none), which
+ * never arrives; the other blocks' wait then runs out after `timeout_ms`
+ * (1..2000).  Synchronous on `cuda_stream`.  Returns SISDC_OK if the
+ * barrier completed, SISDC_E_TIMEOUT if the wait gave up, SISDC_E_ARG for
+ * arguments out of range, SISDC_E_CUDA for launch errors. */
+sisdc_status sisdc_barrier_selftest(int nblocks, int absent, double timeout_ms, void* cuda_stream);
+
 /* Message of the last failing call on this context ("" if none). */
 const char* sisdc_last_error(sisdc_ctx ctx);
 

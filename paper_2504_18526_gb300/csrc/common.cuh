@@ -123,6 +123,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // On timeout the block records DEV_TIMEOUT in *err and returns false; callers
 // then leave the kernel, so that every wait in the grid ends.
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;   // 2 s
+// second bound on the polls, in case the global timer does not advance
+// (about 10-15 s of L2 round trips)
+constexpr unsigned BARRIER_MAX_SPINS = 1u << 24;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
@@ -136,7 +139,8 @@ __device__ __forceinline__ unsigned atom_add_release_gpu(unsigned* p, unsigned v
     return old;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* /*exits*/, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* /*exits*/, int* err,
+                                             unsigned long long timeout_ns = BARRIER_TIMEOUT_NS) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -148,7 +152,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* /*exits*
             const unsigned long long t0 = globaltimer_ns();
             unsigned spins = 0;
             while (ld_acquire_gpu(count) < target) {
-                if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                if ((++spins & 255u) == 0u && (globaltimer_ns() - t0 > timeout_ns || spins >= BARRIER_MAX_SPINS)) {
                     atomicOr(err, DEV_TIMEOUT);
                     ok = 0;
                     break;

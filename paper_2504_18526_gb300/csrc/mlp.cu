@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/sisdc.h"
+#include "ds.cuh"
 #include "ops.h"
 
 namespace sisdc {
@@ -40,7 +41,7 @@ __global__ void k_mlp_elem_ss(const double* __restrict__ f, long long rows, int 
 }
 
 __global__ void k_mlp_scale(const double* __restrict__ ss, int nex, int ney, int q, long long rows,
-                            float* __restrict__ s, double* __restrict__ sinv) {
+                            float* __restrict__ s, float* __restrict__ sinv) {
     const int nel = nex * ney;
     for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
          row += (long long)gridDim.x * blockDim.x) {
@@ -54,18 +55,20 @@ __global__ void k_mlp_scale(const double* __restrict__ ss, int nex, int ney, int
         double sc = sqrt(tot / (9.0 * q));
         sc = sc > 0.0 ? sc : 1.0;
         s[row] = (float)sc;
-        sinv[row] = 1.0 / sc;
+        sinv[row] = (float)(1.0 / sc);
     }
 }
 
-__global__ void k_mlp_fill(const double* __restrict__ f, const double* __restrict__ sinv, int nex, int ney, int q,
+// (FP32 arithmetic: the value rounded to FP32 on the integer pipe, then
+// scaled; GB300's FP64 unit would otherwise set this kernel's time)
+__global__ void k_mlp_fill(const double* __restrict__ f, const float* __restrict__ sinv, int nex, int ney, int q,
                            long long rows, int n_in, float feat, float* __restrict__ X) {
     const int nel = nex * ney;
     const long long N = (long long)nel * q;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int c = (int)(row / nel), e = (int)(row - (long long)c * nel);
         const int ex = e % nex, ey = e / nex;
-        const double si = sinv[row];
+        const float si = sinv[row];
         const double* fc = f + c * N;
         float* xr = X + row * n_in;
         for (int t = threadIdx.x; t < n_in; t += blockDim.x) {
@@ -76,7 +79,7 @@ __global__ void k_mlp_fill(const double* __restrict__ f, const double* __restric
             const int k = t / q, node = t - k * q;
             const int dy = k / 3 - 1, dx = k % 3 - 1;
             const int en = ((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex;
-            xr[t] = (float)(fc[(long long)en * q + node] * si);
+            xr[t] = d2f_int(fc[(long long)en * q + node]) * si;
         }
     }
 }
@@ -86,7 +89,7 @@ __global__ void k_mlp_targets(const double* __restrict__ dx, const double* __res
                               int q, long long rows, float* __restrict__ T) {
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < rows * q; k += (long long)gridDim.x * blockDim.x) {
         const long long row = k / q;
-        T[k] = (float)((dx[k] - r[k]) / (double)s[row]);
+        T[k] = d2f_int(dx[k] - r[k]) / s[row];
     }
 }
 
@@ -94,7 +97,7 @@ __global__ void k_mlp_targets(const double* __restrict__ dx, const double* __res
 __global__ void k_mlp_scatter(const float* __restrict__ Y, const float* __restrict__ s, const double* __restrict__ r,
                               int q, long long rows, double* __restrict__ z, int add) {
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < rows * q; k += (long long)gridDim.x * blockDim.x) {
-        const double v = r[k] + (double)Y[k] * (double)s[k / q];
+        const double v = r[k] + f2d_int(Y[k] * s[k / q]);
         z[k] = add ? z[k] + v : v;
     }
 }
@@ -179,38 +182,57 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, const unsigned* a, cons
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <class TA, class TB>
-__global__ void __launch_bounds__(128) k_gemm_tc(const TA* __restrict__ A, const TB* __restrict__ B,
+template <class TA, class TB, bool ta, bool tb>
+__global__ void __launch_bounds__(128, 4) k_gemm_tc(const TA* __restrict__ A, const TB* __restrict__ B,
                                                  float* __restrict__ C, const float* bias, int M, int N, int K,
-                                                 int lda, int ldb, int ldc, int ta, int tb, int epi, int kchunk) {
+                                                 int lda, int ldb, int ldc, int epi, int kchunk) {
     __shared__ __align__(16) __nv_bfloat16 As[TC_BM][TC_BK + TC_PAD];   // [m][k]
     __shared__ __align__(16) __nv_bfloat16 Bs[TC_BN][TC_BK + TC_PAD];   // [n][k]
+    constexpr int PER = TC_BM * TC_BK / 128;                           // staged elements per thread and operand
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t4 = lane & 3;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
     const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-    float acc[2][4][4] = {};
-    for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
-        // stage op(A)[m0.., k0..] and op(B)[k0.., n0..]; consecutive threads
-        // walk the operand's contiguous index
-        for (int t = threadIdx.x; t < TC_BM * TC_BK; t += blockDim.x) {
+    // staging slot i of this thread: consecutive threads walk the operand's
+    // contiguous index (k for row-major A, m for transposed A; n / k for B)
+    auto slotA = [&](int i, int& mm, int& kk) {
+        const int t = threadIdx.x + i * 128;
+        if constexpr (ta) { kk = t / TC_BM; mm = t - kk * TC_BM; } else { mm = t / TC_BK; kk = t - mm * TC_BK; }
+    };
+    auto slotB = [&](int i, int& nn, int& kk) {
+        const int t = threadIdx.x + i * 128;
+        if constexpr (tb) { nn = t / TC_BK; kk = t - nn * TC_BK; } else { kk = t / TC_BN; nn = t - kk * TC_BN; }
+    };
+    float ra[PER], rb[PER];
+    // global -> registers for the slice at k0 (all loads issued before use)
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
             int mm, kk;
-            if (ta) { kk = t / TC_BM; mm = t - kk * TC_BM; } else { mm = t / TC_BK; kk = t - mm * TC_BK; }
+            slotA(i, mm, kk);
             const int m = m0 + mm, k = k0 + kk;
-            float v = 0.f;
-            if (m < M && k < kend) v = ld_as_float<TA>(A, ta ? (long long)k * lda + m : (long long)m * lda + k);
-            As[mm][kk] = __float2bfloat16_rn(v);
+            ra[i] = (m < M && k < kend) ? ld_as_float<TA>(A, ta ? (long long)k * lda + m : (long long)m * lda + k) : 0.f;
+            int nn, kb;
+            slotB(i, nn, kb);
+            const int n = n0 + nn, kq = k0 + kb;
+            rb[i] = (n < N && kq < kend) ? ld_as_float<TB>(B, tb ? (long long)n * ldb + kq : (long long)kq * ldb + n) : 0.f;
         }
-        for (int t = threadIdx.x; t < TC_BN * TC_BK; t += blockDim.x) {
-            int nn, kk;
-            if (tb) { nn = t / TC_BK; kk = t - nn * TC_BK; } else { kk = t / TC_BN; nn = t - kk * TC_BN; }
-            const int n = n0 + nn, k = k0 + kk;
-            float v = 0.f;
-            if (n < N && k < kend) v = ld_as_float<TB>(B, tb ? (long long)n * ldb + k : (long long)k * ldb + n);
-            Bs[nn][kk] = __float2bfloat16_rn(v);
+    };
+    float acc[2][4][4] = {};
+    if (kbeg < kend) fetch(kbeg);
+    for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            int mm, kk;
+            slotA(i, mm, kk);
+            As[mm][kk] = __float2bfloat16_rn(ra[i]);
+            int nn, kb;
+            slotB(i, nn, kb);
+            Bs[nn][kb] = __float2bfloat16_rn(rb[i]);
         }
         __syncthreads();
+        if (k0 + TC_BK < kend) fetch(k0 + TC_BK);     // next slice in flight during the MMAs
 #pragma unroll
         for (int kk = 0; kk < TC_BK; kk += 16) {
             unsigned af[2][4], bfr[4][2];
@@ -367,7 +389,8 @@ struct sisdc_mlp_s {
           *s = nullptr;
     double* part = nullptr;
     float* ws = nullptr;            // split-K partials of the tensor-core GEMMs
-    double *ss = nullptr, *sinv = nullptr;   // per-row sums of squares, 1 / patch scale
+    double* ss = nullptr;                    // per-row sums of squares
+    float* sinv = nullptr;                   // 1 / patch scale
     double* lacc = nullptr;                  // loss accumulator of a training epoch
     long long adam_t = 0;
     std::string err;
@@ -406,7 +429,7 @@ void gemm(sisdc_mlp_s* p, const float* A, const TB* B, float* C, const float* bi
     const long long tiles = (long long)grid.x * grid.y;
     int kz = 1;
     if (epi == EPI_NONE && tiles < 152 && K >= 8 * TC_BK) {
-        kz = (int)std::min<long long>((2 * 152 + tiles - 1) / tiles, K / (4 * TC_BK));
+        kz = (int)std::min<long long>((8 * 152 + tiles - 1) / tiles, K / (4 * TC_BK));
         kz = (int)std::min<long long>(kz, MLP_SPLITK_WS / ((long long)M * N));
         if (kz < 1) kz = 1;
     }
@@ -414,8 +437,15 @@ void gemm(sisdc_mlp_s* p, const float* A, const TB* B, float* C, const float* bi
     kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
     kz = (K + kchunk - 1) / kchunk;
     grid.z = (unsigned)kz;
-    k_gemm_tc<float, TB><<<grid, 128, 0, p->stream>>>(A, B, kz > 1 ? p->ws : C, bias, M, N, K, lda, ldb, ldc, ta,
-                                                     tb, epi, kchunk);
+    float* out = kz > 1 ? p->ws : C;
+    if (!ta && !tb)
+        k_gemm_tc<float, TB, false, false><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+    else if (ta && !tb)
+        k_gemm_tc<float, TB, true, false><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+    else if (!ta && tb)
+        k_gemm_tc<float, TB, false, true><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+    else
+        k_gemm_tc<float, TB, true, true><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
     mck(p, cudaGetLastError(), "gemm_tc");
     if (kz > 1) {
         k_splitk_sum<<<ew((long long)M * N), 256, 0, p->stream>>>(p->ws, kz, M, N, C, ldc);
@@ -586,7 +616,7 @@ sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long see
     al((void**)&p->part, 256 * sizeof(double));
     al((void**)&p->ws, MLP_SPLITK_WS * sizeof(float));
     al((void**)&p->ss, R * sizeof(double));
-    al((void**)&p->sinv, R * sizeof(double));
+    al((void**)&p->sinv, R * sizeof(float));
     al((void**)&p->lacc, sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(p->theta, w.data(), p->nparam * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->m, 0, p->nparam * sizeof(float));

@@ -13,6 +13,13 @@
 
 namespace sisdc {
 
+// one grid barrier that block `absent` skips (failure-detection test)
+__global__ void k_barrier_selftest(unsigned* count, unsigned* exits, int* err, int absent,
+                                   unsigned long long timeout_ns) {
+    if ((int)blockIdx.x != absent) grid_barrier(count, exits, err, timeout_ns);
+    grid_exit(count, exits);
+}
+
 __global__ void k_convert(int kind, const void* in, long long n, void* out) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         if (kind == 0) {
@@ -272,4 +279,35 @@ extern "C" sisdc_status sisdc_convert(int kind, const void* d_in, long long n, v
     if (n == 0) return SISDC_OK;
     k_convert<<<ew_grid(n, 256), 256, 0, (cudaStream_t)cuda_stream>>>(kind, d_in, n, d_out);
     return cudaGetLastError() == cudaSuccess ? SISDC_OK : SISDC_E_CUDA;
+}
+
+extern "C" sisdc_status sisdc_barrier_selftest(int nblocks, int absent, double timeout_ms, void* cuda_stream) {
+    using namespace sisdc;
+    int dev = 0, nsm = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SISDC_E_CUDA;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop || nblocks < 1 || nblocks > nsm || absent >= nblocks || !(timeout_ms >= 1.0 && timeout_ms <= 2000.0))
+        return SISDC_E_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned* words = nullptr;   // count, exits, err
+    if (cudaMalloc(&words, 3 * sizeof(unsigned)) != cudaSuccess) return SISDC_E_CUDA;
+    sisdc_status out = SISDC_OK;
+    if (cudaMemsetAsync(words, 0, 3 * sizeof(unsigned), st) != cudaSuccess) out = SISDC_E_CUDA;
+    unsigned* count = words;
+    unsigned* exits = words + 1;
+    int* err = reinterpret_cast<int*>(words + 2);
+    unsigned long long tns = (unsigned long long)(timeout_ms * 1e6);
+    void* args[] = {&count, &exits, &err, &absent, &tns};
+    if (out == SISDC_OK &&
+        cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3((unsigned)nblocks), dim3(32), args, 0, st) !=
+            cudaSuccess)
+        out = SISDC_E_CUDA;
+    int h_err = 0;
+    if (out == SISDC_OK && (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                            cudaStreamSynchronize(st) != cudaSuccess))
+        out = SISDC_E_CUDA;
+    cudaFree(words);
+    if (out != SISDC_OK) return out;
+    return (h_err & DEV_TIMEOUT) ? SISDC_E_TIMEOUT : SISDC_OK;
 }

@@ -124,6 +124,7 @@ def load():
         "sisdc_autotune": (c_int, [c_void_p, c_void_p, c_double, c_int, c_void_p]),
         "sisdc_stability": (c_int, [P(sisdc_stab_opts), c_void_p, c_void_p, c_ll, c_void_p]),
         "sisdc_convert": (c_int, [c_int, c_void_p, c_ll, c_void_p, c_void_p]),
+        "sisdc_barrier_selftest": (c_int, [c_int, c_int, c_double, c_void_p]),
         "sisdc_level_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
         "sisdc_ens_create": (c_int, [P(sisdc_ens_instance), c_int, P(sisdc_ens_opts), c_void_p, P(c_void_p)]),
         "sisdc_ens_destroy": (None, [c_void_p]),
