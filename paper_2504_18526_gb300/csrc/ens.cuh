@@ -320,6 +320,8 @@ struct EnsSweeper {
         return V(I.rho) * X + V(I.irho) * Y;
     }
 
+    __device__ static double znew(double z, double beta, double pold) { return beta == 0.0 ? z : z + beta * pold; }
+
     template <class V>
     __device__ static V pnew(V r, V dinv, V beta, V pold) {
         const V z = r * dinv;
@@ -413,6 +415,7 @@ struct EnsSweeper {
         set_coeffs(m);
         if (MIX) return solve_mix(m, x, xsrc, R, Lx0, part, cnt);
         const double rtol2 = a.rtol * a.rtol;
+        double* Z = static_cast<double*>(a.rf);    // z = D^-1 r, stored with r
         // initial residual r = M b - (M + c A) x0
         tiles<2>(part, 0, [&](const EnsInst& I, long long e0, int nle, int li, double* acc) {
             const bool act = le < nle;
@@ -433,9 +436,11 @@ struct EnsSweeper {
                 const double xv = su[le * Q + node];
                 const double Ax = Lx0 ? -ms * __ldcg(Lx0 + id) : opA<double>(I, su, sf, sA);
                 const double rr = mb - (ms * xv + c * Ax);
+                const double zz = rr * dinv;
                 a.r[id] = rr;
+                Z[id] = zz;
                 acc[0] += mb * mb * dinv;
-                acc[1] += rr * (rr * dinv);
+                acc[1] += rr * zz;
             }
         });
         if (!bar()) return false;
@@ -457,17 +462,16 @@ struct EnsSweeper {
                 const bool act = le < nle;
                 const long long e = e0 + le, id = e * Q + node;
                 const double beta = L[li].beta, c = L[li].c;
-                const double* dv = dinv_tab + (size_t)li * Q;
                 double pn = 0.0;
                 if (act) {
-                    pn = pnew<double>(__ldcg(a.r + id), dv[node], beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
+                    pn = znew(__ldcg(Z + id), beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
                     pcur[id] = pn;
                     su[le * Q + node] = pn;
                 }
                 __syncthreads();
                 faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) {
                     const long long idn = en * Q + nd;
-                    return pnew<double>(__ldcg(a.r + idn), dv[nd], beta, beta == 0.0 ? 0.0 : __ldcg(pold + idn));
+                    return znew(__ldcg(Z + idn), beta, beta == 0.0 ? 0.0 : __ldcg(pold + idn));
                 });
                 __syncthreads();
                 if (act) {
@@ -486,8 +490,10 @@ struct EnsSweeper {
                     const double alpha = L[li].alpha, dinv = dinv_tab[(size_t)li * Q + node];
                     x[id] = __ldcg(x + id) + alpha * __ldcg(pcur + id);
                     const double rr = __ldcg(a.r + id) - alpha * __ldcg(AP + id);
+                    const double zz = rr * dinv;
                     a.r[id] = rr;
-                    acc[0] += rr * (rr * dinv);
+                    Z[id] = zz;
+                    acc[0] += rr * zz;
                 }
             });
             if (!bar()) return false;

@@ -93,7 +93,7 @@ struct SweepArgs {
     void *c0, *dC, *tmpc;   // [NV] (FP64, or FP32 when mix)
     double* r;              // CG residual, or M b of the refinement (FP64) [NV]
     void *p, *p2, *Ap;      // CG vectors (FP64, or FP32 when mix) [NV]
-    void* rf;               // inner FP32 residual of the refinement (mix) [NV]
+    void* rf;               // inner FP32 residual of the refinement (mix); FP64 form: z = D^-1 r [NV]
     double* lam;            // [2][MMAX+1] spectral radius slots (old, new)
     double* part;           // 8 * grid partial sums
     double* partmax;        // (MMAX+1) * grid partial maxima

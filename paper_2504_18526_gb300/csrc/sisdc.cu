@@ -43,7 +43,7 @@ struct sisdc_level_s {
     double *c0 = nullptr, *dC = nullptr, *tmpc = nullptr;
     double *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *trx = nullptr, *trp = nullptr;
     double* cg_p2 = nullptr;    // second search-direction buffer of the sweep kernel
-    double* cg_rf = nullptr;    // FP32 inner residual of the mixed-precision refinement
+    double* cg_rf = nullptr;    // FP32 inner residual of the mixed-precision refinement; FP64 form: z = D^-1 r
     double* FV = nullptr;       // Navier-Stokes viscous fluxes [6][N]
     int sw_grid = 0, sw_epb = 0, sw_block = 0;
     double* lam = nullptr;      // [2][MMAX+1]: old, new spectral radius slots

@@ -370,6 +370,9 @@ struct Sweeper {
     __device__ double opA64(int l, int c) const { return opA<double>(l, c, su, sf, sD, sK, sw); }
     __device__ RT opAR(int l, int c) const { return opA<RT>(l, c, ru, rf, rD, rK, rw); }
 
+    // new search direction from the stored z = D^-1 r (shared by owner and neighbours)
+    __device__ static double znew(double z, double beta, double pold) { return beta == 0.0 ? z : z + beta * pold; }
+
     // new search direction at one node (shared by owner and neighbours)
     template <class V>
     __device__ static V pnew(V r, V dinv, V beta, V pold) {
@@ -412,6 +415,9 @@ struct Sweeper {
         set_dinv(c);
         const double dinv = sdinv[node];
         double acc_bb = 0.0, acc = 0.0;
+        // preconditioned residual z = D^-1 r, stored with r so that a search
+        // direction p = z + beta p_old costs one FMA for owner and neighbours
+        double* Z = static_cast<double*>(a.rf);
         const int slot = log_base + log_n;
         const bool logit = a.log_r && slot < a.log_cap;
         ++log_n;
@@ -446,13 +452,15 @@ struct Sweeper {
                     const double xv = su[(le * NC + cc) * Q + node];
                     const double Ax = Lx0 ? -mass * __ldcg(Lx0 + id) : opA64(le, cc);
                     const double rr = mb - (mass * xv + c * Ax);
+                    const double zz = rr * dinv;
                     a.r[id] = rr;
+                    Z[id] = zz;
                     if (logit) {
                         lr[id] = rr / mass;      // nodal residual b - (x0 - c L x0)
                         ldx[id] = xv;
                     }
                     acc_bb += mb * mb * dinv;
-                    acc += rr * (rr * dinv);
+                    acc += rr * zz;
                 }
             }
             __syncthreads();
@@ -481,7 +489,7 @@ struct Sweeper {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
                         const long long id = vidx(cc, e);
-                        pn[cc] = pnew<double>(__ldcg(a.r + id), dinv, beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
+                        pn[cc] = znew(__ldcg(Z + id), beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
                         pcur[id] = pn[cc];
                         su[(le * NC + cc) * Q + node] = pn[cc];
                     }
@@ -489,7 +497,7 @@ struct Sweeper {
                 __syncthreads();
                 faces<double>(nle, e0, su, sf, sD, [&](int cc, long long en, int nd) {
                     const long long id = cc * N + en * Q + nd;
-                    return pnew<double>(__ldcg(a.r + id), sdinv[nd], beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
+                    return znew(__ldcg(Z + id), beta, beta == 0.0 ? 0.0 : __ldcg(pold + id));
                 });
                 __syncthreads();
                 if (act) {
@@ -514,8 +522,10 @@ struct Sweeper {
                         const long long id = vidx(cc, e);
                         x[id] = __ldcg(x + id) + alpha * __ldcg(pcur + id);
                         const double rr = __ldcg(a.r + id) - alpha * __ldcg(AP + id);
+                        const double zz = rr * dinv;
                         a.r[id] = rr;
-                        acc += rr * (rr * dinv);
+                        Z[id] = zz;
+                        acc += rr * zz;
                     }
                 }
             });

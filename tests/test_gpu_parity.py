@@ -282,6 +282,36 @@ def test_step_parity_convdiff1d_full(dev):
     assert sp.l2(u - inputs.convdiff1d_exact(X, 2.0)) < 2e-4
 
 
+def test_step_parity_burgers2d_full_bench_configuration(dev):
+    """The headline workload at its full size (32 x 32 elements, P = 7/3,
+    Radau-Right 5/3, SI(2), Cascade, 3 V-cycles) in the launch configuration
+    the bench times (CUDA graph, autotuned tile shapes): two steps within
+    1e-12 of the oracle (both sides solve to 1e-14, so the comparison is not
+    limited by the solver tolerance); the tuned mixed form (FP32 inner solves
+    on the fine level, the bench's 1e-12 tolerance) within 1e-6 of it."""
+    w = inputs.WORKLOADS["burgers2d"]
+    sp = oracle_space(w, w["levels"][-1])
+    X, Y = sp.coords()
+    u0 = inputs.initial_state("burgers2d", X, Y)
+    lv = w["levels"][-1]
+    dt = inputs.cfl_dt(w["cfl"], (w["hi"][0] - w["lo"][0]) / lv["nel"][0], lv["P"],
+                       inputs.max_wave_speed("burgers", u0))
+    om = oracle_ml(w)
+    uref = [u0]
+    for n in range(2):
+        uref.append(om.step(uref[-1], dt, w["ncycles"], start=w["start"]))
+    for prec, mask, tol, rtol in ((S.SISDC_FP64, 0, TOL, 1e-14), (S.SISDC_MIXED, 1 << (len(w["levels"]) - 1), 1e-6,
+                                                                  1e-12)):
+        ctx = S.Context(w, precision=prec, cg_rtol=rtol, cg_maxit=10000, use_graph=1, mixed_levels=mask)
+        du = T(u0, dev)
+        S.sisdc_autotune(ctx.ctx, du, dt, len(w["levels"]))
+        for n in range(2):
+            S.sisdc_step(ctx.ctx, du, n * dt, dt, w["ncycles"], S.START_IDS[w["start"]], 1)
+            assert rel_l2(N(du), uref[n + 1]) < tol
+        S.sisdc_sync(ctx.ctx)
+        ctx.close()
+
+
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_step_parity_burgers_small(dev, use_graph):
     w = inputs.scaled("burgers2d", nel=(6, 6))
