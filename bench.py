@@ -282,7 +282,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x 
 # DRAM bytes (read + write) of one fine-level correction-sweep launch of the
 # burgers2d workload (FP64 form), from the ncu capture summarised in
 # profiles/k_sweep_burgers2d_fp64.md; None for other workloads or forms.
-SWEEP_TRAFFIC_BYTES = {("burgers2d", "fp64"): 22.403840e6 + 13.386752e6}
+SWEEP_TRAFFIC_BYTES = {("burgers2d", "fp64"): 22.407168e6 + 13.949952e6}
 
 
 # ---------------------------------------------------------------------------
