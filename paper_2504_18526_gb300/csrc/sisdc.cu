@@ -966,9 +966,6 @@ sisdc_status sisdc_autotune(sisdc_ctx c, const double* d_u, double dt, int reps,
     if (c->levels.empty()) return fail(c, SISDC_E_STATE, "no level created");
     std::vector<sisdc_level_s*>& L = c->levels;
     const int nl = (int)L.size();
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     try {
         check(c, cudaEventCreate(&e0), "event");
@@ -990,8 +987,12 @@ sisdc_status sisdc_autotune(sisdc_ctx c, const double* d_u, double dt, int reps,
                 int epb = e, block = 0;
                 const int gmax = sweep_config(lv->geo, c->prob.pde, lv->mix ? 1 : 0, &epb, &block);
                 if (gmax < 1 || gmax > c->max_grid) continue;
-                for (int grid : {gmax, gmax / 2}) {
-                    if (grid < 1 || (grid == gmax / 2 && gmax < 2 * nsm)) continue;
+                // fewer blocks than tiles trade FP64 parallelism for cheaper grid
+                // barriers (small, latency-bound levels)
+                int last = 0;
+                for (int grid : {gmax, gmax / 2, gmax / 4}) {
+                    if (grid < 1 || grid == last || (grid != gmax && grid < 8)) continue;
+                    last = grid;
                     lv->sw_epb = epb;
                     lv->sw_grid = grid;
                     lv->sw_block = block;
