@@ -11,19 +11,26 @@
 // radius entering nu_tilde) go through the bounded grid barrier.  Data other
 // blocks write during the launch is read through L2 (__ldcg).
 //
+// Operators: the SIPG application is one branch-free sum of products with
+// pre-scaled coefficients (sipg.cuh); the Rusanov face fluxes of c(u) are
+// evaluated once per face node in face tasks, x faces and y faces in
+// separate whole warps, and added at the end nodes after a block barrier.
+//
 // Implicit solves: Jacobi-PCG on (M + c A) x = M b with two barriers per
-// iteration.  A block forms the face lines of a neighbour's new search
-// direction p_new = D^-1 r + beta p_old itself, from the neighbour's r and
-// p_old (p is double-buffered), with the same inline arithmetic the owner
-// uses, so both sides of every face see bitwise-identical values and p never
-// has to be published before it is used.
+// iteration.  The update phase stores z = D^-1 r beside r; a block forms the
+// face lines of a neighbour's new search direction p_new = z + beta p_old
+// itself, from the neighbour's z and p_old (p is double-buffered), with the
+// same inline arithmetic the owner uses, so both sides of every face see
+// bitwise-identical values and p never has to be published before use.
 //
 // MIX = true (mixed precision): the implicit solves run as an iterative
 // refinement whose residual, right-hand side, inner products and solution
 // update are FP64 while the inner CG (its matvecs and vectors) is FP32.  The
-// explicit operator evaluations (c(u), L u) and all cached quantities stay
-// FP64: evaluated in FP32 they perturb every sweep by eps_32 * dt_m * |c|,
-// which the few sweeps of a step do not iterate away.
+// explicit operator evaluations (c(u), L u) keep at least ~48-bit accuracy
+// (FP64, or double-single arithmetic on the FP32 pipe for the scalar
+// convection-diffusion and Burgers PDEs) and all cached quantities stay
+// FP64: evaluated in FP32 they would perturb every sweep by eps_32 * dt_m *
+// |c|, which the few sweeps of a step do not iterate away.
 //
 // The first residual of a solve whose initial guess is the previous iterate
 // x0 = u^{k-1}_m reuses the cached L x0:  (M + c A) x0 = M x0 - c M L x0.
