@@ -279,6 +279,16 @@ def sweep_flops(P, ncomp, M, nsweeps, iters, nv):
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 
+
+# Algorithmic memory traffic of one correction-sweep launch if no array
+# stayed on chip (the HBM view of the roofline): per collocation node and
+# DOF, 11 state-sized FP64 arrays (old and previous-node iterate, f, c and
+# L u caches, S.F, FAS g; new iterate, f, c, L u) plus 4 per implicit solve
+# of the two SI(2) stages (right-hand side terms, r, z); per CG iteration
+# 11 (r, z, p_old, p, Ap, x read or written).
+def sweep_bytes(M, nsweeps, iters, nv):
+    return 8.0 * nv * (nsweeps * M * (11 + 2 * 4) + iters * 11)
+
 # DRAM bytes (read + write) of one fine-level correction-sweep launch of the
 # burgers2d workload (FP64 form), from the ncu capture summarised in
 # profiles/k_sweep_burgers2d_fp64.md; None for other workloads or forms.
@@ -438,6 +448,9 @@ def main_arm(args):
     flops = sweep_flops(lv["P"], nc, M, nsw / max(1, kt["launches"]), kt["iters"] / max(1, kt["launches"]), nv)
     avg_ms = kt["ms"] / max(1, kt["launches"])
     achieved = flops / (avg_ms * 1e-3) / 1e12
+    hbm_peak, hbm_kind = measured_peaks()
+    nbytes = sweep_bytes(M, nsw / max(1, kt["launches"]), kt["iters"] / max(1, kt["launches"]), nv)
+    hbm_gbs = nbytes / (avg_ms * 1e-3) / 1e9
 
     # ---- the other precision form and time-to-solution at equal L2 error ----
     forms = {}
@@ -514,6 +527,10 @@ def main_arm(args):
                      "cg_iters_per_launch": kt["iters"] / max(1, kt["launches"]),
                      "algorithmic_flop_per_launch": flops,
                      "kernel_share_of_step": kt["ms"] / max(1e-9, eager_s * 1e3)},
+        "hbm_view": {"algorithmic_bytes_per_launch": nbytes, "achieved": hbm_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": hbm_gbs / hbm_peak, "peak_kind": hbm_kind + " copy bandwidth",
+                     "note": "bytes a launch would move if no array stayed on chip; the level is L2-resident "
+                             "(roofline.traffic) and the kernel is FP64-ALU bound, so this is not its limit"},
         "forms": forms, "time_to_solution": tts,
         "cpu_baseline": cpu,
         "clocks": clocks,
