@@ -60,27 +60,51 @@ __global__ void k_mlp_scale(const double* __restrict__ ss, int nex, int ney, int
 }
 
 // (FP32 arithmetic: the value rounded to FP32 on the integer pipe, then
-// scaled; GB300's FP64 unit would otherwise set this kernel's time)
-__global__ void k_mlp_fill(const double* __restrict__ f, const float* __restrict__ sinv, int nex, int ney, int q,
-                           long long rows, int n_in, float feat, float* __restrict__ X) {
+// scaled; GB300's FP64 unit would otherwise set this kernel's time).  A thread
+// keeps the same input slots t = threadIdx.x + j blockDim.x for every row, so
+// their (neighbour, node) split is computed once; the nine neighbour offsets
+// of a row are computed once per row in shared memory.
+constexpr int FILL_THREADS = 128, FILL_SLOTS = 8;   // n_in <= 1024
+
+template <class TX>
+__device__ __forceinline__ TX to_x(float v);
+template <>
+__device__ __forceinline__ float to_x<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_x<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// X[row][t] for t < n_in, rows ldx apart (FP32, or BF16 for the tensor cores)
+template <class TX>
+__global__ void __launch_bounds__(FILL_THREADS) k_mlp_fill(const double* __restrict__ f, const float* __restrict__ sinv,
+                                                         int nex, int ney, int q, long long rows, int n_in, int ldx,
+                                                         float feat, TX* __restrict__ X) {
+    __shared__ long long nbase[9];
     const int nel = nex * ney;
     const long long N = (long long)nel * q;
+    int tk[FILL_SLOTS], tn[FILL_SLOTS];
+#pragma unroll
+    for (int j = 0; j < FILL_SLOTS; ++j) {
+        const int t = threadIdx.x + j * FILL_THREADS;
+        tk[j] = t / q;
+        tn[j] = t - tk[j] * q;
+    }
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int c = (int)(row / nel), e = (int)(row - (long long)c * nel);
-        const int ex = e % nex, ey = e / nex;
-        const float si = sinv[row];
-        const double* fc = f + c * N;
-        float* xr = X + row * n_in;
-        for (int t = threadIdx.x; t < n_in; t += blockDim.x) {
-            if (t == 9 * q) {
-                xr[t] = feat;
-                continue;
-            }
-            const int k = t / q, node = t - k * q;
-            const int dy = k / 3 - 1, dx = k % 3 - 1;
-            const int en = ((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex;
-            xr[t] = d2f_int(fc[(long long)en * q + node]) * si;
+        if (threadIdx.x < 9) {
+            const int c = (int)(row / nel), e = (int)(row - (long long)c * nel);
+            const int ex = e % nex, ey = e / nex;
+            const int dy = (int)threadIdx.x / 3 - 1, dx = (int)threadIdx.x % 3 - 1;
+            nbase[threadIdx.x] = c * N + (long long)(((ey + dy + ney) % ney) * nex + (ex + dx + nex) % nex) * q;
         }
+        __syncthreads();
+        const float si = sinv[row];
+        TX* xr = X + row * ldx;
+#pragma unroll
+        for (int j = 0; j < FILL_SLOTS; ++j) {
+            const int t = threadIdx.x + j * FILL_THREADS;
+            if (t < 9 * q) xr[t] = to_x<TX>(d2f_int(f[nbase[tk[j]] + tn[j]]) * si);
+            else if (t == 9 * q) xr[t] = to_x<TX>(feat);
+        }
+        __syncthreads();
     }
 }
 
@@ -204,15 +228,44 @@ __global__ void __launch_bounds__(128, 4) k_gemm_tc(const TA* __restrict__ A, co
         const int t = threadIdx.x + i * 128;
         if constexpr (tb) { nn = t / TC_BK; kk = t - nn * TC_BK; } else { kk = t / TC_BN; nn = t - kk * TC_BN; }
     };
-    float ra[PER], rb[PER];
+    // a row-major BF16 A (rows 16-byte aligned: lda % 8 == 0, checked by the
+    // host) is staged 8 values per 16-byte load
+    constexpr bool VA = std::is_same<TA, __nv_bfloat16>::value && !ta;
+    constexpr int PA = VA ? TC_BM * TC_BK / 8 / 128 : PER;             // staged A items per thread
+    float ra[VA ? 1 : PER], rb[PER];
+    uint4 va[VA ? PA : 1];
+    auto slotV = [&](int i, int& mm, int& kq) {
+        const int c = threadIdx.x + i * 128;
+        mm = c / (TC_BK / 8);
+        kq = (c - mm * (TC_BK / 8)) * 8;
+    };
     // global -> registers for the slice at k0 (all loads issued before use)
     auto fetch = [&](int k0) {
+        if constexpr (VA) {
+#pragma unroll
+            for (int i = 0; i < PA; ++i) {
+                int mm, kq;
+                slotV(i, mm, kq);
+                const int m = m0 + mm, k = k0 + kq;
+                if (m < M && k + 8 <= kend) {
+                    va[i] = *reinterpret_cast<const uint4*>(A + (long long)m * lda + k);
+                } else {
+                    __align__(16) __nv_bfloat16 tmp[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        tmp[e] = (m < M && k + e < kend) ? A[(long long)m * lda + k + e] : __float2bfloat16_rn(0.f);
+                    va[i] = *reinterpret_cast<const uint4*>(tmp);
+                }
+            }
+        }
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            int mm, kk;
-            slotA(i, mm, kk);
-            const int m = m0 + mm, k = k0 + kk;
-            ra[i] = (m < M && k < kend) ? ld_as_float<TA>(A, ta ? (long long)k * lda + m : (long long)m * lda + k) : 0.f;
+            if constexpr (!VA) {
+                int mm, kk;
+                slotA(i, mm, kk);
+                const int m = m0 + mm, k = k0 + kk;
+                ra[i] = (m < M && k < kend) ? ld_as_float<TA>(A, ta ? (long long)k * lda + m : (long long)m * lda + k) : 0.f;
+            }
             int nn, kb;
             slotB(i, nn, kb);
             const int n = n0 + nn, kq = k0 + kb;
@@ -222,11 +275,21 @@ __global__ void __launch_bounds__(128, 4) k_gemm_tc(const TA* __restrict__ A, co
     float acc[2][4][4] = {};
     if (kbeg < kend) fetch(kbeg);
     for (int k0 = kbeg; k0 < kend; k0 += TC_BK) {
+        if constexpr (VA) {
+#pragma unroll
+            for (int i = 0; i < PA; ++i) {
+                int mm, kq;
+                slotV(i, mm, kq);
+                *reinterpret_cast<uint4*>(&As[mm][kq]) = va[i];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            int mm, kk;
-            slotA(i, mm, kk);
-            As[mm][kk] = __float2bfloat16_rn(ra[i]);
+            if constexpr (!VA) {
+                int mm, kk;
+                slotA(i, mm, kk);
+                As[mm][kk] = __float2bfloat16_rn(ra[i]);
+            }
             int nn, kb;
             slotB(i, nn, kb);
             Bs[nn][kb] = __float2bfloat16_rn(rb[i]);
@@ -389,6 +452,8 @@ struct sisdc_mlp_s {
           *s = nullptr;
     double* part = nullptr;
     float* ws = nullptr;            // split-K partials of the tensor-core GEMMs
+    __nv_bfloat16* Xb = nullptr;    // BF16 mode: the patch inputs, rows ldx apart (zero padding)
+    int ldx = 0;
     double* ss = nullptr;                    // per-row sums of squares
     float* sinv = nullptr;                   // 1 / patch scale
     double* lacc = nullptr;                  // loss accumulator of a training epoch
@@ -417,12 +482,12 @@ constexpr long long MLP_SPLITK_WS = 1ll << 22;
 // C = op(A) op(B) (+ bias, tanh): tensor cores in the BF16 mode (split-K when
 // the output has too few tiles for the GPU and K is long, as for the weight
 // gradients whose reduction runs over all rows), FP32 SIMT otherwise
-template <class TB>
-void gemm(sisdc_mlp_s* p, const float* A, const TB* B, float* C, const float* bias, int M, int N, int K, int lda,
+template <class TB, class TA = float>
+void gemm(sisdc_mlp_s* p, const TA* A, const TB* B, float* C, const float* bias, int M, int N, int K, int lda,
           int ldb, int ldc, int ta, int tb, int epi) {
     dim3 grid((N + 63) / 64, (M + 63) / 64);
     if (!p->bf16) {
-        k_gemm<float, TB><<<grid, 256, 0, p->stream>>>(A, B, C, bias, M, N, K, lda, ldb, ldc, ta, tb, epi);
+        k_gemm<TA, TB><<<grid, 256, 0, p->stream>>>(A, B, C, bias, M, N, K, lda, ldb, ldc, ta, tb, epi);
         mck(p, cudaGetLastError(), "gemm");
         return;
     }
@@ -438,14 +503,17 @@ void gemm(sisdc_mlp_s* p, const float* A, const TB* B, float* C, const float* bi
     kz = (K + kchunk - 1) / kchunk;
     grid.z = (unsigned)kz;
     float* out = kz > 1 ? p->ws : C;
+    if (std::is_same<TA, __nv_bfloat16>::value && !ta &&
+        (lda % 8 != 0 || reinterpret_cast<unsigned long long>(A) % 16 != 0))
+        mck(p, cudaErrorInvalidValue, "gemm_tc: BF16 A rows must be 16-byte aligned");
     if (!ta && !tb)
-        k_gemm_tc<float, TB, false, false><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+        k_gemm_tc<TA, TB, false, false><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
     else if (ta && !tb)
-        k_gemm_tc<float, TB, true, false><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+        k_gemm_tc<TA, TB, true, false><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
     else if (!ta && tb)
-        k_gemm_tc<float, TB, false, true><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+        k_gemm_tc<TA, TB, false, true><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
     else
-        k_gemm_tc<float, TB, true, true><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
+        k_gemm_tc<TA, TB, true, true><<<grid, 128, 0, p->stream>>>(A, B, out, bias, M, N, K, lda, ldb, ldc, epi, kchunk);
     mck(p, cudaGetLastError(), "gemm_tc");
     if (kz > 1) {
         k_splitk_sum<<<ew((long long)M * N), 256, 0, p->stream>>>(p->ws, kz, M, N, C, ldc);
@@ -467,7 +535,7 @@ void colsum(sisdc_mlp_s* p, const float* D, int rows, int cols, float* out) {
 void forward(sisdc_mlp_s* p) {
     const int R = (int)p->rows;
     if (p->bf16) {
-        gemm<__nv_bfloat16>(p, p->X, p->theta_b + p->oW1, p->H1, p->theta + p->ob1, R, p->H, p->n_in, p->n_in, p->H,
+        gemm<__nv_bfloat16>(p, p->Xb, p->theta_b + p->oW1, p->H1, p->theta + p->ob1, R, p->H, p->n_in, p->ldx, p->H,
                             p->H, 0, 0, EPI_BIAS_TANH);
         gemm<__nv_bfloat16>(p, p->H1, p->theta_b + p->oW2, p->H2, p->theta + p->ob2, R, p->H, p->H, p->H, p->H, p->H,
                             0, 0, EPI_BIAS_TANH);
@@ -488,7 +556,12 @@ void gather(sisdc_mlp_s* p, const double* field, double c) {
     k_mlp_elem_ss<<<ew(p->rows), 256, 0, p->stream>>>(field, p->rows, p->q, p->ss);
     k_mlp_scale<<<ew(p->rows), 256, 0, p->stream>>>(p->ss, p->nex, p->ney, p->q, p->rows, p->s, p->sinv);
     const unsigned fb = (unsigned)std::min<long long>(p->rows, 152LL * 16);
-    k_mlp_fill<<<fb, 128, 0, p->stream>>>(field, p->sinv, p->nex, p->ney, p->q, p->rows, p->n_in, feat, p->X);
+    if (p->bf16)
+        k_mlp_fill<__nv_bfloat16><<<fb, FILL_THREADS, 0, p->stream>>>(field, p->sinv, p->nex, p->ney, p->q, p->rows,
+                                                                      p->n_in, p->ldx, feat, p->Xb);
+    else
+        k_mlp_fill<float><<<fb, FILL_THREADS, 0, p->stream>>>(field, p->sinv, p->nex, p->ney, p->q, p->rows, p->n_in,
+                                                              p->n_in, feat, p->X);
     mck(p, cudaGetLastError(), "patches");
 }
 
@@ -525,7 +598,10 @@ void loss_grad_dev(sisdc_mlp_s* p, const double* r, const double* dx, double c) 
         gemm<float>(p, p->dH, p->theta + p->oW2, p->H2, nullptr, R, p->H, p->H, p->H, p->H, p->H, 0, 1, EPI_NONE);
     k_tanh_back<<<ew((long long)R * p->H), 256, 0, p->stream>>>(p->H1, p->H2, (long long)R * p->H);
     // layer 1
-    gemm<float>(p, p->X, p->H2, g + p->oW1, nullptr, p->n_in, p->H, R, p->n_in, p->H, p->H, 1, 0, EPI_NONE);
+    if (p->bf16)
+        gemm<float>(p, p->Xb, p->H2, g + p->oW1, nullptr, p->n_in, p->H, R, p->ldx, p->H, p->H, 1, 0, EPI_NONE);
+    else
+        gemm<float>(p, p->X, p->H2, g + p->oW1, nullptr, p->n_in, p->H, R, p->n_in, p->H, p->H, 1, 0, EPI_NONE);
     colsum(p, p->H2, R, p->H, g + p->ob1);
     mck(p, cudaGetLastError(), "backward");
 }
@@ -568,6 +644,10 @@ sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long see
     p->H = hidden;
     p->bf16 = bf16 ? 1 : 0;
     p->n_in = 9 * p->q + 1;
+    if (p->n_in > FILL_THREADS * FILL_SLOTS) {   // patch gather limit (2D levels have P <= 8)
+        delete p;
+        return SISDC_E_ARG;
+    }
     p->rows = (long long)p->nc * p->nex * p->ney;
     p->oW1 = 0;
     p->ob1 = p->oW1 + (long long)p->n_in * p->H;
@@ -605,7 +685,13 @@ sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long see
     al((void**)&p->m, p->nparam * sizeof(float));
     al((void**)&p->v, p->nparam * sizeof(float));
     al((void**)&p->theta_b, p->nparam * sizeof(__nv_bfloat16));
-    al((void**)&p->X, R * p->n_in * sizeof(float));
+    p->ldx = (p->n_in + 7) / 8 * 8;
+    if (p->bf16) {
+        al((void**)&p->Xb, R * p->ldx * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMemset(p->Xb, 0, R * p->ldx * sizeof(__nv_bfloat16));
+    } else {
+        al((void**)&p->X, R * p->n_in * sizeof(float));
+    }
     al((void**)&p->H1, R * p->H * sizeof(float));
     al((void**)&p->H2, R * p->H * sizeof(float));
     al((void**)&p->dH, R * p->H * sizeof(float));
@@ -639,7 +725,7 @@ void sisdc_mlp_destroy(sisdc_mlp p) {
     cudaFree(p->theta); cudaFree(p->grad); cudaFree(p->m); cudaFree(p->v); cudaFree(p->theta_b);
     cudaFree(p->X); cudaFree(p->H1); cudaFree(p->H2); cudaFree(p->dH); cudaFree(p->Y); cudaFree(p->T);
     cudaFree(p->dY); cudaFree(p->s); cudaFree(p->part); cudaFree(p->ws);
-    cudaFree(p->ss); cudaFree(p->sinv); cudaFree(p->lacc);
+    cudaFree(p->ss); cudaFree(p->sinv); cudaFree(p->lacc); cudaFree(p->Xb);
     delete p;
 }
 
