@@ -24,7 +24,8 @@
  * device, owned by the caller, and must stay valid until the work queued
  * on the context stream has finished.  Pointers named h_* are HOST
  * pointers, read or written synchronously.  Level work arrays are owned by
- * the library (cudaMalloc at sisdc_create_level, freed by sisdc_destroy).
+ * the library (allocated at sisdc_create_level, by cudaMalloc or by the
+ * caller's allocator of sisdc_set_allocator, and released by sisdc_destroy).
  *
  * Streams and errors.  All device work is queued on the stream given to
  * sisdc_create and runs asynchronously; calls return after queuing.  Every
@@ -36,6 +37,8 @@
  */
 #ifndef SISDC_H
 #define SISDC_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -134,6 +137,11 @@ typedef struct {
                            others run in FP64; 0 = every level.  Levels whose
                            sweeps are barrier-latency bound (small coarse
                            levels) are often faster in FP64                    */
+    double nu_tilde;    /* 0: nu_tilde = nu_d + dt_m/2 lam_max^2 per node and
+                           sweep (Sec. 3.3, the diffusion-type coefficient of
+                           the SI integrators); > 0: this constant instead
+                           (the converged collocation result does not depend
+                           on it; it changes the iteration only)            */
 } sisdc_problem;
 
 typedef struct {
@@ -154,11 +162,26 @@ typedef struct {
 sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ctx* out);
 void sisdc_destroy(sisdc_ctx ctx);
 
+/* Device allocator for the level work arrays (optional; the default is
+ * cudaMalloc/cudaFree).  alloc(bytes, cuda_stream, user) returns device
+ * memory of the context's device, at least 256-byte aligned and usable on
+ * the context's stream, or NULL on failure (sisdc_create_level then returns
+ * SISDC_E_OOM); release(ptr, bytes, cuda_stream, user) takes back exactly
+ * what alloc returned, with the same size, at sisdc_destroy (after the
+ * stream has finished).  This lets a caller's caching allocator (for
+ * instance PyTorch's) own the memory.  Must be set before the first
+ * sisdc_create_level (SISDC_E_STATE otherwise); both NULL restores the
+ * default; exactly one NULL is SISDC_E_ARG.  The callbacks must outlive the
+ * context. */
+typedef void* (*sisdc_alloc_fn)(size_t bytes, void* cuda_stream, void* user);
+typedef void (*sisdc_release_fn)(void* ptr, size_t bytes, void* cuda_stream, void* user);
+sisdc_status sisdc_set_allocator(sisdc_ctx ctx, sisdc_alloc_fn alloc, sisdc_release_fn release, void* user);
+
 /* Add a level (Sec. 6.1).  Levels must be added from coarse (l = 1) to fine
  * (l = L); adjacent levels must share the element grid (p-coarsening in
  * space, Sec. 6.2) and node kind (p-coarsening in time).  Work arrays are
- * allocated here (SISDC_E_OOM on failure).  The handle lives until
- * sisdc_destroy. */
+ * allocated here (through the allocator of sisdc_set_allocator if one is
+ * set; SISDC_E_OOM on failure).  The handle lives until sisdc_destroy. */
 sisdc_status sisdc_create_level(sisdc_ctx ctx, const sisdc_level_desc* desc, sisdc_level* out);
 
 /* Sizes of a level: components, nodes per component N, collocation nodes M. */

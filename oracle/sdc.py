@@ -42,6 +42,12 @@ class Level:
 
 
 def nutilde(space, u_b, dtm):
+    # a space may carry a fixed nu_tilde (the library's sisdc_problem.nu_tilde
+    # option); the collocation limit does not depend on it (Sec. 3.3: the
+    # Delta H terms vanish at convergence)
+    fix = getattr(space, "nu_tilde_fix", 0.0)
+    if fix > 0.0:
+        return fix
     return space.nu_d + 0.5 * dtm * space.lam_max(u_b) ** 2
 
 

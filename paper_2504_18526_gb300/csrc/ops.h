@@ -75,6 +75,7 @@ struct SweepArgs {
     double gamma, ax, ay;   // flux parameters
     double nu;              // physical diffusion in f
     double nu_d;            // nu_d of nu_tilde = nu_d + dt_m/2 lam_max^2
+    double nu_tilde_fix;    // > 0: constant nu_tilde instead of the formula
     double mu, kappa;       // Navier-Stokes viscosity and heat conductivity
     double* FV;             // Navier-Stokes viscous flux scratch [6][N]: F_v^x, F_v^y of
                             // the momentum and energy components

@@ -37,6 +37,7 @@ struct sisdc_level_s {
     long long N = 0, NV = 0;
     double* d_tab = nullptr;
     double* d_mem = nullptr;
+    size_t tab_bytes = 0, mem_bytes = 0;
     // state and caches
     double *U = nullptr, *u0 = nullptr;
     double *F = nullptr, *CC = nullptr, *LU = nullptr, *Qb = nullptr, *G = nullptr, *V = nullptr, *R = nullptr;
@@ -81,6 +82,10 @@ struct sisdc_ctx_s {
     int log_cap = 0;
     int* d_log_count = nullptr;
     int max_grid = 0;
+    // caller's allocator for the level work arrays (sisdc_set_allocator)
+    sisdc_alloc_fn ualloc = nullptr;
+    sisdc_release_fn urelease = nullptr;
+    void* uuser = nullptr;
     std::string err;
     long long launches = 0;
     long long sweeps[8] = {0};
@@ -270,6 +275,7 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.ay = c->prob.adv[1];
     a.nu = nu_phys(c->prob);
     a.nu_d = nu_d(c->prob);
+    a.nu_tilde_fix = c->prob.nu_tilde;
     a.mu = c->prob.pde == SISDC_PDE_NS ? c->prob.mu : 0.0;
     a.kappa = kappa_ns(c->prob);
     a.FV = lv->FV;
@@ -472,6 +478,32 @@ void enqueue_step(sisdc_ctx_s* c, double* d_u, double dt, int ncycles, int start
 // ============================================================================
 // C ABI
 // ============================================================================
+// Level work memory: the caller's allocator when one is set, else cudaMalloc.
+static cudaError_t level_alloc(sisdc_ctx_s* c, double** p, size_t bytes) {
+    *p = nullptr;
+    if (!c->ualloc) return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    void* q = c->ualloc(bytes, c->stream, c->uuser);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<unsigned long long>(q) % 256 != 0) {
+        c->urelease(q, bytes, c->stream, c->uuser);
+        return cudaErrorMisalignedAddress;
+    }
+    *p = static_cast<double*>(q);
+    return cudaSuccess;
+}
+
+static void level_free(sisdc_ctx_s* c, double* p, size_t bytes) {
+    if (!p) return;
+    if (c->urelease) c->urelease(p, bytes, c->stream, c->uuser);
+    else cudaFree(p);
+}
+
+static void level_free_all(sisdc_ctx_s* c, sisdc_level_s* lv) {
+    level_free(c, lv->d_tab, lv->tab_bytes);
+    level_free(c, lv->d_mem, lv->mem_bytes);
+    lv->d_tab = lv->d_mem = nullptr;
+}
+
 extern "C" {
 
 sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ctx* out) {
@@ -490,6 +522,7 @@ sisdc_status sisdc_create(const sisdc_problem* prob, void* cuda_stream, sisdc_ct
     if (prob->fmg_cycles < 0) return SISDC_E_ARG;
     if (prob->form != 0 && prob->form != 1) return SISDC_E_ARG;
     if (prob->nu < 0.0) return SISDC_E_ARG;
+    if (!(prob->nu_tilde >= 0.0) || !std::isfinite(prob->nu_tilde)) return SISDC_E_ARG;
     sisdc_ctx_s* c = new sisdc_ctx_s();
     c->prob = *prob;
     c->stream = (cudaStream_t)cuda_stream;
@@ -530,8 +563,7 @@ void sisdc_destroy(sisdc_ctx c) {
     cudaFree(c->d_iters);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     for (sisdc_level_s* lv : c->levels) {
-        cudaFree(lv->d_tab);
-        cudaFree(lv->d_mem);
+        level_free_all(c, lv);
         delete lv;
     }
     cudaFree(c->d_bar);
@@ -541,6 +573,16 @@ void sisdc_destroy(sisdc_ctx c) {
     cudaFree(c->d_norms);
     cudaFree(c->d_log_count);
     delete c;
+}
+
+sisdc_status sisdc_set_allocator(sisdc_ctx c, sisdc_alloc_fn alloc, sisdc_release_fn release, void* user) {
+    if (!c) return SISDC_E_ARG;
+    if ((alloc == nullptr) != (release == nullptr)) return fail(c, SISDC_E_ARG, "allocator: alloc and release go together");
+    if (!c->levels.empty()) return fail(c, SISDC_E_STATE, "allocator must be set before the first level");
+    c->ualloc = alloc;
+    c->urelease = release;
+    c->uuser = alloc ? user : nullptr;
+    return SISDC_OK;
 }
 
 sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_level* out) {
@@ -644,24 +686,34 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         off_one = push(std::vector<double>{1.0});
     }
     const size_t ntab = htab.size() + ttab.size();
-    cudaError_t e = cudaMalloc(&lv->d_tab, ntab * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemcpy(lv->d_tab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    lv->tab_bytes = ntab * sizeof(double);
+    cudaError_t e = level_alloc(c, &lv->d_tab, lv->tab_bytes);
+    // stream-ordered copies: memory of a caller's caching allocator may still
+    // be in use by earlier work on the context stream
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lv->d_tab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !ttab.empty())
-        e = cudaMemcpy(lv->d_tab + htab.size(), ttab.data(), ttab.size() * sizeof(double), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(lv->d_tab + htab.size(), ttab.data(), ttab.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream);
     // work arrays
     const long long NV = lv->NV, MV = (long long)lv->M * NV;
     const long long ntr = (long long)c->prob.ncomp * lv->nel * 2 * d->dim * 2 * nq;
     const long long nfv = c->prob.pde == SISDC_PDE_NS ? 6 * lv->N : 0;
     const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1) + nfv;
-    if (e == cudaSuccess) e = cudaMalloc(&lv->d_mem, total * sizeof(double));
+    lv->mem_bytes = total * sizeof(double);
+    if (e == cudaSuccess) e = level_alloc(c, &lv->d_mem, lv->mem_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lv->d_mem, 0, lv->mem_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        cudaFree(lv->d_tab);
-        cudaFree(lv->d_mem);
+        cudaStreamSynchronize(c->stream);
+        level_free_all(c, lv);
         delete lv;
-        return fail(c, e == cudaErrorMemoryAllocation ? SISDC_E_OOM : SISDC_E_CUDA,
-                    std::string("level allocation: ") + cudaGetErrorString(e));
+        return fail(c, e == cudaErrorMemoryAllocation ? SISDC_E_OOM
+                       : e == cudaErrorMisalignedAddress ? SISDC_E_ARG : SISDC_E_CUDA,
+                    std::string("level allocation: ") +
+                        (e == cudaErrorMisalignedAddress ? "allocator returned memory not 256-byte aligned"
+                                                          : cudaGetErrorString(e)));
     }
-    cudaMemset(lv->d_mem, 0, total * sizeof(double));
     double* p = lv->d_mem;
     auto take = [&](long long n) { double* q = p; p += n; return q; };
     lv->U = take(MV); lv->F = take(MV); lv->CC = take(MV); lv->LU = take(MV);
@@ -689,8 +741,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     lv->pcg_grid = pcg_grid(g, &lv->pcg_block);
     lv->sw_grid = sweep_config(g, c->prob.pde, lv->mix, &lv->sw_epb, &lv->sw_block);
     if (lv->pcg_grid < 1 || lv->pcg_grid > c->max_grid || lv->sw_grid < 1 || lv->sw_grid > c->max_grid) {
-        cudaFree(lv->d_tab);
-        cudaFree(lv->d_mem);
+        level_free_all(c, lv);
         delete lv;
         return fail(c, SISDC_E_CUDA, "cooperative PCG launch configuration unavailable");
     }

@@ -14,6 +14,10 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sisdc.h")
 
 c_int, c_double, c_ll, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
 
+# sisdc_alloc_fn / sisdc_release_fn of include/sisdc.h
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p, c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, c_void_p, ctypes.c_size_t, c_void_p, c_void_p)
+
 SISDC_OK, SISDC_E_ARG, SISDC_E_CUDA, SISDC_E_NOCONV = 0, -1, -2, -3
 SISDC_E_TIMEOUT, SISDC_E_NONFINITE, SISDC_E_OOM, SISDC_E_STATE = -4, -5, -6, -7
 STATUS_NAMES = {0: "SISDC_OK", -1: "SISDC_E_ARG", -2: "SISDC_E_CUDA", -3: "SISDC_E_NOCONV",
@@ -35,7 +39,8 @@ class sisdc_problem(ctypes.Structure):
                 ("adv", c_double * 2), ("precision", c_int), ("si_stages", c_int),
                 ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("use_graph", c_int),
                 ("mu", c_double), ("Pr", c_double), ("rho_ref", c_double), ("projection", c_int),
-                ("fmg_cycles", c_int), ("form", c_int), ("mixed_levels", c_int)]
+                ("fmg_cycles", c_int), ("form", c_int), ("mixed_levels", c_int),
+                ("nu_tilde", c_double)]
 
 
 class sisdc_stats(ctypes.Structure):
@@ -88,6 +93,7 @@ def load():
         "sisdc_create": (c_int, [P(sisdc_problem), c_void_p, P(c_void_p)]),
         "sisdc_destroy": (None, [c_void_p]),
         "sisdc_create_level": (c_int, [c_void_p, P(sisdc_level_desc), P(c_void_p)]),
+        "sisdc_set_allocator": (c_int, [c_void_p, ALLOC_FN, RELEASE_FN, c_void_p]),
         "sisdc_level_info": (c_int, [c_void_p, P(c_int), P(c_ll), P(c_int)]),
         "sisdc_level_coords": (c_int, [c_void_p, c_void_p, c_void_p]),
         "sisdc_level_tables": (c_int, [c_void_p] + [c_void_p] * 5),
@@ -186,6 +192,42 @@ def sisdc_create(prob, stream=0):
 
 def sisdc_destroy(ctx):
     load().sisdc_destroy(ctx)
+
+
+class TorchAllocator:
+    """sisdc_set_allocator callbacks backed by PyTorch's caching allocator, so
+    that the level work arrays are part of torch's memory pool.  Keep the
+    object alive as long as the context (Context does)."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.live = {}
+
+        def _alloc(nbytes, stream, user):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            except Exception:
+                return None
+            self.live[ptr] = int(nbytes)
+            return ptr
+
+        def _release(ptr, nbytes, stream, user):
+            if ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.release = RELEASE_FN(_release)
+
+
+def sisdc_set_allocator(ctx, allocator=None):
+    """Install an allocator object with .alloc/.release ctypes callbacks
+    (e.g. TorchAllocator()), or restore cudaMalloc with None."""
+    if allocator is None:
+        _check(load().sisdc_set_allocator(ctx, ALLOC_FN(), RELEASE_FN(), None), ctx)
+    else:
+        _check(load().sisdc_set_allocator(ctx, allocator.alloc, allocator.release, None), ctx)
 
 
 def sisdc_create_level(ctx, desc):
@@ -546,7 +588,7 @@ START_IDS = {"spread": SISDC_START_SPREAD, "predictor": SISDC_START_PREDICTOR,
 
 def make_problem(w, precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12, cg_maxit=1000, Nc=2,
                  use_graph=0, projection="interp", fmg_cycles=1, form="incremental",
-                 mixed_levels=0):
+                 mixed_levels=0, nu_tilde=0.0):
     p = sisdc_problem()
     p.pde = PDE_IDS[w["pde"]]
     p.ncomp = w["ncomp"]
@@ -564,6 +606,7 @@ def make_problem(w, precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12, cg_maxit=1
     p.fmg_cycles = fmg_cycles
     p.form = {"incremental": 0, "zero_to_node": 1}[form]
     p.mixed_levels = mixed_levels
+    p.nu_tilde = nu_tilde
     if w["pde"] == "ns":
         p.mu = 1.0 / w["Re"]
         p.Pr = w["Pr"]
@@ -587,9 +630,12 @@ def make_level_desc(w, lvl):
 class Context:
     """Owns one sisdc context and its levels (coarse to fine)."""
 
-    def __init__(self, w, stream=0, **kw):
+    def __init__(self, w, stream=0, allocator=None, **kw):
         self.w = w
         self.ctx = sisdc_create(make_problem(w, **kw), stream)
+        self.allocator = allocator           # kept alive with the context
+        if allocator is not None:
+            sisdc_set_allocator(self.ctx, allocator)
         self.levels = [sisdc_create_level(self.ctx, make_level_desc(w, lv)) for lv in w["levels"]]
 
     def info(self, l=-1):

@@ -72,3 +72,11 @@ def test_invalid_ensemble_rejected_without_gpu(lib):
         with pytest.raises(sisdc.SisdcError) as ei:
             sisdc.sisdc_ens_create([sisdc.make_ens_instance(good)], opts)
         assert ei.value.status == sisdc.SISDC_E_ARG
+
+
+def test_set_allocator_rejects_without_gpu(lib):
+    """sisdc_set_allocator checks its arguments before touching the device:
+    a NULL context, or alloc without release, is SISDC_E_ARG."""
+    assert lib.sisdc_set_allocator(None, sisdc.ALLOC_FN(), sisdc.RELEASE_FN(), None) == sisdc.SISDC_E_ARG
+    dummy_alloc = sisdc.ALLOC_FN(lambda n, s, u: None)
+    assert lib.sisdc_set_allocator(None, dummy_alloc, sisdc.RELEASE_FN(), None) == sisdc.SISDC_E_ARG

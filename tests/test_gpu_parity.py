@@ -312,6 +312,36 @@ def test_step_parity_burgers2d_full_bench_configuration(dev):
         ctx.close()
 
 
+def test_step_parity_fixed_nutilde(dev):
+    """sisdc_problem.nu_tilde > 0 (a constant nu_tilde instead of
+    nu_d + dt_m/2 lam_max^2) against the oracle with the same option, and
+    the option does change the iterate of a step."""
+    w = inputs.scaled("burgers2d", nel=(5, 5))
+    X, Y = oracle_space(w, w["levels"][-1]).coords()
+    u0 = inputs.burgers2d_initial(X, Y)
+    dt = inputs.cfl_dt(0.5, 1.0 / 5, 7, inputs.max_wave_speed("burgers", u0))
+    fix = 0.02
+    om = oracle_ml(w)
+    for lv in om.levels:
+        lv.space.nu_tilde_fix = fix
+    ctx = make_ctx(w, nu_tilde=fix)
+    u = u0.copy()
+    du = T(u0, dev)
+    for n in range(2):
+        u = om.step(u, dt, 3, start="cascade")
+        S.sisdc_step(ctx.ctx, du, n * dt, dt, 3, S.START_IDS["cascade"], 1)
+        assert rel_l2(N(du), u) < TOL
+    S.sisdc_sync(ctx.ctx)
+    ctx.close()
+    plain = make_ctx(w)
+    dp = T(u0, dev)
+    for n in range(2):
+        S.sisdc_step(plain.ctx, dp, n * dt, dt, 3, S.START_IDS["cascade"], 1)
+    S.sisdc_sync(plain.ctx)
+    plain.close()
+    assert rel_l2(N(dp), u) > 1e-12
+
+
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_step_parity_burgers_small(dev, use_graph):
     w = inputs.scaled("burgers2d", nel=(6, 6))

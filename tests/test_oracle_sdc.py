@@ -161,6 +161,24 @@ def test_converged_result_independent_of_nutilde(monkeypatch):
     assert np.max(np.abs(few_ref - ml.step(u0, 0.2, 1))) > 1e-8   # nu_tilde does act
 
 
+def test_fixed_nutilde_option_same_collocation_limit():
+    """A space carrying a fixed nu_tilde (the option the library exposes as
+    sisdc_problem.nu_tilde) converges to the same collocation solution as the
+    method's nu_d + dt_m/2 lam_max^2, and with few sweeps it does act."""
+    mk = _tiny_problem()
+    X, _ = mk(4).coords()
+    u0 = np.sin(X)[None]
+
+    def run(ncyc, fix):
+        levels = [Level(mk(2), "radau_right", 3), Level(mk(4), "radau_right", 5)]
+        for lv in levels:
+            lv.space.nu_tilde_fix = fix
+        return MLSDC(levels, stages=2).step(u0, 0.2, ncyc)
+
+    assert np.max(np.abs(run(45, 0.1) - run(45, 0.0))) < 1e-12
+    assert np.max(np.abs(run(1, 0.1) - run(1, 0.0))) > 1e-8
+
+
 def test_mass_conservation_burgers_step():
     pde = Burgers2(5e-3)
     mk = lambda p: DGSpace(2, (4, 4), p, (0.0, 0.0), (1.0, 1.0), pde, cg_rtol=1e-15)
