@@ -63,6 +63,33 @@ def test_collocation_limit_is_pade(z, kind, Ms):
         assert abs(stability(z, Ms, kind, stages, ncycles=30, start="predictor") - pade) < 1e-12
 
 
+@pytest.mark.parametrize("kind,M,order", [("radau_right", 2, 3), ("radau_right", 3, 5),
+                                           ("lobatto", 3, 4), ("lobatto", 4, 6)])
+def test_converged_order_radau_2m_minus_1_lobatto_2m_minus_2(kind, M, order):
+    """At convergence the SDC step is the collocation method, of order 2M-1
+    on Radau-Right nodes (Radau IIA) and 2M-2 on Lobatto nodes (Lobatto
+    IIIA) (Sec. 3.3): the one-step error |R(z) - e^z| scales as |z|^(p+1)."""
+    z0 = -0.6 + 0.8j
+    errs = []
+    for h in (0.4, 0.2):
+        z = h * z0
+        errs.append(abs(stability(z, [M], kind, 2, ncycles=60) - np.exp(z)))
+    slope = np.log2(errs[0] / errs[1])
+    assert abs(slope - (order + 1)) < 0.35
+
+
+@pytest.mark.parametrize("stages", [1, 2])
+@pytest.mark.parametrize("M,sweeps", [(3, 1), (3, 4), (5, 2), (5, 8)])
+def test_radau_si_sdc_l_stable(stages, M, sweeps):
+    """L-stability of the SI-SDC step on Radau-Right nodes for any number of
+    sweeps (the property the paper cites for SI-SDC): as the stiff implicit
+    part grows, Re z -> -inf with the explicit part fixed, every iterate is
+    O(1/|z|), so R(z) -> 0."""
+    r = [abs(stability(-x + 2.0j, [M], "radau_right", stages, ncycles=sweeps)) for x in (1e8, 1e9)]
+    assert r[1] < 1e-7
+    assert 5.0 < r[0] / r[1] < 20.0          # decays like 1/|z|
+
+
 def test_mlsdc_fewer_cycles_than_sdc_sweeps():
     """MLSDC reaches a given accuracy in fewer fine sweeps (Sec. 5.2, Sec. 7)."""
     z = -2.0 + 4.0j
