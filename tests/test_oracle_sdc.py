@@ -152,6 +152,13 @@ def test_pde_converges_to_collocation(kind):
             _, Us = ml.step(u0, dt, nc, start="cascade", return_levels=True)
             errs.append(np.max(np.abs(Us[-1] - Uc)))
         assert errs[-1] < 1e-11 and errs[0] > errs[1] > errs[2]
+        # every level converges to the fine solution (the FAS right-hand side at
+        # work): the coarse iterate is the projection of the fine collocation
+        # solution, not the coarse level's own collocation solution
+        Pc = ml.T[0].project(Uc)
+        assert np.max(np.abs(Us[0] - Pc)) < 1e-11
+        own = _collocation(mk(2), kind, 3, ml.T[0].project_space(u0), dt)
+        assert np.max(np.abs(own - Pc)) > 1e-6
 
 
 @pytest.mark.parametrize("projection", ["interp", "l2"])
