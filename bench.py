@@ -580,11 +580,13 @@ def ensemble_arm(args):
     forms, main = {}, None
     nsteps_total = args.warmup + args.steps
     u0_host = ex_host = None
-    for prec_name in (args.precision, "mixed" if args.precision == "fp64" else "fp64"):
-        prec = S.SISDC_MIXED if prec_name == "mixed" else S.SISDC_FP64
+    # the mixed form on both levels and on the fine level only (bit 1)
+    names = [args.precision] + [n for n in ("fp64", "mixed", "mixed_fine_level") if n != args.precision]
+    for prec_name in names:
+        prec = S.SISDC_FP64 if prec_name == "fp64" else S.SISDC_MIXED
         E = S.Ensemble(insts, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
                        M=w["M"], Mc=w["Mc"], nodes=w["nodes"], ncycles=ncyc, start=w["start"],
-                       use_graph=0 if args.no_graph else 1)
+                       use_graph=0 if args.no_graph else 1, mixed_levels=2 if prec_name == "mixed_fine_level" else 0)
         if u0_host is None:       # the packed layout does not depend on the precision
             u0_host = exact_field(E, lambda d: 0.0)
             ex_host = exact_field(E, lambda d: nsteps_total * d["dt"])

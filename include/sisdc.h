@@ -406,6 +406,8 @@ typedef struct {
     int start;           /* SISDC_START_CASCADE or SISDC_START_PREDICTOR          */
     int post_sweep;      /* final fine sweep after the last cycle                 */
     int use_graph;       /* capture one ensemble step as a CUDA graph             */
+    int mixed_levels;    /* SISDC_MIXED only: bit 0 = coarse level, bit 1 = fine
+                            level run the mixed form, the other FP64; 0 = both  */
 } sisdc_ens_opts;
 
 /* Create an ensemble of n instances on the current device and the stream

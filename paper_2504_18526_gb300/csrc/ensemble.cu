@@ -221,7 +221,8 @@ void build_level(sisdc_ens_s* c, EnsGroup& g, int which, int P, int M, bool fine
     L.nq = P + 1;
     L.Q = L.nq * L.nq;
     L.M = M;
-    L.mix = c->opts.precision == SISDC_MIXED && P >= 3;
+    const int ml = c->opts.mixed_levels;
+    L.mix = c->opts.precision == SISDC_MIXED && P >= 3 && (ml == 0 || ((ml >> (fine ? 1 : 0)) & 1));
     if (!build_level_tables(P, M, c->opts.nodes == SISDC_LOBATTO, &L.tab)) {
         c->err = "table construction failed";
         throw Fail{SISDC_E_ARG};
@@ -569,6 +570,7 @@ sisdc_status sisdc_ens_create(const sisdc_ens_instance* inst, int n, const sisdc
     if (o->nodes != SISDC_RADAU_RIGHT && o->nodes != SISDC_LOBATTO) return SISDC_E_ARG;
     if (o->nodes == SISDC_LOBATTO && o->Mc < 2) return SISDC_E_ARG;
     if (o->precision != SISDC_FP64 && o->precision != SISDC_MIXED) return SISDC_E_ARG;
+    if (o->mixed_levels < 0 || o->mixed_levels > 3) return SISDC_E_ARG;
     if (o->si_stages != 1 && o->si_stages != 2) return SISDC_E_ARG;
     if (!(o->cg_rtol > 0.0) || o->cg_maxit < 1 || o->Nc < 0 || o->ncycles < 0) return SISDC_E_ARG;
     if (o->start != SISDC_START_CASCADE && o->start != SISDC_START_PREDICTOR) return SISDC_E_ARG;

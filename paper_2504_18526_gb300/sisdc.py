@@ -55,7 +55,7 @@ class sisdc_ens_instance(ctypes.Structure):
 class sisdc_ens_opts(ctypes.Structure):
     _fields_ = [("M", c_int), ("Mc", c_int), ("nodes", c_int), ("precision", c_int), ("si_stages", c_int),
                 ("cg_rtol", c_double), ("cg_maxit", c_int), ("Nc", c_int), ("ncycles", c_int), ("start", c_int),
-                ("post_sweep", c_int), ("use_graph", c_int)]
+                ("post_sweep", c_int), ("use_graph", c_int), ("mixed_levels", c_int)]
 
 
 class sisdc_stab_opts(ctypes.Structure):
@@ -546,11 +546,12 @@ def make_ens_instance(d):
 
 
 def make_ens_opts(M=5, Mc=3, nodes="radau_right", precision=SISDC_FP64, si_stages=2, cg_rtol=1e-12,
-                  cg_maxit=1000, Nc=2, ncycles=3, start="cascade", post_sweep=1, use_graph=0):
+                  cg_maxit=1000, Nc=2, ncycles=3, start="cascade", post_sweep=1, use_graph=0, mixed_levels=0):
     o = sisdc_ens_opts()
     o.M, o.Mc, o.nodes, o.precision, o.si_stages = M, Mc, NODE_IDS[nodes], precision, si_stages
     o.cg_rtol, o.cg_maxit, o.Nc, o.ncycles = cg_rtol, cg_maxit, Nc, ncycles
     o.start, o.post_sweep, o.use_graph = START_IDS[start], post_sweep, use_graph
+    o.mixed_levels = mixed_levels
     return o
 
 

@@ -151,20 +151,22 @@ def test_mixed_precision_error_within_bar(dev):
     exact solution after 10 steps is at most 1.05x the FP64 form's."""
     insts = inputs.ensemble_instances(12)
     insts = [dict(d, nel=(min(d["nel"][0], 12), min(d["nel"][1], 12))) for d in insts]
-    res = {}
-    for prec in (S.SISDC_FP64, S.SISDC_MIXED):
-        E = S.Ensemble(insts, cg_rtol=1e-12, cg_maxit=500, use_graph=1, precision=prec)
+    res, irs = {}, {}
+    # FP64; mixed on both levels; mixed on the fine level only (mixed_levels bit 1)
+    for key, prec, ml in (("fp64", S.SISDC_FP64, 0), ("mixed", S.SISDC_MIXED, 0), ("fine", S.SISDC_MIXED, 2)):
+        E = S.Ensemble(insts, cg_rtol=1e-12, cg_maxit=500, use_graph=1, precision=prec, mixed_levels=ml)
         u = pack(E, dev)
         S.sisdc_ens_step(E.ens, u, 10)
         S.sisdc_ens_sync(E.ens)
-        res[prec] = [unpack(E, u, k) for k in range(len(insts))]
-        if prec == S.SISDC_MIXED:
-            assert S.sisdc_ens_get_stats(E.ens)["ir_steps"] > 0
+        res[key] = [unpack(E, u, k) for k in range(len(insts))]
+        irs[key] = S.sisdc_ens_get_stats(E.ens)["ir_steps"]
         E.close()
+    assert irs["fp64"] == 0 and 0 < irs["fine"] < irs["mixed"]
     for k, d in enumerate(insts):
-        e64 = exact_error(d, res[S.SISDC_FP64][k], 10 * d["dt"])
-        emx = exact_error(d, res[S.SISDC_MIXED][k], 10 * d["dt"])
-        assert emx <= 1.05 * e64 + 1e-14, (k, e64, emx)
+        e64 = exact_error(d, res["fp64"][k], 10 * d["dt"])
+        for key in ("mixed", "fine"):
+            emx = exact_error(d, res[key][k], 10 * d["dt"])
+            assert emx <= 1.05 * e64 + 1e-14, (key, k, e64, emx)
 
 
 def test_full_ensemble_sampled_parity(dev):
