@@ -336,8 +336,10 @@ sisdc_status sisdc_get_kernel_timing(sisdc_ctx ctx, double* h_ms_total, long lon
  * z = r_centre + s MLP(r_patch / s) (the residual itself is the exact
  * correction as c -> 0; the network learns the deviation);
  * per element and component, n_in = 9 Q + 1 -> hidden -> hidden (tanh) -> Q.
- * Weights BF16 (bf16 = 1) or FP32 (bf16 = 0) with FP32 accumulation, FP32
- * master copy and Adam for training.  2D levels only. */
+ * bf16 = 1: BF16 weights, and every GEMM multiplies BF16 operands on the
+ * tensor cores with FP32 accumulation; bf16 = 0: FP32 weights and FP32 GEMMs
+ * (the reference form).  FP32 master copy and Adam for training.  2D levels
+ * with n_in <= 1024 (P <= 9); SISDC_E_ARG otherwise. */
 sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long seed, int bf16, sisdc_mlp* out);
 void sisdc_mlp_destroy(sisdc_mlp mlp);
 sisdc_status sisdc_mlp_info(sisdc_mlp mlp, int* n_in, int* hidden, int* n_out, long long* nparam);

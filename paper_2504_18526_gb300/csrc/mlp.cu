@@ -7,8 +7,11 @@
 // feature 0.1 log(c / h^2); a perceptron n_in -> H -> H -> Q with tanh hidden
 // layers predicts the deviation of the centre element's correction from r
 // itself (the exact correction as c -> 0): z = r + s MLP(r_patch / s).
-// Weights are BF16 (FP32 master copy for training), every product is
-// accumulated in FP32.
+// BF16 mode (the default): weights are BF16 (FP32 master copy for training),
+// both operands of every GEMM are BF16 on the tensor cores (warp-level
+// mma.sync m16n8k16) with FP32 accumulation, and the patch matrix is stored
+// in BF16.  FP32 mode: the same network with FP32 SIMT GEMMs, the reference
+// form for the gradient checks.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
