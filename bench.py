@@ -1,11 +1,18 @@
 #!/usr/bin/env python
 """Benchmark: fine-level DOF-sweeps/s of SI-MLSDC time steps on GB300.
 
-Workload (default): 2D viscous Burgers, 2 components, periodic [0,1]^2,
-nu = 5e-3, 32x32 elements, fine P = 7 / coarse P = 3, Radau-Right 5/3
-collocation nodes, SI(2), Cascade start, 3 V-cycles + final fine post-sweep
-per step (4 fine sweeps), dt from CFL 0.5.  One "step" = one time step
-through the C ABI (sisdc_step): every row of the hot path runs in it.
+Workload (default, the largest single-GPU configuration): an ensemble of 512
+independent 2D convection-diffusion problems on the periodic unit square
+(element grids 8^2..48^2, fine degree 3..8, coarse degree ceil(P/2),
+Radau-Right 5/3 collocation nodes, SI(2), Cascade start, 3 V-cycles + final
+fine post-sweep per step, dt from CFL 0.5 per instance; 21.7 M fine nodes),
+all instances of one degree in one persistent launch per sweep, one step as
+one CUDA graph.  One "step" = one time step of every instance through the C
+ABI (sisdc_ens_step): every row of the hot path runs in it.
+
+Other workloads (--workload): burgers2d, euler_vortex, euler256 (the vortex
+on 256^2 elements), ns_shear, convdiff1d (sisdc_step), stability_map,
+mlp_ns_level.
 
 Output: one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores instead (bounded samples of the same workload).
@@ -32,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sisdc", choices=["sisdc", "reference"])
-    ap.add_argument("--workload", default="burgers2d")
+    ap.add_argument("--workload", default="ensemble512")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cg-rtol", type=float, default=1e-12)
     ap.add_argument("--no-graph", action="store_true")
@@ -42,14 +49,28 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default tile shapes (no sisdc_autotune)")
     ap.add_argument("--per-instance", type=int, default=0,
                     help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-nel", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--shard", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--nshards", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--seconds", type=float, default=10.0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 def workload(args):
     from paper_2504_18526_gb300 import inputs
-    w = inputs.scaled(args.workload, nel=(8, 8) if args.small else None)
-    return w
+    nel = (8, 8) if args.small else None
+    if getattr(args, "oracle_nel", 0):
+        nel = (args.oracle_nel, args.oracle_nel)
+    return inputs.scaled(args.workload, nel=nel)
+
+
+# the largest fine level (DOFs) on which the CPU baseline times one full
+# oracle step; bigger workloads are sampled on a coarser element grid of the
+# same physics and levels (the oracle's cost per DOF does not depend on the
+# number of elements)
+ORACLE_MAX_DOFS = 1_100_000
 
 
 def fine_dofs(w):
@@ -152,7 +173,9 @@ def oracle_sample(args):
 
 
 def ensemble_oracle_sample(args):
-    """One oracle time step of each of the smallest ensemble instances (FP64)."""
+    """One oracle time step of ensemble instances, smallest first, this
+    shard's share of them (instances shard, shard + nshards, ...), until
+    `seconds` have passed (at least one instance)."""
     import numpy as np
     from paper_2504_18526_gb300 import inputs
     from oracle.dg import ConvDiff, DGSpace
@@ -160,11 +183,12 @@ def ensemble_oracle_sample(args):
     from oracle.sdc import Level
     w = inputs.WORKLOADS["ensemble512"]
     insts = inputs.ensemble_instances(w["ninst"])
-    order = np.argsort([d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2 for d in insts])
+    order = list(np.argsort([d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2 for d in insts], kind="stable"))
+    order = order[args.shard::max(1, args.nshards)]
     t0 = time.perf_counter()
     dofs = 0
     k = 0
-    while k < len(order) and (k < 2 or time.perf_counter() - t0 < 10.0):
+    while k < len(order) and (k < 1 or time.perf_counter() - t0 < args.seconds):
         d = insts[order[k]]
         sp = lambda P: DGSpace(2, d["nel"], P, (0.0, 0.0), (1.0, 1.0), ConvDiff(d["adv"], d["nu"]),
                                cg_rtol=args.cg_rtol, cg_maxit=1000)
@@ -176,6 +200,58 @@ def ensemble_oracle_sample(args):
         k += 1
     print(json.dumps({"seconds": time.perf_counter() - t0, "steps": 1, "instances": k, "dof_sweeps": dofs,
                       "finite": True}))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def ensemble_oracle_run(args, nshards, seconds):
+    """The oracle on `nshards` single-threaded processes at once, each on its
+    share of the instances for about `seconds`; DOF-sweeps/s over the wall
+    time of the slowest shard."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    procs = []
+    for sh in range(nshards):
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", "ensemble512",
+               "--cg-rtol", str(args.cg_rtol), "--shard", str(sh), "--nshards", str(nshards),
+               "--seconds", str(seconds)]
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                                      cwd=ROOT))
+    res = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle shard failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    wall = max(r["seconds"] for r in res)
+    dofs = sum(r["dof_sweeps"] for r in res)
+    return {"value": dofs / wall, "seconds": wall, "instances": sum(r["instances"] for r in res),
+            "dof_sweeps": dofs}
+
+
+def cpu_baseline_ensemble(args):
+    """The oracle as it stands on every host core (one process per core, each
+    on its share of the instances), and on one core."""
+    try:
+        n = host_cores()
+        allc = ensemble_oracle_run(args, n, 10.0)
+        one = ensemble_oracle_run(args, 1, 10.0)
+        return {"value": allc["value"], "unit": UNIT, "cores": n, "kind": "oracle",
+                "sample": "one FP64 numpy oracle time step of %d ensemble instances (smallest first, "
+                          "spread over %d single-threaded processes), %.1f s wall" %
+                          (allc["instances"], n, allc["seconds"]),
+                "cpu": cpu_model(),
+                "single_thread": {"value": one["value"], "cores": 1,
+                                  "sample": "%d instances, smallest first, %.1f s" % (one["instances"],
+                                                                                       one["seconds"])}}
+    except Exception as e:   # reported, not fatal
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
 
 
 def mlp_oracle_sample(args):
@@ -196,12 +272,27 @@ def mlp_oracle_sample(args):
     print(json.dumps({"seconds": time.perf_counter() - t0, "rows": rows * reps, "passes": reps}))
 
 
-def run_oracle_child(args, steps):
+def oracle_nel_for(args):
+    """0 = the workload's own grid, else the elements per side of the sample."""
+    if args.small or args.workload in ("ensemble512", "mlp_ns_level", "stability_map"):
+        return 0
+    w = workload(args)
+    n = fine_dofs(w)
+    nel = w["levels"][-1]["nel"][0]
+    while n > ORACLE_MAX_DOFS and nel % 2 == 0:
+        nel //= 2
+        n //= 4
+    return 0 if nel == w["levels"][-1]["nel"][0] else nel
+
+
+def run_oracle_child(args, steps, nel=0):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--steps", str(steps),
            "--workload", args.workload, "--cg-rtol", str(args.cg_rtol)] + (["--small"] if args.small else [])
+    if nel:
+        cmd += ["--oracle-nel", str(nel)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
@@ -226,17 +317,20 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "ensemble512":
+        return reference_arm_ensemble(args)
     w = workload(args)
+    onel = oracle_nel_for(args)
     for _ in range(args.warmup):
-        run_oracle_child(args, 1)
+        run_oracle_child(args, 1, onel)
     tot_s, tot_d = 0.0, 0
     for _ in range(args.steps):
-        r = run_oracle_child(args, 1)
+        r = run_oracle_child(args, 1, onel)
         tot_s += r["seconds"]
         tot_d += r["dof_sweeps"]
     v = tot_d / tot_s
-    sample = "%d oracle time steps (1 per bench step) of the %s workload, FP64 numpy, 1 thread" % (
-        args.steps, args.workload)
+    sample = "%d oracle time steps (1 per bench step) of the %s workload%s, FP64 numpy, 1 thread" % (
+        args.steps, args.workload, " on %d^2 elements (same physics, degrees and nodes)" % onel if onel else "")
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -244,6 +338,36 @@ def reference_arm(args):
            "config": {"workload": args.workload, "fine_dofs": fine_dofs(w), "levels": w["levels"],
                       "fine_sweeps_per_step": w["ncycles"] + 1},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "cpu": cpu_model()},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def reference_arm_ensemble(args):
+    """The oracle as it stands on every host core: each bench step is one
+    bounded sample (about 3 s of wall time) of ensemble instances, one oracle
+    time step each, spread over one single-threaded process per core."""
+    from paper_2504_18526_gb300 import inputs
+    w = inputs.WORKLOADS["ensemble512"]
+    n = host_cores()
+    for _ in range(args.warmup):
+        ensemble_oracle_run(args, n, 1.0)
+    tot_s, tot_d, tot_i = 0.0, 0, 0
+    for _ in range(args.steps):
+        r = ensemble_oracle_run(args, n, 3.0)
+        tot_s += r["seconds"]
+        tot_d += r["dof_sweeps"]
+        tot_i += r["instances"]
+    v = tot_d / tot_s
+    sample = ("%d samples (1 per bench step) of about 3 s: one FP64 numpy oracle time step of each of %d "
+              "ensemble instances in all (smallest first), %d single-threaded processes" % (args.steps, tot_i, n))
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "ensemble512", "instances": w["ninst"],
+                      "fine_sweeps_per_step": w["ncycles"] + 1},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample,
                             "cpu": cpu_model()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -289,10 +413,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x 
 def sweep_bytes(M, nsweeps, iters, nv):
     return 8.0 * nv * (nsweeps * M * (11 + 2 * 4) + iters * 11)
 
-# DRAM bytes (read + write) of one fine-level correction-sweep launch of the
-# burgers2d workload (FP64 form), from the ncu capture summarised in
-# profiles/k_sweep_burgers2d_fp64.md; None for other workloads or forms.
-SWEEP_TRAFFIC_BYTES = {("burgers2d", "fp64"): 22.407168e6 + 13.949952e6}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# fine-level correction-sweep launch, from an ncu capture of that launch, per
+# (workload, form), with the digest of the kernel sources it was measured on;
+# reported as null for any other kernel version.
+SWEEP_TRAFFIC_BYTES = {}
+SWEEP_KERNEL_SOURCES = ("sweep.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh")
 
 
 # ---------------------------------------------------------------------------
@@ -311,6 +437,13 @@ def max_over_ranks(ms, dist=None, device=None):
 def whole_job_value(units_per_step_per_rank, steps, world, ms):
     """Units processed by all ranks per second (weak scaling: fixed work per rank)."""
     return world * units_per_step_per_rank * steps / (ms * 1e-3)
+
+
+def sweep_traffic(args):
+    rec = SWEEP_TRAFFIC_BYTES.get((args.workload, args.precision))
+    if args.small or not rec or rec[1] != kernel_digest(SWEEP_KERNEL_SOURCES):
+        return None
+    return rec[0]
 
 
 def make_ctx(S, w, stream, prec, rtol, use_graph, mixed_levels=0):
@@ -453,52 +586,56 @@ def main_arm(args):
     hbm_gbs = nbytes / (avg_ms * 1e-3) / 1e9
 
     # ---- the other precision form and time-to-solution at equal L2 error ----
-    forms = {}
-    win = max(4, min(20, args.steps))
-    ref_ctx = make_ctx(S, w, stream, S.SISDC_FP64, min(args.cg_rtol, 1e-13), 1)
-    ur = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
-    torch.cuda.synchronize()
-    run_steps(S, ref_ctx, ur, dt / 4, 6, start, 4 * win)
-    S.sisdc_sync(ref_ctx.ctx)
-    ref_ctx.close()
-    # mixed form on every level, and on the finest level only (the coarse
-    # level's sweeps are barrier-latency bound, where FP64 solves are faster)
-    for pf, name, mask in ((S.SISDC_FP64, "fp64_plain", 0), (S.SISDC_MIXED, "mixed_all_levels", 0),
-                           (S.SISDC_MIXED, "mixed_fine_level", 1 << (nlev - 1))):
-        fctx = make_ctx(S, w, stream, pf, args.cg_rtol, 1, mask)
-        uf = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
-        tune(S, args, fctx, uf, dt, nlev)
-        run_steps(S, fctx, uf, dt, ncyc, start, 2)                 # capture + warm
-        S.sisdc_sync(fctx.ctx)                                     # the reset must follow them
-        uf.copy_(torch.from_numpy(np.ascontiguousarray(u0)))
+    forms, tts = {}, None
+    if not args.no_forms:
+        win = max(4, min(20, args.steps))
+        ref_ctx = make_ctx(S, w, stream, S.SISDC_FP64, min(args.cg_rtol, 1e-13), 1)
+        ur = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
         torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        run_steps(S, fctx, uf, dt, ncyc, start, win)
-        a1.record(stream)
-        S.sisdc_sync(fctx.ctx)
-        tms = a0.elapsed_time(a1)
-        err = float(torch.linalg.vector_norm(uf - ur) / torch.linalg.vector_norm(ur))
-        forms[name] = {"ms_per_step": tms / win, "dof_sweeps_per_s": dofs_per_step * win / (tms * 1e-3),
-                       "time_to_solution_ms": tms, "rel_l2_error_vs_reference": err, "mixed_levels": mask}
-        fctx.close()
-    best = min(("mixed_all_levels", "mixed_fine_level"), key=lambda k: forms[k]["time_to_solution_ms"])
-    forms["mixed_tuned"] = dict(forms[best], variant=best)
-    tts = {"window_steps": win, "reference": "FP64 GPU path at dt/4 with 6 V-cycles per step",
-           "error_ratio_tuned_over_plain": forms["mixed_tuned"]["rel_l2_error_vs_reference"] /
-           max(1e-300, forms["fp64_plain"]["rel_l2_error_vs_reference"]),
-           "speedup_tuned_over_plain": forms["fp64_plain"]["time_to_solution_ms"] /
-           forms["mixed_tuned"]["time_to_solution_ms"]}
+        run_steps(S, ref_ctx, ur, dt / 4, 6, start, 4 * win)
+        S.sisdc_sync(ref_ctx.ctx)
+        ref_ctx.close()
+        # mixed form on every level, and on the finest level only (the coarse
+        # level's sweeps are barrier-latency bound, where FP64 solves are faster)
+        for pf, name, mask in ((S.SISDC_FP64, "fp64_plain", 0), (S.SISDC_MIXED, "mixed_all_levels", 0),
+                               (S.SISDC_MIXED, "mixed_fine_level", 1 << (nlev - 1))):
+            fctx = make_ctx(S, w, stream, pf, args.cg_rtol, 1, mask)
+            uf = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+            tune(S, args, fctx, uf, dt, nlev)
+            run_steps(S, fctx, uf, dt, ncyc, start, 2)                 # capture + warm
+            S.sisdc_sync(fctx.ctx)                                     # the reset must follow them
+            uf.copy_(torch.from_numpy(np.ascontiguousarray(u0)))
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            run_steps(S, fctx, uf, dt, ncyc, start, win)
+            a1.record(stream)
+            S.sisdc_sync(fctx.ctx)
+            tms = a0.elapsed_time(a1)
+            err = float(torch.linalg.vector_norm(uf - ur) / torch.linalg.vector_norm(ur))
+            forms[name] = {"ms_per_step": tms / win, "dof_sweeps_per_s": dofs_per_step * win / (tms * 1e-3),
+                           "time_to_solution_ms": tms, "rel_l2_error_vs_reference": err, "mixed_levels": mask}
+            fctx.close()
+        best = min(("mixed_all_levels", "mixed_fine_level"), key=lambda k: forms[k]["time_to_solution_ms"])
+        forms["mixed_tuned"] = dict(forms[best], variant=best)
+        tts = {"window_steps": win, "reference": "FP64 GPU path at dt/4 with 6 V-cycles per step",
+               "error_ratio_tuned_over_plain": forms["mixed_tuned"]["rel_l2_error_vs_reference"] /
+               max(1e-300, forms["fp64_plain"]["rel_l2_error_vs_reference"]),
+               "speedup_tuned_over_plain": forms["fp64_plain"]["time_to_solution_ms"] /
+               forms["mixed_tuned"]["time_to_solution_ms"]}
+
 
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            r = run_oracle_child(args, 1 if not args.small else 3)
+            onel = oracle_nel_for(args)
+            r = run_oracle_child(args, 1 if not args.small else 3, onel)
+            grid = " on %d^2 elements (same physics, degrees and nodes)" % onel if onel else ""
             cpu = {"value": r["dof_sweeps"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "%d full time step(s) of the %s workload by the FP64 numpy oracle "
-                             "(single-threaded BLAS), %.1f s" % (r["steps"], args.workload, r["seconds"]),
+                   "sample": "%d full time step(s) of the %s workload%s by the FP64 numpy oracle "
+                             "(single-threaded BLAS), %.1f s" % (r["steps"], args.workload, grid, r["seconds"]),
                    "cpu": cpu_model()}
         except Exception as e:   # reported, not fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
@@ -520,7 +657,7 @@ def main_arm(args):
         "roofline": {"bound": "alu", "kernel": "k_sweep correction launches, fine level",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None if args.small else SWEEP_TRAFFIC_BYTES.get((args.workload, args.precision)),
+                     "traffic": sweep_traffic(args),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
                      "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20)",
                      "avg_launch_us": avg_ms * 1e3, "launches": kt["launches"],
@@ -548,16 +685,58 @@ def main_arm(args):
 # ---------------------------------------------------------------------------
 # ensemble workload: 512 independent convection-diffusion problems
 # ---------------------------------------------------------------------------
+def kernel_digest(files):
+    """Short digest of the kernel sources (ties a stored ncu traffic figure
+    to the kernel version it was measured on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2504_18526_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+ENS_KERNEL_SOURCES = ("ens.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh")
+
+# DRAM traffic of the dominant ensemble launch (a fine-level correction sweep
+# of the P = 8 group, FP64 form): dram__bytes_read.sum + dram__bytes_write.sum
+# of one ncu capture of that launch on the first 96 instances of the draw,
+# per fine node of the group (the traffic grows with the group's nodes: the
+# group's arrays exceed L2 in both cases), and the digest of the kernel
+# sources it was measured on; traffic is reported as null for any other
+# kernel version or form.
+ENS_TRAFFIC = {"digest": None, "bytes_per_node": None, "P": 8, "form": "fp64"}
+
+
+def ens_cfg_apply(S, ens, cfg):
+    """Set the tile shapes of sisdc_ens_config rows (fine, then coarse, per group)."""
+    for g in range(len(cfg) // 2):
+        for fine, row in ((1, cfg[2 * g]), (0, cfg[2 * g + 1])):
+            S.sisdc_ens_set_tiles(ens, g, fine, int(row[2]), int(row[3]))
+
+
 def ensemble_arm(args):
     import numpy as np
     import torch
     from paper_2504_18526_gb300 import inputs, sisdc as S
-    from paper_2504_18526_gb300.build import build
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    build()
+    if rank == 0 or world == 1:
+        from paper_2504_18526_gb300.build import build
+        build()
+    if dist:
+        dist.barrier()
     S.load()
+
     w = inputs.WORKLOADS["ensemble512"]
     insts = inputs.ensemble_instances(w["ninst"])
     if args.ninst > 0:
@@ -567,129 +746,214 @@ def ensemble_arm(args):
     nodes = [d["nel"][0] * d["nel"][1] * (d["P"] + 1) ** 2 for d in insts]
     dofs_per_step = sum(nodes) * (ncyc + 1)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    names = {"fp64": (S.SISDC_FP64, 0), "mixed": (S.SISDC_MIXED, 0), "mixed_fine_level": (S.SISDC_MIXED, 2)}
 
-    def exact_field(E, t_of):
-        from oracle.dg import ConvDiff, DGSpace
+    def make(name, graph):
+        prec, mask = names[name]
+        return S.Ensemble(insts, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
+                          M=w["M"], Mc=w["Mc"], nodes=w["nodes"], ncycles=ncyc, start=w["start"],
+                          use_graph=graph, mixed_levels=mask)
+
+    main_name = "fp64" if args.precision == "fp64" else "mixed"
+    E = make(main_name, 0 if args.no_graph else 1)
+    # initial data and exact solutions at the library's node coordinates
+    hx, hy = np.zeros(E.total), np.zeros(E.total)
+    S.sisdc_ens_coords(E.ens, hx, hy)
+
+    def exact_field(t_of):
         u = np.zeros(E.total)
         for k, d in enumerate(insts):
-            sp = DGSpace(2, d["nel"], d["P"], (0.0, 0.0), (1.0, 1.0), ConvDiff(d["adv"], d["nu"]))
-            X, Y = sp.coords()
-            u[E.offsets[k]:E.offsets[k] + nodes[k]] = inputs.ensemble_exact(d, X, Y, t_of(d)).ravel()
+            a, b = E.offsets[k], E.offsets[k] + nodes[k]
+            u[a:b] = inputs.ensemble_exact(d, hx[a:b], hy[a:b], t_of(d)).ravel()
         return u
 
-    forms, main = {}, None
+    u0_host = exact_field(lambda d: 0.0)
+    u0 = torch.from_numpy(u0_host).to(dev)
+    cfg = S.sisdc_ens_config(E.ens) if args.no_autotune else S.sisdc_ens_autotune(E.ens, u0, 1)
+    u = u0.clone()
+    S.sisdc_ens_step(E.ens, u, args.warmup)
+    S.sisdc_ens_sync(E.ens)
+    S.sisdc_ens_reset_stats(E.ens)
+
+    # ---- timed region: K steps, L2 flushed between steps -------------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        evs[k][0].record(stream)
+        S.sisdc_ens_step(E.ens, u, 1)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    S.sisdc_ens_sync(E.ens)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    st = S.sisdc_ens_get_stats(E.ens, len(insts))
+    ms = max_over_ranks(ms, dist, dev)
+    value = whole_job_value(dofs_per_step, args.steps, world, ms)
     nsteps_total = args.warmup + args.steps
-    u0_host = ex_host = None
-    # the mixed form on both levels and on the fine level only (bit 1)
-    names = [args.precision] + [n for n in ("fp64", "mixed", "mixed_fine_level") if n != args.precision]
-    for prec_name in names:
-        prec = S.SISDC_FP64 if prec_name == "fp64" else S.SISDC_MIXED
-        E = S.Ensemble(insts, stream=stream.cuda_stream, precision=prec, cg_rtol=args.cg_rtol, cg_maxit=1000,
-                       M=w["M"], Mc=w["Mc"], nodes=w["nodes"], ncycles=ncyc, start=w["start"],
-                       use_graph=0 if args.no_graph else 1, mixed_levels=2 if prec_name == "mixed_fine_level" else 0)
-        if u0_host is None:       # the packed layout does not depend on the precision
-            u0_host = exact_field(E, lambda d: 0.0)
-            ex_host = exact_field(E, lambda d: nsteps_total * d["dt"])
-        u0 = torch.from_numpy(u0_host).to(dev)
-        cfg = S.sisdc_ens_config(E.ens) if args.no_autotune else S.sisdc_ens_autotune(E.ens, u0, 1)
-        u = u0.clone()
-        S.sisdc_ens_step(E.ens, u, args.warmup)
-        S.sisdc_ens_sync(E.ens)
-        S.sisdc_ens_reset_stats(E.ens)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        sampler = ClockSampler(dev.index or 0)
-        sampler.start()
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))
-            evs[k][0].record(stream)
-            S.sisdc_ens_step(E.ens, u, 1)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        clocks = sampler.stop()
-        S.sisdc_ens_sync(E.ens)
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        st = S.sisdc_ens_get_stats(E.ens, len(insts))
+    ex_host = exact_field(lambda d: nsteps_total * d["dt"])
+
+    def errors(uu):
         ex = torch.from_numpy(ex_host).to(dev)
         rel = []
         for k in range(len(insts)):
             a, b = E.offsets[k], E.offsets[k] + nodes[k]
-            rel.append(float(torch.linalg.vector_norm(u[a:b] - ex[a:b]) / torch.linalg.vector_norm(ex[a:b])))
-        # algorithmic FP64 work of the fine-level sweeps per step (coarse level not counted)
-        iters = st["inst_iters"] / args.steps
-        flops = sum(sweep_flops(d["P"], 1, w["M"], ncyc + 1, iters[k], nodes[k]) for k, d in enumerate(insts))
-        achieved = flops / (ms / args.steps * 1e-3) / 1e12
-        forms[prec_name] = {
-            "ms_per_step": ms / args.steps, "dof_sweeps_per_s": dofs_per_step * args.steps / (ms * 1e-3),
-            "rel_l2_error_vs_exact": {"mean": float(np.mean(rel)), "max": float(np.max(rel))},
-            "steps_for_error": nsteps_total,
-            "cg_iters_per_solve": st["cg_iters"] / max(1, st["cg_solves"]),
-            "ir_steps": st["ir_steps"], "launches_per_step": st["launches"] / args.steps,
-            "fine_sweep_fp64_tflops": achieved,
-            "tiles": cfg.tolist(), "clocks": clocks}
-        if main is None:
-            main = dict(forms[prec_name], ms=ms, clocks=clocks, achieved=achieved, flops=flops, st=st)
-        E.close()
+            rel.append(float(torch.linalg.vector_norm(uu[a:b] - ex[a:b]) / torch.linalg.vector_norm(ex[a:b])))
+        return {"mean": float(np.mean(rel)), "max": float(np.max(rel))}
 
-    per_inst = None
-    if args.per_instance > 0:
-        # the same instances stepped one by one through the single-problem path (FP64)
-        idx = list(range(0, len(insts), max(1, len(insts) // args.per_instance)))[: args.per_instance]
-        tot_ms, tot_nodes = 0.0, 0
-        for k in idx:
-            d = insts[k]
-            wk = dict(pde="convdiff", dim=2, ncomp=1, adv=d["adv"], nu=d["nu"], lo=(0.0, 0.0), hi=(1.0, 1.0),
-                      nodes=w["nodes"], levels=[dict(nel=d["nel"], P=(d["P"] + 1) // 2, M=w["Mc"]),
-                                                dict(nel=d["nel"], P=d["P"], M=w["M"])])
-            ctx = S.Context(wk, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, cg_maxit=1000, use_graph=1)
-            from oracle.dg import ConvDiff, DGSpace
-            X, Y = DGSpace(2, d["nel"], d["P"], (0.0, 0.0), (1.0, 1.0), ConvDiff(d["adv"], d["nu"])).coords()
-            uk = torch.from_numpy(inputs.ensemble_exact(d, X, Y, 0.0).ravel().copy()).to(dev)
-            for _ in range(2):
-                S.sisdc_step(ctx.ctx, uk, 0.0, d["dt"], ncyc, S.START_IDS[w["start"]], 1)
-            S.sisdc_sync(ctx.ctx)
+    err_main = errors(u)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region --
+    h_in = torch.from_numpy(u0_host).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_e2e = torch.empty_like(u0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ke = max(3, args.steps // 4)
+    t_e2e = 0.0
+    torch.cuda.synchronize()
+    for k in range(ke):
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            d_e2e.copy_(h_in, non_blocking=True)
+        S.sisdc_ens_step(E.ens, d_e2e, 1)
+        with torch.cuda.stream(stream):
+            h_out.copy_(d_e2e, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e += e0.elapsed_time(e1)
+    S.sisdc_ens_sync(E.ens)
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
+    e2e_val = world * dofs_per_step * ke / (t_e2e * 1e-3)
+    E.close()
+
+    # ---- dominant kernel: live CUDA-event timing of the fine correction launches --
+    Ek = make(main_name, 0)
+    ens_cfg_apply(S, Ek.ens, cfg)
+    uk = u0.clone()
+    S.sisdc_ens_step(Ek.ens, uk, 1)
+    S.sisdc_ens_sync(Ek.ens)
+    S.sisdc_ens_reset_stats(Ek.ens)
+    S.sisdc_ens_set_kernel_timing(Ek.ens, True)
+    kt_steps = 2
+    t0 = time.perf_counter()
+    for k in range(kt_steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        S.sisdc_ens_step(Ek.ens, uk, 1)
+    g_ms, g_launch = S.sisdc_ens_get_kernel_timing(Ek.ens)
+    eager_ms = (time.perf_counter() - t0) * 1e3
+    kst = S.sisdc_ens_get_stats(Ek.ens, len(insts))
+    S.sisdc_ens_sync(Ek.ens)
+    Ek.close()
+    degrees = sorted({d["P"] for d in insts})
+    per_group = []
+    for gi, P in enumerate(degrees):
+        members = [k for k, d in enumerate(insts) if d["P"] == P]
+        nl = max(1, int(g_launch[gi]))
+        fl = sum(sweep_flops(P, 1, w["M"], 1, kst["inst_iters"][k] / nl, nodes[k]) for k in members)
+        per_group.append({"P": P, "instances": len(members), "fine_nodes": sum(nodes[k] for k in members),
+                          "launches": int(g_launch[gi]), "avg_launch_ms": float(g_ms[gi]) / nl,
+                          "algorithmic_flop_per_launch": fl,
+                          "tflops": fl / (float(g_ms[gi]) / nl * 1e-3) / 1e12 if g_ms[gi] > 0 else 0.0})
+    dom = max(per_group, key=lambda r: r["avg_launch_ms"] * r["launches"])
+    traffic = None
+    if (ENS_TRAFFIC["digest"] == kernel_digest(ENS_KERNEL_SOURCES) and dom["P"] == ENS_TRAFFIC["P"]
+            and main_name == ENS_TRAFFIC["form"] and ENS_TRAFFIC["bytes_per_node"]):
+        traffic = ENS_TRAFFIC["bytes_per_node"] * dom["fine_nodes"]
+    hbm_peak, hbm_kind = measured_peaks()
+    dom_members = [k for k, d in enumerate(insts) if d["P"] == dom["P"]]
+    nbytes = sum(sweep_bytes(w["M"], 1, kst["inst_iters"][k] / max(1, dom["launches"]), nodes[k])
+                 for k in dom_members)
+
+    # ---- the other precision forms: time-to-solution at equal error vs exact --
+    forms = {main_name: {"ms_per_step": ms / args.steps, "dof_sweeps_per_s": value / world,
+                         "rel_l2_error_vs_exact": err_main, "steps_for_error": nsteps_total,
+                         "cg_iters_per_solve": st["cg_iters"] / max(1, st["cg_solves"]),
+                         "ir_steps": st["ir_steps"], "tiles": cfg.tolist()}}
+    if not args.no_forms:
+        for name in [n for n in ("fp64", "mixed_fine_level") if n != main_name]:
+            Ef = make(name, 0 if args.no_graph else 1)
+            cf = S.sisdc_ens_config(Ef.ens) if args.no_autotune else S.sisdc_ens_autotune(Ef.ens, u0, 1)
+            uf = u0.clone()
+            S.sisdc_ens_step(Ef.ens, uf, args.warmup)
+            S.sisdc_ens_sync(Ef.ens)
+            S.sisdc_ens_reset_stats(Ef.ens)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
             a0.record(stream)
-            S.sisdc_step(ctx.ctx, uk, 0.0, d["dt"], ncyc, S.START_IDS[w["start"]], 1)
+            S.sisdc_ens_step(Ef.ens, uf, args.steps)
             a1.record(stream)
-            S.sisdc_sync(ctx.ctx)
-            tot_ms += a0.elapsed_time(a1)
-            tot_nodes += nodes[k]
-            ctx.close()
-        per_inst = {"instances": len(idx), "ms_for_sample": tot_ms,
-                    "dof_sweeps_per_s": tot_nodes * (ncyc + 1) / (tot_ms * 1e-3),
-                    "note": "FP64 single-problem path, one graph-captured step per instance, sequential"}
+            S.sisdc_ens_sync(Ef.ens)
+            tms = a0.elapsed_time(a1)
+            sf = S.sisdc_ens_get_stats(Ef.ens, 0)
+            forms[name] = {"ms_per_step": tms / args.steps, "dof_sweeps_per_s": dofs_per_step * args.steps / (tms * 1e-3),
+                           "rel_l2_error_vs_exact": errors(uf), "steps_for_error": nsteps_total,
+                           "cg_iters_per_solve": sf["cg_iters"] / max(1, sf["cg_solves"]),
+                           "ir_steps": sf["ir_steps"], "tiles": cf.tolist()}
+            Ef.close()
+    tts = None
+    if "fp64" in forms and "mixed_fine_level" in forms:
+        tts = {"window_steps": nsteps_total, "reference": "exact solution of every instance",
+               "error_ratio_tuned_over_plain": forms["mixed_fine_level"]["rel_l2_error_vs_exact"]["mean"] /
+               max(1e-300, forms["fp64"]["rel_l2_error_vs_exact"]["mean"]),
+               "speedup_tuned_over_plain": forms["fp64"]["ms_per_step"] / forms["mixed_fine_level"]["ms_per_step"]}
 
-    cpu = None
-    if not args.no_cpu_baseline:
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", "ensemble512",
-                            "--cg-rtol", str(args.cg_rtol)], capture_output=True, text=True, env=env, cwd=ROOT)
-        if r.returncode == 0:
-            o = json.loads(r.stdout.strip().splitlines()[-1])
-            cpu = {"value": o["dof_sweeps"] / o["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "one oracle time step of each of the %d smallest instances (%.1f s, FP64 numpy, "
-                             "1 thread)" % (o["instances"], o["seconds"]), "cpu": cpu_model()}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline_ensemble(args)
     out = {
-        "metric": METRIC, "value": dofs_per_step * args.steps / (main["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "dtype": "f64" if main_name == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": "ensemble512" + (" (first %d instances)" % len(insts) if args.ninst else ""),
                    "instances": len(insts), "fine_nodes": sum(nodes), "autotuned": not args.no_autotune,
                    "fine_sweeps_per_step": ncyc + 1, "levels": "fine P, coarse ceil(P/2); Radau-Right 5/3",
-                   "precision": args.precision, "cuda_graph": not args.no_graph,
-                   "l2": "state larger than L2 (174 MB per vector) and 512 MB flush between steps"},
-        "roofline": {"bound": "alu", "kernel": "k_ens_sweep (all launches of a step; fine-level work counted)",
-                     "achieved": main["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": main["achieved"] / FP64_PEAK_TFLOPS, "traffic": None,
-                     "algorithmic_flop_per_step": main["flops"]},
-        "forms": forms, "per_instance_path": per_inst, "cpu_baseline": cpu, "clocks": main["clocks"],
-        "gpu_launches": int(round(main["st"]["launches"])),
+                   "start": w["start"], "si_stages": 2, "cg_rtol": args.cg_rtol,
+                   "precision": main_name, "cuda_graph": not args.no_graph,
+                   "l2": "state larger than L2 (%.0f MB per vector) and a 512 MB flush between timed steps"
+                         % (sum(nodes) * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "k_ens_sweep fine-level correction launch of the P = %d group"
+                                               % dom["P"],
+                     "achieved": dom["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": dom["tflops"] / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+                     "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured 1.20)",
+                     "avg_launch_us": dom["avg_launch_ms"] * 1e3, "launches": dom["launches"],
+                     "algorithmic_flop_per_launch": dom["algorithmic_flop_per_launch"],
+                     "kernel_share_of_step": sum(r["avg_launch_ms"] * r["launches"] for r in per_group) /
+                     max(1e-9, eager_ms),
+                     "step_level_frac": sum(sweep_flops(d["P"], 1, w["M"], ncyc + 1,
+                                                        st["inst_iters"][k] / args.steps, nodes[k])
+                                            for k, d in enumerate(insts)) / (ms / args.steps * 1e-3) / 1e12
+                     / FP64_PEAK_TFLOPS,
+                     "groups": per_group},
+        "hbm_view": {"algorithmic_bytes_per_launch": nbytes,
+                     "achieved": nbytes / (dom["avg_launch_ms"] * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": nbytes / (dom["avg_launch_ms"] * 1e-3) / 1e9 / hbm_peak,
+                     "peak_kind": hbm_kind + " copy bandwidth",
+                     "note": "bytes the launch would move if no array stayed on chip; the kernel is FP64-ALU "
+                             "bound, so this is not its limit"},
+        "forms": forms, "time_to_solution": tts, "cpu_baseline": cpu, "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(sum(nodes)) * 8,
+                "d2h_bytes_per_step": int(sum(nodes)) * 8},
+        "gpu_launches": int(round(st["launches"])),
+        "cg": {"solves_per_step": st["cg_solves"] / args.steps,
+               "iters_per_solve": st["cg_iters"] / max(1, st["cg_solves"]), "max_iters": st["cg_max_iters"]},
     }
     print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------

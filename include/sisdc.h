@@ -230,7 +230,11 @@ sisdc_status sisdc_solve(sisdc_level lv, double c, const double* d_rhs, double* 
  * the same Jacobi-PCG kernel, but needs no context and no level: every
  * piece of scratch lives in one static device array of
  * SISDC_NOALLOC_SCRATCH_BYTES (16 MiB) that each GPU loading the library
- * holds until the process exits.  It calls no cudaMalloc/cudaFree.
+ * holds until the process exits.  It calls no cudaMalloc/cudaFree; the
+ * driver commits the array when it loads the library's code on a device,
+ * which under CUDA's default lazy module loading happens at the first call
+ * on that device (that call may then take memory and synchronise, the later
+ * ones do not): make that first call at set-up time.
  *   - Fits when 5 * NV doubles (NV = ncomp * nodes) plus face traces and
  *     tables fit in the array (e.g. 2 x 32x32 elements of P = 7); larger
  *     problems are rejected with SISDC_E_ARG and a message in h_err.
@@ -426,6 +430,13 @@ void sisdc_ens_destroy(sisdc_ens ens);
  * Either pointer may be NULL. */
 sisdc_status sisdc_ens_layout(sisdc_ens ens, long long* h_offsets, long long* h_total);
 
+/* Node coordinates of the packed state (host arrays of *total doubles, as
+ * sisdc_ens_layout): instance k's node (ey, ex, j, i) sits at
+ * x = (ex + (xi_i + 1)/2) / nel[0], y = (ey + (xi_j + 1)/2) / nel[1] on the
+ * unit square, xi the GLL nodes of its degree (Sec. 6).  For evaluating
+ * initial data and exact solutions at the nodes.  h_y may be NULL. */
+sisdc_status sisdc_ens_coords(sisdc_ens ens, double* h_x, double* h_y);
+
 /* Advance every instance by nsteps steps of its own dt; d_u = packed state
  * (device, caller-owned), updated in place.  Asynchronous on the stream. */
 sisdc_status sisdc_ens_step(sisdc_ens ens, double* d_u, int nsteps);
@@ -454,6 +465,16 @@ sisdc_status sisdc_ens_sync(sisdc_ens ens);
  * CG iterations of each instance. */
 sisdc_status sisdc_ens_get_stats(sisdc_ens ens, sisdc_stats* out, long long* h_inst_iters);
 sisdc_status sisdc_ens_reset_stats(sisdc_ens ens);
+
+/* Measurement hook: with enable != 0, every fine-level correction-sweep
+ * launch of every group is bracketed by CUDA events on the ensemble's
+ * stream (eager mode only: SISDC_E_STATE when use_graph is set).
+ * sisdc_ens_get_kernel_timing (synchronous) returns, per group (in
+ * increasing degree; arrays of sisdc_ens_num_groups entries, nullable), the
+ * summed launch time in ms and the number of launches since the hook was
+ * enabled or last read, and clears them. */
+sisdc_status sisdc_ens_set_kernel_timing(sisdc_ens ens, int enable);
+sisdc_status sisdc_ens_get_kernel_timing(sisdc_ens ens, double* h_ms, long long* h_launches);
 const char* sisdc_ens_last_error(sisdc_ens ens);
 
 /* --- stability function on the Dahlquist problem (Sec. 5) -----------------

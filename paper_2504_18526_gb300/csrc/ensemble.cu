@@ -146,6 +146,11 @@ struct sisdc_ens_s {
     long long launches = 0;
     long long sweeps[2] = {0, 0};
     std::string err;
+    // measurement hook: events around fine-level correction launches, per group
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_group;
+    size_t ev_used = 0;
     cudaGraphExec_t gexec = nullptr;
     double* g_u = nullptr;
     long long g_launches = 0, g_sweeps[2] = {0, 0};   // per replay of the captured step
@@ -419,7 +424,21 @@ void run_sweep(sisdc_ens_s* c, EnsGroup& g, int which, int mode, const double* G
     a.rtol = c->opts.cg_rtol;
     a.maxit = c->opts.cg_maxit;
     a.inst_iters = which == 1 ? c->iters_view[g.index] : nullptr;   // fine-level counters per instance
+    const bool timed = c->timing && which == 1 && mode == SW_CORRECT;
+    if (timed) {
+        while (c->ev.size() < c->ev_used + 2) {
+            cudaEvent_t e;
+            check(c, cudaEventCreate(&e), "timing event");
+            c->ev.push_back(e);
+        }
+        check(c, cudaEventRecord(c->ev[c->ev_used], c->stream), "timing event");
+    }
     check(c, launch_ens_sweep(a, L.nq, L.mix ? 1 : 0, L.grid, c->stream), "ensemble sweep kernel");
+    if (timed) {
+        check(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream), "timing event");
+        c->ev_used += 2;
+        c->ev_group.push_back(g.index);
+    }
     c->launches++;
     if (mode != SW_REFRESH) c->sweeps[which] += mode == SW_PREDICT ? 1 : nsweeps;
 }
@@ -536,6 +555,8 @@ void enqueue_step(sisdc_ens_s* c, double* u) {
 
 void destroy_all(sisdc_ens_s* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
     for (EnsGroup* g : c->groups) {
         release_level(g->lv[0]);
         release_level(g->lv[1]);
@@ -666,6 +687,57 @@ sisdc_status sisdc_ens_layout(sisdc_ens c, long long* offsets, long long* total)
     if (offsets)
         for (size_t k = 0; k < c->inst.size(); ++k) offsets[k] = c->offset[k];
     if (total) *total = c->total;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_ens_coords(sisdc_ens c, double* hx, double* hy) {
+    if (!c || !hx) return SISDC_E_ARG;
+    for (size_t k = 0; k < c->inst.size(); ++k) {
+        const EnsGroup* g = c->groups[c->group_of[k]];
+        const EnsLevel& F = g->lv[1];
+        const sisdc_ens_instance& d = c->inst[k];
+        const double h0 = 1.0 / d.nel[0], h1 = 1.0 / d.nel[1];
+        long long id = c->offset[k];
+        for (int ey = 0; ey < d.nel[1]; ++ey)
+            for (int ex = 0; ex < d.nel[0]; ++ex)
+                for (int j = 0; j < F.nq; ++j)
+                    for (int i = 0; i < F.nq; ++i, ++id) {
+                        hx[id] = (ex + (F.tab.gll[i] + 1.0) / 2.0) * h0;
+                        if (hy) hy[id] = (ey + (F.tab.gll[j] + 1.0) / 2.0) * h1;
+                    }
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_ens_set_kernel_timing(sisdc_ens c, int enable) {
+    if (!c) return SISDC_E_ARG;
+    if (enable && c->opts.use_graph) return fail(c, SISDC_E_STATE, "kernel timing needs eager mode (use_graph = 0)");
+    c->timing = enable != 0;
+    c->ev_used = 0;
+    c->ev_group.clear();
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_ens_get_kernel_timing(sisdc_ens c, double* ms, long long* launches) {
+    if (!c) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+    const size_t ng = c->groups.size();
+    std::vector<double> tot(ng, 0.0);
+    std::vector<long long> cnt(ng, 0);
+    for (size_t k = 0; k < c->ev_used / 2; ++k) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]);
+        if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, std::string("elapsed: ") + cudaGetErrorString(e));
+        tot[c->ev_group[k]] += t;
+        cnt[c->ev_group[k]] += 1;
+    }
+    for (size_t gi = 0; gi < ng; ++gi) {
+        if (ms) ms[gi] = tot[gi];
+        if (launches) launches[gi] = cnt[gi];
+    }
+    c->ev_used = 0;
+    c->ev_group.clear();
     return SISDC_OK;
 }
 

@@ -11,6 +11,7 @@
 // passes only the right-hand side and the solution.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "../../include/sisdc.h"
@@ -26,7 +27,9 @@ constexpr size_t kScratchDoubles = (size_t)SISDC_NOALLOC_SCRATCH_BYTES / sizeof(
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
-double* s_scratch[kMaxDevices] = {nullptr};   // device address of the array, per device
+// device address of the array, per device; several host threads may look it
+// up at once (they store the same value)
+std::atomic<double*> s_scratch[kMaxDevices];
 
 // Header layout (in doubles) at the start of the scratch array.
 constexpr size_t H_BAR = 0;       // 2 unsigned (barrier arrival counter, exit counter)
@@ -74,16 +77,19 @@ extern "C" sisdc_status sisdc_solve_noalloc(const sisdc_level_desc* d, int ncomp
         return SISDC_E_CUDA;
     }
     // once per device, with that device current: the array's device address
-    if (!s_scratch[dev]) {
+    // (under lazy module loading this first lookup also loads the module and
+    // commits the array on the device)
+    double* base = s_scratch[dev].load(std::memory_order_acquire);
+    if (!base) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             set_msg(h_err, h_err_len, "cudaGetSymbolAddress of the scratch array failed");
             return SISDC_E_CUDA;
         }
-        s_scratch[dev] = static_cast<double*>(p);
+        base = static_cast<double*>(p);
+        s_scratch[dev].store(base, std::memory_order_release);
     }
-    double* base = s_scratch[dev];
 
     // geometry and launch shape (no device memory needed for the query)
     const double hx = (d->hi[0] - d->lo[0]) / d->nel[0];

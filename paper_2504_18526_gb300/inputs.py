@@ -46,6 +46,15 @@ WORKLOADS = {
                 dict(nel=(64, 64), P=7, M=5)],
         nodes="lobatto", cfl=0.5, nsteps=200, ncycles=3, start="fmg1",
         vortex_beta=5.0, mach=0.5, angle_deg=45.0),
+    # the same Euler vortex on 256x256 elements (4.2 M nodes x 4 variables): a
+    # size whose level arrays do not fit in L2
+    "euler256": dict(
+        id=6, pde="euler", dim=2, ncomp=4, gamma=1.4,
+        lo=(-10.0, -10.0), hi=(10.0, 10.0),
+        levels=[dict(nel=(256, 256), P=3, M=2), dict(nel=(256, 256), P=5, M=3),
+                dict(nel=(256, 256), P=7, M=5)],
+        nodes="lobatto", cfl=0.5, nsteps=20, ncycles=3, start="fmg1",
+        vortex_beta=5.0, mach=0.5, angle_deg=45.0),
     # 2D compressible Navier-Stokes doubly periodic shear layer, 128x128 elements, P = 5
     "ns_shear": dict(
         id=4, pde="ns", dim=2, ncomp=4, gamma=1.4, Re=2500.0, Pr=0.72, mach=0.3,
@@ -165,7 +174,7 @@ def initial_state(name, X, Y, seed_extra=0):
         return convdiff1d_exact(X, 0.0, w["nu"], w["adv"][0])
     if name == "burgers2d":
         return burgers2d_initial(X, Y, seed_extra, w["fourier_K"], w["fourier_amp"])
-    if name == "euler_vortex":
+    if name in ("euler_vortex", "euler256"):
         return isentropic_vortex(X, Y, 0.0, w["gamma"], w["vortex_beta"], w["mach"],
                                  w["angle_deg"], w["lo"], w["hi"])
     if name == "ns_shear":

@@ -144,6 +144,9 @@ def load():
         "sisdc_ens_get_stats": (c_int, [c_void_p, P(sisdc_stats), c_void_p]),
         "sisdc_ens_reset_stats": (c_int, [c_void_p]),
         "sisdc_ens_last_error": (ctypes.c_char_p, [c_void_p]),
+        "sisdc_ens_coords": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "sisdc_ens_set_kernel_timing": (c_int, [c_void_p, c_int]),
+        "sisdc_ens_get_kernel_timing": (c_int, [c_void_p, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -482,6 +485,24 @@ def sisdc_ens_layout(ens, n):
     tot = c_ll()
     _echeck(load().sisdc_ens_layout(ens, off.ctypes.data, ctypes.byref(tot)), ens)
     return off, tot.value
+
+
+def sisdc_ens_coords(ens, hx, hy=None):
+    _echeck(load().sisdc_ens_coords(ens, _hptr(hx), _hptr(hy) if hy is not None else None), ens)
+
+
+def sisdc_ens_set_kernel_timing(ens, enable):
+    _echeck(load().sisdc_ens_set_kernel_timing(ens, 1 if enable else 0), ens)
+
+
+def sisdc_ens_get_kernel_timing(ens):
+    """Per group (increasing degree): summed fine correction-launch ms and launch counts."""
+    import numpy as np
+    ng = sisdc_ens_num_groups(ens)
+    ms = np.zeros(ng)
+    cnt = np.zeros(ng, dtype=np.int64)
+    _echeck(load().sisdc_ens_get_kernel_timing(ens, ms.ctypes.data, cnt.ctypes.data), ens)
+    return ms, cnt
 
 
 def sisdc_ens_step(ens, u, nsteps=1):

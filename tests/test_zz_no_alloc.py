@@ -49,6 +49,40 @@ def test_noalloc_solve_matches_allocating_solve():
     ctx.close()
 
 
+def test_noalloc_allocates_nothing_after_first_call():
+    """After a first call on the device (which may commit the static array),
+    a further call leaves the device's free memory and PyTorch's reserved
+    memory unchanged; a 1D single-component level (the 1D convection-
+    diffusion fine level: 16 elements of degree 4) matches sisdc_solve too."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import math
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    w1 = dict(pde="convdiff", dim=1, ncomp=1, adv=(1.0, 0.0), nu=0.01, lo=(0.0, 0.0), hi=(2 * math.pi, 0.0),
+              nodes="lobatto", levels=[dict(nel=(16, 1), P=4, M=5)])
+    ctx = S.Context(w1, cg_rtol=1e-14, cg_maxit=10000)
+    desc = S.make_level_desc(w1, w1["levels"][0])
+    nc, n, _ = ctx.info(0)
+    rng = np.random.default_rng(7)
+    rhs = torch.from_numpy(rng.standard_normal(nc * n)).to(dev)
+    x0 = torch.from_numpy(rng.standard_normal(nc * n)).to(dev)
+    x_ref, xa, xb = x0.clone(), x0.clone(), x0.clone()
+    S.sisdc_solve(ctx.levels[0], 0.03, rhs, x_ref)
+    S.sisdc_sync(ctx.ctx)
+    S.sisdc_solve_noalloc(desc, nc, 0.03, rhs, xa, 1e-14, 10000)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    res0 = torch.cuda.memory_reserved(dev)
+    S.sisdc_solve_noalloc(desc, nc, 0.03, rhs, xb, 1e-14, 10000)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0 and torch.cuda.memory_reserved(dev) == res0
+    for x in (xa, xb):
+        assert _rel(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-12
+    ctx.close()
+
+
 def test_noalloc_rejects_oversized_problem():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
