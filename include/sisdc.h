@@ -220,6 +220,19 @@ sisdc_status sisdc_apply_f(sisdc_level lv, const double* d_u, double* d_out);
  * h_iters is not NULL. */
 sisdc_status sisdc_solve(sisdc_level lv, double c, const double* d_rhs, double* d_x, int* h_iters);
 
+/* The same solve with the element-wise fast-diagonalisation preconditioner
+ * in place of Jacobi (the paper runs its implicit solves with PCG or a fast
+ * diagonalisation solver, Sec. 8 "Runtime analysis"; the element-wise form
+ * is this library's reading).  On the uniform periodic mesh the SIPG
+ * stiffness is a Kronecker sum of 1D line operators; dropping the coupling
+ * to neighbour elements leaves per element the block
+ * B_e = M_y(x)M_x + c (M_y(x)K_x + K_y(x)M_x), inverted exactly through the
+ * generalised eigenvectors of (K_x, M_x) and (K_y, M_y): four contractions
+ * of length P+1 per node per CG iteration.  Stopping rule as sisdc_solve
+ * with D^-1 replaced by B^-1.  Arguments, layout and errors as sisdc_solve;
+ * uses the level's work arrays. */
+sisdc_status sisdc_solve_fds(sisdc_level lv, double c, const double* d_rhs, double* d_x, int* h_iters);
+
 /* No-allocation solve (the paper has no counterpart; this is a service for
  * callers that cannot allocate device memory when they need a solve -- for
  * instance code that must stay inside a fixed memory budget owned by another

@@ -47,6 +47,8 @@ struct Geo {
     const double* w;              // [nq] GLL weights (device)
     const double* dline_x;        // [nq] diagonal of the 1D SIPG line operator (x)
     const double* dline_y;        // [nq] (y)
+    const double* fds;            // element-wise fast diagonalisation: S_x [nq*nq], lam_x [nq],
+                                  // S_y, lam_y (nullable: Jacobi only)
     // host-computed factors (no divisions in the kernels' inner loops)
     double sx, sy;                // 2/h_x, 2/h_y
     double ihx, ihy;              // 1/h_x, 1/h_y

@@ -40,7 +40,10 @@ struct PCGArgs {
     double rtol;
     int maxit;
     int* iters_out;       // iteration count of this solve (nullable)
+    int prec;             // PCG_JACOBI, or PCG_FDS (element-wise fast diagonalisation, g.fds)
+    double* z;            // PCG_FDS: preconditioned residual B^-1 r
 };
+enum PcgPrec : int { PCG_JACOBI = 0, PCG_FDS = 1 };
 
 cudaError_t launch_traces(const Geo& g, const double* u, double* tr, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);

@@ -149,6 +149,50 @@ __device__ __forceinline__ void node_mass_diag(const Geo& g, const double* sw, c
     }
 }
 
+// Element-wise fast diagonalisation (the separable preconditioner of the
+// implicit SIPG system): z = B_e^{-1} r for every element of the tile, with
+// B_e^{-1} = (S_y (x) S_x) diag(f) (S_y (x) S_x)^T, f = 1 / (1 + c (lam_y[j] +
+// lam_x[i])) the thread's own factor.  sr holds r on entry (all threads of
+// the block call this; both buffers are clobbered); returns z at the
+// thread's node.
+template <int NQ, int DIM>
+__device__ __forceinline__ double tile_fds(double* sr, double* st, const double* sSx, const double* sSy,
+                                           double f, int le, int i, int j, bool act) {
+    using S = Sh<NQ, DIM>;
+    const int base = le * S::Q;
+    __syncthreads();
+    if (act) {                                    // S_x^T along x
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) s += sSx[a * NQ + i] * sr[base + j * NQ + a];
+        st[base + j * NQ + i] = DIM == 1 ? s * f : s;
+    }
+    __syncthreads();
+    if (DIM == 2) {
+        if (act) {                                // S_y^T along y, scale
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < NQ; ++b) s += sSy[b * NQ + j] * st[base + b * NQ + i];
+            sr[base + j * NQ + i] = s * f;
+        }
+        __syncthreads();
+        if (act) {                                // S_y along y
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < NQ; ++b) s += sSy[j * NQ + b] * sr[base + b * NQ + i];
+            st[base + j * NQ + i] = s;
+        }
+        __syncthreads();
+    }
+    double z = 0.0;
+    if (act) {                                    // S_x along x
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) z += sSx[i * NQ + a] * st[base + j * NQ + a];
+    }
+    __syncthreads();
+    return z;
+}
+
 // ---------------------------------------------------------------------------
 // Standalone traces / apply kernels
 // ---------------------------------------------------------------------------
@@ -242,9 +286,17 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
     double* su = scoef + MAXTERMS;
     const int epb = blockDim.x / S::Q;
     double* sf = su + epb * S::Q;
+    double* sSx = sf + epb * S::TRS;     // fast-diagonalisation tables and buffer
+    double* slx = sSx + NQ * NQ;
+    double* sSy = slx + NQ;
+    double* sly = sSy + NQ * NQ;
+    double* st = sly + NQ;
     const Geo& g = a.g;
+    const bool fds = a.prec == PCG_FDS;
     load_tables<NQ>(g, sD, sK, sw, sdx, sdy);
     for (int t = threadIdx.x; t < MAXTERMS; t += blockDim.x) scoef[t] = t < a.nterms ? coef_value(a.coef[t]) : 0.0;
+    if (fds)
+        for (int t = threadIdx.x; t < 2 * (NQ * NQ + NQ); t += blockDim.x) sSx[t] = g.fds[t];
     __syncthreads();
 
     const long long nec = (long long)g.ncomp * g.nel;
@@ -256,6 +308,7 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
     double mass, diagA;
     node_mass_diag<NQ, DIM>(g, sw, sdx, sdy, i, j, mass, diagA);
     const double dinv = 1.0 / (mass + c * diagA);
+    const double ffds = fds ? 1.0 / (1.0 + c * (slx[i] + (DIM == 2 ? sly[j] : 0.0))) : 0.0;
     double* part = a.part;
 
     // phase 0: r = M b, traces of x, partial b^T D^-1 b
@@ -265,17 +318,23 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
         const int nle = (int)min((long long)epb, nec - ec0);
         const bool act = le < nle;
         const long long idx = (ec0 + le) * S::Q + node;
+        double mb = 0.0;
         if (act) {
             double b = 0.0;
             for (int q = 0; q < a.nterms; ++q) b += scoef[q] * a.in[q][idx];
-            const double mb = mass * b;
+            mb = mass * b;
             a.r[idx] = mb;
-            acc += mb * mb * dinv;
+            if (!fds) acc += mb * mb * dinv;
             su[le * S::Q + node] = a.x[idx];
         }
         __syncthreads();
         tile_traces<NQ, DIM>(su, nle, ec0, g, sD, a.trx);
         __syncthreads();
+        if (fds) {                 // b^T B^-1 b
+            if (act) su[le * S::Q + node] = mb;
+            const double z = tile_fds<NQ, DIM>(su, st, sSx, sSy, ffds, le, i, j, act);
+            if (act) acc += mb * z;
+        }
     }
     {
         const double bs = block_sum(acc, scratch);
@@ -293,15 +352,26 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
         if (act) su[le * S::Q + node] = a.x[idx];
         tile_faces<NQ, DIM>(a.trx, ec0, nle, g, sf);
         __syncthreads();
-        double z = 0.0;
+        double z = 0.0, rr = 0.0;
         if (act) {
             const double xv = su[le * S::Q + node];
             const double Ax = node_A<NQ, DIM>(su + le * S::Q, sf + le * S::NF * 2 * NQ, i, j, g, sD, sK, sw);
-            const double rr = a.r[idx] - (mass * xv + c * Ax);
+            rr = a.r[idx] - (mass * xv + c * Ax);
             a.r[idx] = rr;
-            z = rr * dinv;
-            a.p[idx] = z;
-            acc += rr * z;
+            if (!fds) {
+                z = rr * dinv;
+                a.p[idx] = z;
+                acc += rr * z;
+            }
+        }
+        if (fds) {
+            __syncthreads();       // every thread has read x from su
+            if (act) su[le * S::Q + node] = rr;
+            z = tile_fds<NQ, DIM>(su, st, sSx, sSy, ffds, le, i, j, act);
+            if (act) {
+                a.p[idx] = z;
+                acc += rr * z;
+            }
         }
         __syncthreads();
         if (act) su[le * S::Q + node] = z;
@@ -352,12 +422,22 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
         for (long long t = blockIdx.x; t < ntiles; t += G) {
             const long long ec0 = t * epb;
             const int nle = (int)min((long long)epb, nec - ec0);
-            if (le < nle) {
-                const long long idx = (ec0 + le) * S::Q + node;
+            const bool act = le < nle;
+            const long long idx = (ec0 + le) * S::Q + node;
+            double rr = 0.0;
+            if (act) {
                 a.x[idx] += alpha * a.p[idx];
-                const double rr = a.r[idx] - alpha * a.Ap[idx];
+                rr = a.r[idx] - alpha * a.Ap[idx];
                 a.r[idx] = rr;
-                acc += rr * (rr * dinv);
+                if (!fds) acc += rr * (rr * dinv);
+            }
+            if (fds) {             // z = B^-1 r, kept for the next search direction
+                if (act) su[le * S::Q + node] = rr;
+                const double z = tile_fds<NQ, DIM>(su, st, sSx, sSy, ffds, le, i, j, act);
+                if (act) {
+                    a.z[idx] = z;
+                    acc += rr * z;
+                }
             }
         }
         {
@@ -379,7 +459,7 @@ __device__ __forceinline__ void pcg_body(const PCGArgs& a) {
             const bool act = le < nle;
             const long long idx = (ec0 + le) * S::Q + node;
             if (act) {
-                const double pn = a.r[idx] * dinv + beta * a.p[idx];
+                const double pn = (fds ? a.z[idx] : a.r[idx] * dinv) + beta * a.p[idx];
                 a.p[idx] = pn;
                 su[le * S::Q + node] = pn;
             }
@@ -451,7 +531,8 @@ cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
 template <int NQ, int DIM>
 static size_t pcg_smem(int epb) {
     using S = Sh<NQ, DIM>;
-    return (2 * NQ * NQ + 3 * NQ + 32 + MAXTERMS + (size_t)epb * S::Q + (size_t)epb * S::TRS) * sizeof(double);
+    return (2 * NQ * NQ + 3 * NQ + 32 + MAXTERMS + (size_t)epb * S::Q + (size_t)epb * S::TRS +
+            2 * (NQ * NQ + NQ) + (size_t)epb * S::Q) * sizeof(double);
 }
 
 template <int NQ, int DIM>

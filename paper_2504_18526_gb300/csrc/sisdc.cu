@@ -181,9 +181,11 @@ struct Terms {
     }
 };
 
-void k_pcg(sisdc_level_s* lv, double* x, const Terms& t, Coef cimp) {
+void k_pcg(sisdc_level_s* lv, double* x, const Terms& t, Coef cimp, int prec = PCG_JACOBI) {
     sisdc_ctx_s* c = lv->ctx;
     PCGArgs a{};
+    a.prec = prec;
+    a.z = lv->cg_rf;
     a.g = lv->geo;
     a.x = x;
     a.r = lv->cg_r;
@@ -645,6 +647,14 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         htab[2 * nq * nq + nq + i] = dx;
         htab[2 * nq * nq + 2 * nq + i] = dy;
     }
+    // element-wise fast-diagonalisation tables (x, then y): S_x, lam_x, S_y, lam_y
+    const size_t off_fds = htab.size();
+    htab.resize(off_fds + 2 * (nq * nq + nq));
+    if (!fds_tables(d->P, hx, htab.data() + off_fds, htab.data() + off_fds + nq * nq) ||
+        !fds_tables(d->P, hy, htab.data() + off_fds + nq * nq + nq, htab.data() + off_fds + 2 * nq * nq + nq)) {
+        delete lv;
+        return fail(c, SISDC_E_ARG, "table construction failed");
+    }
     // transfers to the coarser level
     std::vector<double> ttab;
     size_t off_Ix = 0, off_Px = 0, off_Rx = 0, off_It = 0, off_Pt = 0, off_Rt = 0, off_one = 0;
@@ -735,6 +745,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     g.N = lv->N; g.hx = hx; g.hy = hy; g.taux = taux; g.tauy = tauy;
     g.D = lv->d_tab; g.K = lv->d_tab + nq * nq; g.w = lv->d_tab + 2 * nq * nq;
     g.dline_x = g.w + nq; g.dline_y = g.w + 2 * nq;
+    g.fds = lv->d_tab + off_fds;
     g.sx = 2.0 / hx; g.sy = 2.0 / hy; g.ihx = 1.0 / hx; g.ihy = 1.0 / hy;
     g.liftLx = g.sx / lv->tab.w[0]; g.liftRx = g.sx / lv->tab.w[nq - 1];
     g.liftLy = g.sy / lv->tab.w[0]; g.liftRy = g.sy / lv->tab.w[nq - 1];
@@ -818,8 +829,7 @@ sisdc_status sisdc_apply_f(sisdc_level lv, const double* u, double* out) {
     return SISDC_OK;
 }
 
-sisdc_status sisdc_solve(sisdc_level lv, double cval, const double* rhs, double* x, int* iters) {
-    if (!lv || !rhs || !x || !(cval >= 0.0)) return SISDC_E_ARG;
+static sisdc_status solve_prec(sisdc_level lv, double cval, const double* rhs, double* x, int* iters, int prec) {
     sisdc_ctx_s* c = lv->ctx;
     try {
         long long before = 0;
@@ -829,7 +839,7 @@ sisdc_status sisdc_solve(sisdc_level lv, double cval, const double* rhs, double*
         }
         Terms t;
         t.add(rhs, 1.0);
-        k_pcg(lv, x, t, Coef{cval, 0.0, nullptr});
+        k_pcg(lv, x, t, Coef{cval, 0.0, nullptr}, prec);
         if (iters) {
             long long after = 0;
             check(c, cudaStreamSynchronize(c->stream), "sync");
@@ -840,6 +850,16 @@ sisdc_status sisdc_solve(sisdc_level lv, double cval, const double* rhs, double*
         return f.st;
     }
     return SISDC_OK;
+}
+
+sisdc_status sisdc_solve(sisdc_level lv, double cval, const double* rhs, double* x, int* iters) {
+    if (!lv || !rhs || !x || !(cval >= 0.0)) return SISDC_E_ARG;
+    return solve_prec(lv, cval, rhs, x, iters, PCG_JACOBI);
+}
+
+sisdc_status sisdc_solve_fds(sisdc_level lv, double cval, const double* rhs, double* x, int* iters) {
+    if (!lv || !rhs || !x || !(cval >= 0.0)) return SISDC_E_ARG;
+    return solve_prec(lv, cval, rhs, x, iters, PCG_FDS);
 }
 
 sisdc_status sisdc_predict(sisdc_level lv, const double* u0, double* U, double dt) {

@@ -285,3 +285,96 @@ bool gll_tables_fixed(int P, double* xo, double* wo, double* Do, double* Ko) {
 }
 
 }  // namespace sisdc
+
+namespace sisdc {
+
+// Element-wise fast diagonalisation of the 1D SIPG line operator of element
+// width h (the implicit systems' separable preconditioner).  The element's
+// diagonal block of the line operator,
+//   Kt = (2/h) D^T W D - (1/h) (e_P d_P^T + d_P e_P^T) + (1/h) (e_0 d_0^T + d_0 e_0^T)
+//        + tau (e_0 e_0^T + e_P e_P^T),   d_0, d_P = first / last row of D,
+//   tau = 2 (P+1)^2 / h,
+// and the GLL mass Mh = (h/2) W give the generalised eigenpairs
+// Kt s_i = lam_i Mh s_i with s_i^T Mh s_i = 1, found from the symmetric
+// matrix Mh^{-1/2} Kt Mh^{-1/2} by cyclic Jacobi rotations (Golub & Van Loan,
+// the symmetric Jacobi eigenvalue method), in long double.  Output:
+// S[a * (P+1) + i] = component a of s_i, lam[i]; eigenvalues ascending.
+bool fds_tables(int P, double h, double* S, double* lam) {
+    if (P < 1 || P > 15 || !(h > 0.0)) return false;
+    const int nq = P + 1;
+    std::vector<ld> x, w;
+    gll_ld(P, &x, &w);
+    std::vector<ld> bl(nq, 1.0L), Dl(nq * nq, 0.0L);
+    for (int j = 0; j < nq; ++j)
+        for (int k = 0; k < nq; ++k)
+            if (k != j) bl[j] /= (x[j] - x[k]);
+    for (int i = 0; i < nq; ++i) {
+        ld diag = 0.0L;
+        for (int j = 0; j < nq; ++j) {
+            if (i == j) continue;
+            Dl[i * nq + j] = (bl[j] / bl[i]) / (x[i] - x[j]);
+            diag -= Dl[i * nq + j];
+        }
+        Dl[i * nq + i] = diag;
+    }
+    const ld hl = h, tau = 2.0L * nq * nq / hl;
+    std::vector<ld> C(nq * nq), V(nq * nq, 0.0L), ms(nq);
+    for (int i = 0; i < nq; ++i) ms[i] = 1.0L / sqrtl(0.5L * hl * w[i]);
+    for (int i = 0; i < nq; ++i)
+        for (int k = 0; k < nq; ++k) {
+            ld s = 0.0L;
+            for (int q = 0; q < nq; ++q) s += Dl[q * nq + i] * w[q] * Dl[q * nq + k];
+            s *= 2.0L / hl;
+            if (k == P) s -= Dl[P * nq + i] / hl;
+            if (i == P) s -= Dl[P * nq + k] / hl;
+            if (k == 0) s += Dl[i] / hl;
+            if (i == 0) s += Dl[k] / hl;
+            if (i == k && (i == 0 || i == P)) s += tau;
+            C[i * nq + k] = ms[i] * s * ms[k];
+        }
+    for (int i = 0; i < nq; ++i) V[i * nq + i] = 1.0L;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        ld off = 0.0L, tot = 0.0L;
+        for (int p = 0; p < nq; ++p)
+            for (int q = 0; q < nq; ++q) {
+                tot += C[p * nq + q] * C[p * nq + q];
+                if (p != q) off += C[p * nq + q] * C[p * nq + q];
+            }
+        if (off <= 1e-36L * tot) break;
+        for (int p = 0; p < nq - 1; ++p)
+            for (int q = p + 1; q < nq; ++q) {
+                const ld apq = C[p * nq + q];
+                if (apq == 0.0L) continue;
+                const ld theta = (C[q * nq + q] - C[p * nq + p]) / (2.0L * apq);
+                const ld t = (theta >= 0.0L ? 1.0L : -1.0L) / (fabsl(theta) + sqrtl(theta * theta + 1.0L));
+                const ld cs = 1.0L / sqrtl(t * t + 1.0L), sn = t * cs;
+                for (int k = 0; k < nq; ++k) {          // columns p, q
+                    const ld ckp = C[k * nq + p], ckq = C[k * nq + q];
+                    C[k * nq + p] = cs * ckp - sn * ckq;
+                    C[k * nq + q] = sn * ckp + cs * ckq;
+                }
+                for (int k = 0; k < nq; ++k) {          // rows p, q
+                    const ld cpk = C[p * nq + k], cqk = C[q * nq + k];
+                    C[p * nq + k] = cs * cpk - sn * cqk;
+                    C[q * nq + k] = sn * cpk + cs * cqk;
+                }
+                for (int k = 0; k < nq; ++k) {
+                    const ld vkp = V[k * nq + p], vkq = V[k * nq + q];
+                    V[k * nq + p] = cs * vkp - sn * vkq;
+                    V[k * nq + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    std::vector<int> order(nq);
+    for (int i = 0; i < nq; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return C[a * nq + a] < C[b * nq + b]; });
+    for (int i = 0; i < nq; ++i) {
+        const int o = order[i];
+        lam[i] = (double)C[o * nq + o];
+        for (int a = 0; a < nq; ++a) S[a * nq + i] = (double)(ms[a] * V[a * nq + o]);
+    }
+    return true;
+}
+
+}  // namespace sisdc
+

@@ -15,6 +15,11 @@ bool build_level_tables(int P, int M, int lobatto, LevelTables* t);
 // E[p][j] = l_j(pts[p]) for the Lagrange basis on `nodes`.
 std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& pts);
 
+// Element-wise fast diagonalisation of the 1D SIPG line operator of element
+// width h: S[a * (P+1) + i] = component a of the i-th generalised eigenvector
+// of (element block, GLL mass), M-orthonormal; lam[i] ascending.
+bool fds_tables(int P, double h, double* S, double* lam);
+
 // Per-direction L2 projection from degree Pf to Pc under the fine GLL
 // quadrature: (I^T W_f I)^{-1} I^T W_f, row-major (Pc+1) x (Pf+1).
 std::vector<double> l2_projection_matrix(int Pf, int Pc);

@@ -101,6 +101,7 @@ def load():
         "sisdc_apply_lap": (c_int, [c_void_p, c_void_p, c_void_p]),
         "sisdc_apply_f": (c_int, [c_void_p, c_void_p, c_void_p]),
         "sisdc_solve": (c_int, [c_void_p, c_double, c_void_p, c_void_p, P(c_int)]),
+        "sisdc_solve_fds": (c_int, [c_void_p, c_double, c_void_p, c_void_p, P(c_int)]),
         "sisdc_predict": (c_int, [c_void_p, c_void_p, c_void_p, c_double]),
         "sisdc_sweep": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int]),
         "sisdc_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_void_p]),
@@ -269,6 +270,13 @@ def sisdc_apply_f(lv, u, f):
 def sisdc_solve(lv, c, rhs, x, want_iters=False):
     it = c_int()
     _check(load().sisdc_solve(lv, c, _ptr(rhs), _ptr(x), ctypes.byref(it) if want_iters else None),
+           lv=lv)
+    return it.value if want_iters else None
+
+
+def sisdc_solve_fds(lv, c, rhs, x, want_iters=False):
+    it = c_int()
+    _check(load().sisdc_solve_fds(lv, c, _ptr(rhs), _ptr(x), ctypes.byref(it) if want_iters else None),
            lv=lv)
     return it.value if want_iters else None
 

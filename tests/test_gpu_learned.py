@@ -133,7 +133,7 @@ def test_learned_initial_guess_saves_iterations(dev, name):
     l1_tr, l1_te = mean_loss(train), mean_loss(test)
     print("loss train %.3e -> %.3e, held-out %.3e -> %.3e" % (l0_tr, l1_tr, l0_te, l1_te))
     assert l1_tr < 0.5 * l0_tr and l1_te < 0.5 * l0_te
-    plain = learned = flexible = 0
+    plain = learned = flexible = fds = 0
     for k in test:
         rhs = lr_[k].contiguous()                 # (I - cL) x = r0 (nodal), x* = logged correction
         x = torch.zeros_like(rhs)
@@ -147,9 +147,13 @@ def test_learned_initial_guess_saves_iterations(dev, name):
         flexible += S.sisdc_solve_learned(lv, m, float(cs[k]), rhs, x3, 2)
         torch.cuda.synchronize()
         assert float(torch.linalg.vector_norm(x3 - x) / torch.linalg.vector_norm(x)) < 1e-8
+        x4 = torch.zeros_like(rhs)                # the non-learned separable preconditioner
+        fds += S.sisdc_solve_fds(lv, float(cs[k]), rhs, x4, want_iters=True)
+        torch.cuda.synchronize()
+        assert float(torch.linalg.vector_norm(x4 - x) / torch.linalg.vector_norm(x)) < 1e-8
     S.sisdc_sync(ctx.ctx)
-    print("%s held-out solves %d: plain PCG %d iterations, learned guess + PCG %d, learned flexible CG %d"
-          % (name, len(test), plain, learned, flexible))
+    print("%s held-out solves %d: plain PCG %d iterations, learned guess + PCG %d, learned flexible CG %d, "
+          "element-wise FDS-PCG %d" % (name, len(test), plain, learned, flexible, fds))
     assert learned < plain
     S.sisdc_mlp_destroy(m)
     S.sisdc_set_solve_log(ctx.ctx, fine)
