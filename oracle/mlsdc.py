@@ -2,8 +2,10 @@
 (FP64, test infrastructure only).
 
 * Transfers (Sec. 4.2, Sec. 6.2): space-time tensor products of the time
-  transfers I_t, P_t, R_t = I_t^T and per-direction spatial p-coarsening
-  transfers I_x, P_x (embedded interpolation, or the L2 projection) and R_x.
+  transfers I_t, P_t, R_t = I_t^T and per-direction spatial transfers I_x,
+  P_x (embedded interpolation, or the L2 projection) and R_x, for
+  p-coarsening on the same elements and for 2:1 h-coarsening (two fine
+  elements per coarse element and direction, tables.h_transfers).
 * FAS right-hand side (Sec. 4.1, eq. ml-cm:incremental:fas-mg:rhs):
   g_l = F_l(P u_{l+1}) + R (g_{l+1} - F_{l+1}(u_{l+1})), g_L = 0.
 * V-cycle: Algorithm 2.  Reading: after the solution restriction
@@ -20,7 +22,7 @@
 import numpy as np
 
 from .sdc import corrector, corrector_0n, predictor, Fnn, F0n
-from .tables import time_transfers, space_transfers, l2_projection
+from .tables import time_transfers, space_transfers, l2_projection, h_transfers
 
 
 def _apply_space(mat, u, dim):
@@ -29,6 +31,22 @@ def _apply_space(mat, u, dim):
     if dim == 2:
         out = np.einsum('bj,...ja->...ba', mat, out)
     return out
+
+
+def _apply_dir(mats, u, ax_e, ax_n, coarse_to_fine):
+    """One direction of a transfer between element grids of ratio r =
+    len(mats) (1: same elements, 2: 2:1 h-coarsening).  Coarse to fine:
+    fine element e takes mats[e % r] applied to coarse element e // r.  Fine
+    to coarse: coarse element e sums mats[c] applied to fine element r e + c."""
+    r = len(mats)
+    a = np.moveaxis(u, (ax_e, ax_n), (-2, -1))
+    if coarse_to_fine:
+        out = np.zeros(a.shape[:-2] + (a.shape[-2] * r, mats[0].shape[0]))
+        for c in range(r):
+            out[..., c::r, :] = np.einsum('ba,...ea->...eb', mats[c], a)
+    else:
+        out = sum(np.einsum('ab,...eb->...ea', mats[c], a[..., c::r, :]) for c in range(r))
+    return np.moveaxis(out, (-2, -1), (ax_e, ax_n))
 
 
 class Transfer:
@@ -44,10 +62,27 @@ class Transfer:
             self.Ix, self.Px, self.Rx = space_transfers(fs.P, cs.P)
             if projection == "l2":           # solution projection in space: L2 instead of embedded
                 self.Px = l2_projection(fs.P, cs.P)
+            # element ratio per direction: 1 (p-coarsening only) or 2 (2:1 h-coarsening)
+            self.ratio = (fs.nex // cs.nex, fs.ney // cs.ney)
+            for r, nf, nc in zip(self.ratio, (fs.nex, fs.ney), (cs.nex, cs.ney)):
+                if r not in (1, 2) or nf != r * nc:
+                    raise ValueError("levels must have equal or 2:1 element grids")
+            if self.ratio != (1, 1):
+                Ih, Ph, Rh = h_transfers(fs.P, cs.P, projection)
+                self.hmats = {}
+                for d, r in enumerate(self.ratio):
+                    self.hmats[d] = ({'I': Ih, 'P': Ph, 'R': Rh} if r == 2 else
+                                     {'I': [self.Ix], 'P': [self.Px], 'R': [self.Rx]})
 
     def _space(self, which, u):
         if not self.dg:
             return u
+        if self.ratio != (1, 1):             # u[comp, ey, ex, j, i]: x then y
+            c2f = which == 'I'
+            out = _apply_dir(self.hmats[0][which], u, 2, 4, c2f)
+            if self.dim == 2:
+                out = _apply_dir(self.hmats[1][which], out, 1, 3, c2f)
+            return out
         mat = {'I': self.Ix, 'P': self.Px, 'R': self.Rx}[which]
         return _apply_space(mat, u, self.dim)
 

@@ -192,3 +192,62 @@ def l2_projection(P_f, P_c):
     Ix = lagrange_matrix(xc, xf)
     Mc = Ix.T @ (wf[:, None] * Ix)
     return np.linalg.solve(Mc, Ix.T * wf[None, :])
+
+
+def h_transfers(P_f, P_c, projection="interp"):
+    """Per-direction transfers for 2:1 h-coarsening (Sec. 6.2: two adjacent
+    fine elements fused into one coarse element), optionally with p-coarsening.
+    Fine child c (0 = left, 1 = right) covers the half [-1, 0] or [0, 1] of
+    the coarse reference element: coarse coordinate xi = (eta - 1) / 2 or
+    (eta + 1) / 2 of the child's coordinate eta.
+
+    Returns lists over the two children:
+    I[c] ((P_f+1) x (P_c+1)): the coarse polynomial evaluated at the child's
+        GLL nodes (exact for coarse polynomials);
+    P[c] ((P_c+1) x (P_f+1)): the solution projection, as the contribution of
+        child c's nodal values to the coarse nodal values.  "interp"
+        (default): embedded interpolation after removing the jump between the
+        two children by linear blending -- each child is corrected by a linear
+        function that vanishes at its outer end so that both meet the mean of
+        their two interface values -- then each coarse node takes the value
+        of the child whose half contains it (the centre node, where both
+        agree, takes their mean).  "l2": the least-squares fit over both
+        children under the fine GLL quadrature (no blending);
+    R[c] ((P_c+1) x (P_f+1)): the residual restriction R = W_c^{-1} I^T W_f
+        with the masses of the two widths (the child is half as wide), the
+        transpose of I in the mass inner product.
+
+    Readings (the paper names the blending but not its form): linear
+    blending as above; the tensor product of these 1D maps in 2D.  Each map
+    is built here from its definition applied to unit vectors."""
+    xf, wf = gll(P_f)
+    xc, wc = gll(P_c)
+    nf, nc = P_f + 1, P_c + 1
+    I = [lagrange_matrix(xc, (xf - 1.0) / 2.0), lagrange_matrix(xc, (xf + 1.0) / 2.0)]
+    R = [(I[c].T * (0.5 * wf)[None, :]) / wc[:, None] for c in range(2)]
+
+    def blended_value(uL, uR, xi):
+        """Value at coarse coordinate xi of the blended two-child function."""
+        mean = 0.5 * (uL[-1] + uR[0])
+        if xi <= 0.0:
+            eta = 2.0 * xi + 1.0
+            base = float(lagrange_matrix(xf, np.array([eta]))[0] @ uL)
+            return base + (mean - uL[-1]) * (1.0 + eta) / 2.0
+        eta = 2.0 * xi - 1.0
+        base = float(lagrange_matrix(xf, np.array([eta]))[0] @ uR)
+        return base + (mean - uR[0]) * (1.0 - eta) / 2.0
+
+    P = [np.zeros((nc, nf)), np.zeros((nc, nf))]
+    if projection == "l2":
+        E = np.vstack(I)                                   # (2 nf) x nc
+        W = np.concatenate([0.5 * wf, 0.5 * wf])
+        Pl = np.linalg.solve(E.T @ (W[:, None] * E), E.T * W[None, :])
+        P = [Pl[:, :nf], Pl[:, nf:]]
+    else:
+        for c in range(2):
+            for b in range(nf):
+                u = [np.zeros(nf), np.zeros(nf)]
+                u[c][b] = 1.0
+                for a in range(nc):
+                    P[c][a, b] = blended_value(u[0], u[1], xc[a])
+    return I, P, R
