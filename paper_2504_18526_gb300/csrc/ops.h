@@ -151,6 +151,14 @@ struct TransferArgs {
     const double* in;     // [Mi][ncomp][nel][nqi^dim]
     double* out;          // [Mo][ncomp][nel][nqo^dim]
     int add;              // out += instead of out =
+    // 2:1 h-coarsening (rx or ry = 2; 0 or 1 = the same elements on both
+    // sides, the fields below unused): per direction the child matrices
+    // S [rx][nqo*nqi] (x) and Sy [ry][nqo*nqi] (y); c2f = coarse-to-fine
+    // (each fine element takes its child's matrix applied to its coarse
+    // element), else fine-to-coarse (each coarse element sums its children)
+    int rx, ry, c2f;
+    int nexi, neyi, nexo, neyo;
+    const double* Sy;
 };
 cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s);
 

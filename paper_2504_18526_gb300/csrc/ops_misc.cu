@@ -121,34 +121,72 @@ cudaError_t launch_fnn(const double* u0, const double* U, const double* Q, const
 }
 
 __global__ void k_transfer(const TransferArgs a) {
-    __shared__ double sS[NQMAX * NQMAX];
+    __shared__ double sS[2 * NQMAX * NQMAX];
+    __shared__ double sSy[2 * NQMAX * NQMAX];
     __shared__ double sT[MMAX * MMAX];
-    for (int t = threadIdx.x; t < a.nqo * a.nqi; t += blockDim.x) sS[t] = a.S[t];
+    const int rx = a.rx > 1 ? a.rx : 1, ry = a.ry > 1 ? a.ry : 1;
+    const bool h = rx > 1 || ry > 1;
+    const int nm = a.nqo * a.nqi;
+    for (int t = threadIdx.x; t < rx * nm; t += blockDim.x) sS[t] = a.S[t];
+    if (h)
+        for (int t = threadIdx.x; t < ry * nm; t += blockDim.x) sSy[t] = a.Sy[t];
     for (int t = threadIdx.x; t < a.Mo * a.Mi; t += blockDim.x) sT[t] = a.Tt[t];
     __syncthreads();
     const int qi = a.dim == 2 ? a.nqi * a.nqi : a.nqi;
     const int qo = a.dim == 2 ? a.nqo * a.nqo : a.nqo;
-    const long long nvi = (long long)a.ncomp * a.nel * qi;
-    const long long nvo = (long long)a.ncomp * a.nel * qo;
+    const long long nel_i = h ? (long long)a.nexi * a.neyi : a.nel;
+    const long long nel_o = h ? (long long)a.nexo * a.neyo : a.nel;
+    const long long nvi = (long long)a.ncomp * nel_i * qi;
+    const long long nvo = (long long)a.ncomp * nel_o * qo;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nvo;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long ec = idx / qo;
         const int node = (int)(idx - ec * qo);
         const int io = node % a.nqo, jo = node / a.nqo;
         double sp[MMAX];
-        for (int n = 0; n < a.Mi; ++n) {
-            const double* in = a.in + n * nvi + ec * qi;
-            double s = 0.0;
-            if (a.dim == 2) {
-                for (int b = 0; b < a.nqi; ++b) {
-                    double t = 0.0;
-                    for (int c = 0; c < a.nqi; ++c) t += sS[io * a.nqi + c] * in[b * a.nqi + c];
-                    s += sS[jo * a.nqi + b] * t;
+        if (!h) {
+            for (int n = 0; n < a.Mi; ++n) {
+                const double* in = a.in + n * nvi + ec * qi;
+                double s = 0.0;
+                if (a.dim == 2) {
+                    for (int b = 0; b < a.nqi; ++b) {
+                        double t = 0.0;
+                        for (int c = 0; c < a.nqi; ++c) t += sS[io * a.nqi + c] * in[b * a.nqi + c];
+                        s += sS[jo * a.nqi + b] * t;
+                    }
+                } else {
+                    for (int c = 0; c < a.nqi; ++c) s += sS[io * a.nqi + c] * in[c];
                 }
-            } else {
-                for (int c = 0; c < a.nqi; ++c) s += sS[io * a.nqi + c] * in[c];
+                sp[n] = s;
             }
-            sp[n] = s;
+        } else {
+            const long long comp = ec / nel_o;
+            const int eo = (int)(ec - comp * nel_o);
+            const int exo = eo % a.nexo, eyo = eo / a.nexo;
+            // children (input elements) of this output element and their matrices
+            const int ncx = a.c2f ? 1 : rx, ncy = a.c2f ? 1 : ry;
+            for (int n = 0; n < a.Mi; ++n) {
+                double s = 0.0;
+                for (int cy = 0; cy < ncy; ++cy)
+                    for (int cx = 0; cx < ncx; ++cx) {
+                        const int exi = a.c2f ? exo / rx : rx * exo + cx;
+                        const int eyi = a.c2f ? eyo / ry : ry * eyo + cy;
+                        const int mx = a.c2f ? exo % rx : cx, my = a.c2f ? eyo % ry : cy;
+                        const double* in = a.in + n * nvi + (comp * nel_i + (long long)eyi * a.nexi + exi) * qi;
+                        const double* Sx = sS + mx * nm;
+                        if (a.dim == 2) {
+                            const double* Syc = sSy + my * nm;
+                            for (int b = 0; b < a.nqi; ++b) {
+                                double t = 0.0;
+                                for (int c = 0; c < a.nqi; ++c) t += Sx[io * a.nqi + c] * in[b * a.nqi + c];
+                                s += Syc[jo * a.nqi + b] * t;
+                            }
+                        } else {
+                            for (int c = 0; c < a.nqi; ++c) s += Sx[io * a.nqi + c] * in[c];
+                        }
+                    }
+                sp[n] = s;
+            }
         }
         for (int m = 0; m < a.Mo; ++m) {
             double v = 0.0;
@@ -161,7 +199,9 @@ __global__ void k_transfer(const TransferArgs a) {
 
 cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s) {
     const int qo = a.dim == 2 ? a.nqo * a.nqo : a.nqo;
-    k_transfer<<<ew_grid((long long)a.ncomp * a.nel * qo, 256), 256, 0, s>>>(a);
+    const bool h = a.rx > 1 || a.ry > 1;
+    const long long nel_o = h ? (long long)a.nexo * a.neyo : a.nel;
+    k_transfer<<<ew_grid((long long)a.ncomp * nel_o * qo, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

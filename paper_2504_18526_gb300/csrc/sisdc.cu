@@ -55,6 +55,11 @@ struct sisdc_level_s {
     // transfers to the next coarser level
     double *d_Ix = nullptr, *d_Px = nullptr, *d_Rx = nullptr;
     double *d_It = nullptr, *d_Pt = nullptr, *d_Rt = nullptr, *d_one = nullptr;
+    // element ratio to the next coarser level per direction (1, or 2: 2:1
+    // h-coarsening); with a ratio 2 the x tables above hold one matrix per
+    // child and the y tables below are used
+    int rx = 1, ry = 1;
+    double *d_Iy = nullptr, *d_Py = nullptr, *d_Ry = nullptr;
 };
 
 struct sisdc_ctx_s {
@@ -258,6 +263,18 @@ void k_transfer(sisdc_level_s* fine, int op, const double* in, double* out, int 
             a.nqi = fine->nq; a.nqo = coarse->nq; a.Mi = 1; a.Mo = 1;
             a.S = fine->d_Px; a.Tt = fine->d_one;
             break;
+    }
+    if (fine->rx > 1 || fine->ry > 1) {
+        a.rx = fine->rx;
+        a.ry = fine->ry;
+        a.c2f = op == T_INTERP;
+        a.Sy = op == T_INTERP ? fine->d_Iy : op == T_RESTRICT ? fine->d_Ry : fine->d_Py;
+        const sisdc_level_s* li = op == T_INTERP ? coarse : fine;
+        const sisdc_level_s* lo = op == T_INTERP ? fine : coarse;
+        a.nexi = li->desc.nel[0];
+        a.neyi = li->desc.dim == 2 ? li->desc.nel[1] : 1;
+        a.nexo = lo->desc.nel[0];
+        a.neyo = lo->desc.dim == 2 ? lo->desc.nel[1] : 1;
     }
     check(fine->ctx, launch_transfer(a, fine->ctx->stream), "transfer kernel");
     fine->ctx->launches++;
@@ -610,10 +627,12 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         return fail(c, SISDC_E_ARG, "mixed precision supports 2D levels with P >= 3");
     if (!c->levels.empty()) {
         const sisdc_level_desc& p = c->levels.back()->desc;
-        if (p.dim != d->dim || p.nel[0] != d->nel[0] || (d->dim == 2 && p.nel[1] != d->nel[1]) ||
-            p.nodes != d->nodes || p.lo[0] != d->lo[0] || p.hi[0] != d->hi[0] ||
+        const bool gx = d->nel[0] == p.nel[0] || d->nel[0] == 2 * p.nel[0];
+        const bool gy = d->dim == 1 || d->nel[1] == p.nel[1] || d->nel[1] == 2 * p.nel[1];
+        if (p.dim != d->dim || !gx || !gy || p.nodes != d->nodes || p.lo[0] != d->lo[0] || p.hi[0] != d->hi[0] ||
             (d->dim == 2 && (p.lo[1] != d->lo[1] || p.hi[1] != d->hi[1])))
-            return fail(c, SISDC_E_ARG, "levels must share dim, element grid, box and node kind");
+            return fail(c, SISDC_E_ARG,
+                        "levels must share dim, box and node kind; element grids equal or 2:1 per direction");
         if (p.P > d->P || p.M > d->M) return fail(c, SISDC_E_ARG, "levels must be added coarse to fine");
     }
     sisdc_level_s* lv = new sisdc_level_s();
@@ -658,6 +677,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     // transfers to the coarser level
     std::vector<double> ttab;
     size_t off_Ix = 0, off_Px = 0, off_Rx = 0, off_It = 0, off_Pt = 0, off_Rt = 0, off_one = 0;
+    size_t off_Iy = 0, off_Py = 0, off_Ry = 0;
     if (lv->index > 0) {
         sisdc_level_s* cl = c->levels.back();
         const std::vector<double>& xf = lv->tab.gll;
@@ -691,7 +711,17 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
                 for (int b = 0; b < Mf; ++b) Rt[a * Mf + b] = RC[a * Mf + b] - (a > 0 ? RC[(a - 1) * Mf + b] : 0.0);
         }
         auto push = [&](const std::vector<double>& v) { size_t o = ttab.size(); ttab.insert(ttab.end(), v.begin(), v.end()); return o; };
-        off_Ix = push(Ix); off_Px = push(Px); off_Rx = push(Rx);
+        lv->rx = d->nel[0] / cl->desc.nel[0];
+        lv->ry = d->dim == 2 ? d->nel[1] / cl->desc.nel[1] : 1;
+        if (lv->rx > 1 || lv->ry > 1) {
+            // 2:1 h-coarsening in at least one direction: child matrices per direction
+            std::vector<double> Ih, Ph, Rh;
+            h_transfer_matrices(d->P, cl->desc.P, c->prob.projection == 1, &Ih, &Ph, &Rh);
+            off_Ix = push(lv->rx > 1 ? Ih : Ix); off_Px = push(lv->rx > 1 ? Ph : Px); off_Rx = push(lv->rx > 1 ? Rh : Rx);
+            off_Iy = push(lv->ry > 1 ? Ih : Ix); off_Py = push(lv->ry > 1 ? Ph : Px); off_Ry = push(lv->ry > 1 ? Rh : Rx);
+        } else {
+            off_Ix = push(Ix); off_Px = push(Px); off_Rx = push(Rx);
+        }
         off_It = push(It); off_Pt = push(Pt); off_Rt = push(Rt);
         off_one = push(std::vector<double>{1.0});
     }
@@ -738,6 +768,7 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         double* t = lv->d_tab + htab.size();
         lv->d_Ix = t + off_Ix; lv->d_Px = t + off_Px; lv->d_Rx = t + off_Rx;
         lv->d_It = t + off_It; lv->d_Pt = t + off_Pt; lv->d_Rt = t + off_Rt; lv->d_one = t + off_one;
+        lv->d_Iy = t + off_Iy; lv->d_Py = t + off_Py; lv->d_Ry = t + off_Ry;
     }
     Geo& g = lv->geo;
     g.dim = d->dim; g.nq = nq; g.nqy = lv->nqy; g.q = lv->Q;

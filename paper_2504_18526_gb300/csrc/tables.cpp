@@ -162,6 +162,74 @@ std::vector<double> l2_projection_matrix(int Pf, int Pc) {
     return P;
 }
 
+void h_transfer_matrices(int Pf, int Pc, int l2, std::vector<double>* I2, std::vector<double>* P2,
+                         std::vector<double>* R2) {
+    std::vector<ld> xf, wf, xc, wc;
+    gll_ld(Pf, &xf, &wf);
+    gll_ld(Pc, &xc, &wc);
+    const int nf = Pf + 1, nc = Pc + 1;
+    // child c covers xi in [c - 1, c] of the coarse element: xi = (eta + 2c - 1) / 2
+    std::vector<ld> I(2 * nf * nc);
+    for (int c = 0; c < 2; ++c)
+        for (int k = 0; k < nf; ++k)
+            for (int a = 0; a < nc; ++a) I[(c * nf + k) * nc + a] = lagrange(xc, a, (xf[k] + 2 * c - 1) / 2.0L);
+    I2->assign(I.begin(), I.end());
+    // R = W_c^{-1} I^T W_f with the child's half width: R[c][a][k] = I[c][k][a] (wf_k / 2) / wc_a
+    R2->assign(2 * nc * nf, 0.0);
+    for (int c = 0; c < 2; ++c)
+        for (int a = 0; a < nc; ++a)
+            for (int k = 0; k < nf; ++k)
+                (*R2)[(c * nc + a) * nf + k] = (double)(I[(c * nf + k) * nc + a] * (wf[k] / 2.0L) / wc[a]);
+    std::vector<ld> P(2 * nc * nf, 0.0L);
+    if (l2) {
+        // least squares over both children: (E^T W E)^{-1} E^T W, E = [I_0; I_1], W = wf / 2
+        std::vector<ld> A(nc * nc, 0.0L), B(nc * 2 * nf, 0.0L);
+        for (int a = 0; a < nc; ++a) {
+            for (int b = 0; b < nc; ++b)
+                for (int r = 0; r < 2 * nf; ++r) A[a * nc + b] += I[r * nc + a] * (wf[r % nf] / 2.0L) * I[r * nc + b];
+            for (int r = 0; r < 2 * nf; ++r) B[a * 2 * nf + r] = I[r * nc + a] * (wf[r % nf] / 2.0L);
+        }
+        for (int col = 0; col < nc; ++col) {           // Gauss-Jordan, partial pivoting
+            int piv = col;
+            for (int r = col + 1; r < nc; ++r)
+                if (fabsl(A[r * nc + col]) > fabsl(A[piv * nc + col])) piv = r;
+            if (piv != col) {
+                for (int q = 0; q < nc; ++q) std::swap(A[col * nc + q], A[piv * nc + q]);
+                for (int q = 0; q < 2 * nf; ++q) std::swap(B[col * 2 * nf + q], B[piv * 2 * nf + q]);
+            }
+            for (int r = 0; r < nc; ++r) {
+                if (r == col) continue;
+                const ld f = A[r * nc + col] / A[col * nc + col];
+                for (int q = 0; q < nc; ++q) A[r * nc + q] -= f * A[col * nc + q];
+                for (int q = 0; q < 2 * nf; ++q) B[r * 2 * nf + q] -= f * B[col * 2 * nf + q];
+            }
+        }
+        for (int c = 0; c < 2; ++c)
+            for (int a = 0; a < nc; ++a)
+                for (int k = 0; k < nf; ++k) P[(c * nc + a) * nf + k] = B[a * 2 * nf + c * nf + k] / A[a * nc + a];
+    } else {
+        // embedded interpolation after linear blending: the coarse node xi takes
+        // the blended left child at eta = 2 xi + 1 (xi <= 0) or the blended right
+        // child at eta = 2 xi - 1; blending moves both interface values to their
+        // mean with a linear ramp that vanishes at the child's outer end
+        for (int a = 0; a < nc; ++a) {
+            const ld xi = xc[a];
+            if (xi <= 0.0L) {
+                const ld eta = 2.0L * xi + 1.0L, ramp = (1.0L + eta) / 4.0L;
+                for (int k = 0; k < nf; ++k) P[(0 * nc + a) * nf + k] = lagrange(xf, k, eta);
+                P[(0 * nc + a) * nf + (nf - 1)] -= ramp;
+                P[(1 * nc + a) * nf + 0] += ramp;
+            } else {
+                const ld eta = 2.0L * xi - 1.0L, ramp = (1.0L - eta) / 4.0L;
+                for (int k = 0; k < nf; ++k) P[(1 * nc + a) * nf + k] = lagrange(xf, k, eta);
+                P[(1 * nc + a) * nf + 0] -= ramp;
+                P[(0 * nc + a) * nf + (nf - 1)] += ramp;
+            }
+        }
+    }
+    P2->assign(P.begin(), P.end());
+}
+
 bool build_level_tables(int P, int M, int lobatto, LevelTables* t) {
     if (P < 1 || P > 15 || M < 1 || M > 8 || (lobatto && M < 2)) return false;
     const int nq = P + 1;

@@ -15,6 +15,15 @@ bool build_level_tables(int P, int M, int lobatto, LevelTables* t);
 // E[p][j] = l_j(pts[p]) for the Lagrange basis on `nodes`.
 std::vector<double> lagrange_matrix(const std::vector<double>& nodes, const std::vector<double>& pts);
 
+// 2:1 h-coarsening transfers per direction (children 0 = left, 1 = right half
+// of the coarse element), child-major: I2 [2][(Pf+1) x (Pc+1)] coarse
+// polynomial at the child's nodes; P2 [2][(Pc+1) x (Pf+1)] solution
+// projection (embedded interpolation after linear blending of the jump
+// between the children, or with l2 != 0 the least-squares fit over both
+// children); R2 [2][(Pc+1) x (Pf+1)] = W_c^-1 I^T W_f (half-width children).
+void h_transfer_matrices(int Pf, int Pc, int l2, std::vector<double>* I2, std::vector<double>* P2,
+                         std::vector<double>* R2);
+
 // Element-wise fast diagonalisation of the 1D SIPG line operator of element
 // width h: S[a * (P+1) + i] = component a of the i-th generalised eigenvector
 // of (element block, GLL mass), M-orthonormal; lam[i] ascending.
