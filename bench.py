@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--per-instance", type=int, default=0,
                     help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--cfls", type=float, nargs="*", default=[64, 32, 16, 8, 4],
+                    help="paper_convdiff: CFL numbers of the iteration study")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-nel", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--shard", type=int, default=0, help=argparse.SUPPRESS)
@@ -388,15 +390,32 @@ def measured_peaks():
 
 # Algorithmic work of one correction-sweep launch (per fine DOF), from the
 # per-unit operation counts of the path: an SIPG operator application costs
-# 8(P+1) + 20 flop, a convective-operator application 4(P+1) n_c + 10 flop,
-# a CG iteration adds 10 flop of vector updates, a right-hand side 12 flop,
-# and the S.F quadrature 2M flop per collocation node.  Per node of an SI(2)
+# 8(P+1) + 20 flop (the element's two (P+1)-term stiffness sums and the face
+# derivatives and jumps of its four faces), a CG iteration adds 10 flop of
+# vector updates, a right-hand side 12 flop, and the S.F quadrature 2M flop
+# per collocation node.  A convective-operator application costs per node
+# (all components) 4(P+1) flop per component for the two derivative sums,
+# the flux evaluation, and the Rusanov face flux on the 4(P+1) face nodes of
+# each (P+1)^2-node element; for Navier-Stokes also the BR1 viscous term
+# (lifted gradients of three primitive variables and the divergence of
+# three viscous-flux components: 24(P+1) + 40).  Per node of an SI(2)
 # correction sweep: one SIPG application per CG iteration, one for the
 # stage-2 start residual and one for the cached L u; two convective
 # applications.
-def sweep_flops(P, ncomp, M, nsweeps, iters, nv):
+FLUX_FLOPS = {"convdiff": (2, 8), "burgers": (4, 20), "euler": (24, 60), "ns": (24, 60)}   # node, face node
+
+
+def conv_flops_per_dof(P, ncomp, pde):
+    f, r = FLUX_FLOPS[pde]
+    node = ncomp * 4 * (P + 1) + f + 4.0 * r / (P + 1)
+    if pde == "ns":
+        node += 24 * (P + 1) + 40
+    return node / ncomp
+
+
+def sweep_flops(P, ncomp, M, nsweeps, iters, nv, pde="convdiff"):
     mv = 8 * (P + 1) + 20
-    cv = 4 * (P + 1) * ncomp + 10
+    cv = conv_flops_per_dof(P, ncomp, pde)
     per_node = 2 * mv + 2 * cv + 2 * 12 + 2 * M
     return float(nv) * (nsweeps * M * per_node + iters * (mv + 10))
 
@@ -578,7 +597,8 @@ def main_arm(args):
     kctx.close()
     launches_per_step = kstats["launches"] / args.steps
     nsw = kt["dof_sweeps"] / max(1, nv)
-    flops = sweep_flops(lv["P"], nc, M, nsw / max(1, kt["launches"]), kt["iters"] / max(1, kt["launches"]), nv)
+    flops = sweep_flops(lv["P"], nc, M, nsw / max(1, kt["launches"]), kt["iters"] / max(1, kt["launches"]), nv,
+                        w["pde"])
     avg_ms = kt["ms"] / max(1, kt["launches"])
     achieved = flops / (avg_ms * 1e-3) / 1e12
     hbm_peak, hbm_kind = measured_peaks()
@@ -1005,6 +1025,109 @@ def stability_arm(args):
                       "cpu_baseline": cpu}))
 
 
+# ---------------------------------------------------------------------------
+# the paper's 1D convection-diffusion studies through the library
+# ---------------------------------------------------------------------------
+def convdiff_run(S, dev, nels, P, Ms, nu, cfl, ncycles, start="cascade", T=5.0, rtol=1e-13):
+    """One run of u_t + u_x = nu u_xx on the periodic unit interval to time T
+    (the wave packet), levels with nels[l] elements of degree P and Ms[l]
+    Radau-Right nodes, dt from the CFL number on the finest grid
+    (dx = dx_e / (2 P^2), lambda = 1), ncycles V-cycles + post-sweep per step
+    (one level: predictor + ncycles sweeps).  Returns (GLL L2 error at T,
+    steps); the error is inf when the run blew up."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import inputs
+    w = dict(pde="convdiff", dim=1, ncomp=1, adv=(1.0, 0.0), nu=nu, lo=(0.0, 0.0), hi=(1.0, 0.0),
+             nodes="radau_right", levels=[dict(nel=(ne, 1), P=P, M=M) for ne, M in zip(nels, Ms)])
+    ctx = S.Context(w, cg_rtol=rtol, cg_maxit=20000, use_graph=1)
+    nc, n, M = ctx.info(-1)
+    X = np.zeros(n)
+    S.sisdc_level_coords(ctx.levels[-1], X, None)
+    dx = (1.0 / nels[-1]) / (2.0 * P * P)
+    nsteps = int(math.ceil(T / (cfl * dx) - 1e-9))
+    dt = T / nsteps
+    du = torch.from_numpy(inputs.wave_packet(X, 0.0, nu).ravel().copy()).to(dev)
+    ex = torch.from_numpy(inputs.wave_packet(X, T, nu).ravel().copy()).to(dev)
+    st = S.START_IDS[start]
+    try:
+        for k in range(nsteps):
+            S.sisdc_step(ctx.ctx, du, k * dt, dt, ncycles, st, 1)
+            if k % 256 == 255 and not bool(torch.isfinite(du).all()):
+                raise FloatingPointError
+        S.sisdc_sync(ctx.ctx)
+        err = float(S.sisdc_norms(ctx.levels[-1], du, ex)[0][0])
+        if not math.isfinite(err) or err > 1e3:
+            err = float("inf")
+    except (FloatingPointError, S.SisdcError):
+        err = float("inf")
+    ctx.close()
+    return err, nsteps
+
+
+CONVDIFF_TABLE_MESHES = ((5, 10, 20), (10, 20, 40), (20, 40, 80), (40, 80, 160))
+CONVDIFF_TABLE_CFLS = (32, 64, 128, 256)
+
+
+def converged_count(errs):
+    """Iterations after which one more iteration changes the error by less
+    than 10 % (the paper's convergence rule); errs[k] = error after k+1."""
+    for k in range(len(errs) - 1):
+        if abs(errs[k + 1] - errs[k]) <= 0.1 * abs(errs[k]):
+            return k + 1
+    return None
+
+
+def paper_convdiff_arm(args):
+    """The paper's Sec. 8 convection-diffusion studies on the GPU: the L2
+    error table of the convergence analysis (MLSDC^10_{3,5,7}, P = 12,
+    elements doubling per level) and the CFL study (nu = 1e-3: three levels
+    16/32/64 elements of degree 15, M 3/5/7; nu = 0: two levels 32/64, M
+    5/7; Cascade start, N_c = 2) against single-level SDC on the finest
+    level: fine sweeps to convergence per CFL number."""
+    import math
+    import torch
+    from paper_2504_18526_gb300 import sisdc as S
+    from paper_2504_18526_gb300.build import build
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build()
+    S.load()
+    t0 = time.perf_counter()
+    table = {}
+    for mesh in CONVDIFF_TABLE_MESHES:
+        for cfl in CONVDIFF_TABLE_CFLS:
+            e, n = convdiff_run(S, dev, mesh, 12, (3, 5, 7), 1e-3, cfl, 10)
+            table["%d,%d,%d@%d" % (mesh + (cfl,))] = {"error": e, "steps": n}
+    orders = {}
+    for k in range(1, len(CONVDIFF_TABLE_MESHES)):
+        for cfl in CONVDIFF_TABLE_CFLS:
+            a = table["%d,%d,%d@%d" % (CONVDIFF_TABLE_MESHES[k - 1] + (cfl,))]["error"]
+            b = table["%d,%d,%d@%d" % (CONVDIFF_TABLE_MESHES[k] + (cfl,))]["error"]
+            orders["space %s@%d" % (CONVDIFF_TABLE_MESHES[k], cfl)] = math.log2(a / b)
+    study = {}
+    for nu, nels, Ms in ((1e-3, (16, 32, 64), (3, 5, 7)), (0.0, (32, 64), (5, 7))):
+        for cfl in args.cfls:
+            ml, sd = [], []
+            for C in range(1, 13):
+                ml.append(convdiff_run(S, dev, nels, 15, Ms, nu, cfl, C)[0])
+                if converged_count(ml) or not math.isfinite(ml[-1]):
+                    break
+            for N in range(1, 21):
+                sd.append(convdiff_run(S, dev, nels[-1:], 15, Ms[-1:], nu, cfl, N - 1)[0])
+                if converged_count(sd) or not math.isfinite(sd[-1]):
+                    break
+            c_ml, c_sd = converged_count(ml), converged_count(sd)
+            study["nu=%g@CFL%g" % (nu, cfl)] = {
+                "mlsdc_errors_per_cycles": ml, "sdc_errors_per_sweeps": sd,
+                "mlsdc_cycles": c_ml, "mlsdc_fine_sweeps": None if c_ml is None else c_ml + 1,
+                "sdc_sweeps": c_sd}
+    print(json.dumps({"metric": "paper 1D convection-diffusion studies", "workload": "paper_convdiff",
+                      "error_table": table, "orders": orders, "cfl_study": study,
+                      "seconds": time.perf_counter() - t0}))
+
+
 def mlp_flops(rows, n_in, H, q):
     """GEMM flops of one inference (forward) and one training step (forward,
     the five backward products) of the n_in -> H -> H -> q network."""
@@ -1117,6 +1240,8 @@ if __name__ == "__main__":
         ensemble_arm(a)
     elif a.workload == "stability_map":
         stability_arm(a)
+    elif a.workload == "paper_convdiff":
+        paper_convdiff_arm(a)
     elif a.workload == "mlp_ns_level":
         mlp_arm(a)
     else:

@@ -692,14 +692,14 @@ struct EnsSweeper {
             }
             __syncthreads();
             if (act) {
-                double s = 0.0;
+                double s = 0.0, t = 0.0;          // the two derivative sums, interleaved
 #pragma unroll
-                for (int k = 0; k < NQ; ++k) s += sD[i * NQ + k] * sFx[j * NQ + k];
+                for (int k = 0; k < NQ; ++k) {
+                    s += sD[i * NQ + k] * sFx[j * NQ + k];
+                    t += sD[j * NQ + k] * sFy[k * NQ + i];
+                }
                 double cv = -I.sx * s;
-                s = 0.0;
-#pragma unroll
-                for (int k = 0; k < NQ; ++k) s += sD[j * NQ + k] * sFy[k * NQ + i];
-                cv -= I.sy * s;
+                cv -= I.sy * t;
                 const double* fc = sf + (size_t)le * TRS;
                 if (i == 0) cv += fc[j];
                 if (i == NQ - 1) cv += fc[NQ + j];

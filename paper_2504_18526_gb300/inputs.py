@@ -239,6 +239,25 @@ def ensemble_exact(inst, X, Y, t, K=6, amp=1.0):
     return acc.real[None]
 
 
+# Wave packet of the paper's 1D convection-diffusion studies (the coefficient
+# table of the preliminary studies, Sec. 7, reused in Sec. 8): rows
+# (kappa / pi, a, s) of u = sum_i a_i sin(kappa_i (x - s_i - v t)) exp(-kappa_i^2 nu t)
+# on the periodic unit interval.
+WAVE_PACKET = ((2, 1.00, 0.00), (6, 1.50, 0.05), (10, 1.80, 0.10), (14, 1.70, 0.15),
+               (18, 1.50, 0.20), (24, 1.30, 0.30), (30, 1.15, 0.18))
+
+
+def wave_packet(X, t, nu, v=1.0):
+    """The exact wave-packet solution at nodes X (returned with a leading
+    component axis)."""
+    X = np.asarray(X, dtype=float)
+    u = np.zeros(X.shape)
+    for kp, a, s in WAVE_PACKET:
+        k = kp * math.pi
+        u += a * np.sin(k * (X - s - v * t)) * math.exp(-k * k * nu * t)
+    return u[None]
+
+
 def random_field(shape, seed, scale=1.0):
     """Seeded smooth-free random nodal data for operator-level parity tests."""
     return scale * np.random.default_rng(SEED_BASE + 77 + int(seed)).standard_normal(shape)

@@ -54,15 +54,21 @@ def test_clock_record_without_nvidia_smi():
 
 def test_sweep_work_counts():
     """Per-unit counts of a correction-sweep launch: FP64 flops (SIPG
-    application 8(P+1)+20 per DOF, convective 4(P+1)n_c+10, CG iteration 10
-    more, right-hand side 12, quadrature 2M; two SIPG and two convective
-    applications and two right-hand sides per SI(2) node) and bytes (19 FP64
-    arrays per node, 11 per CG iteration)."""
+    application 8(P+1)+20 per DOF; convective per node 4(P+1) per component
+    plus the flux (Burgers: 4 per node, 20 per face node on 4(P+1) of the
+    (P+1)^2 nodes); CG iteration 10 more, right-hand side 12, quadrature 2M;
+    two SIPG and two convective applications and two right-hand sides per
+    SI(2) node) and bytes (19 FP64 arrays per node, 11 per CG iteration)."""
     P, nc, M, nv = 7, 2, 5, 131072
-    mv, cv = 8 * 8 + 20, 4 * 8 * 2 + 10
+    mv, cv = 8 * 8 + 20, (2 * 4 * 8 + 4 + 4 * 20 / 8) / 2
     per_node = 2 * mv + 2 * cv + 2 * 12 + 2 * M
-    assert bench.sweep_flops(P, nc, M, 1, 0, nv) == nv * M * per_node
-    assert bench.sweep_flops(P, nc, M, 1, 10, nv) - bench.sweep_flops(P, nc, M, 1, 0, nv) == nv * 10 * (mv + 10)
+    assert bench.sweep_flops(P, nc, M, 1, 0, nv, "burgers") == nv * M * per_node
+    assert (bench.sweep_flops(P, nc, M, 1, 10, nv, "burgers") - bench.sweep_flops(P, nc, M, 1, 0, nv, "burgers")
+            == nv * 10 * (mv + 10))
+    # one component: the convective count is per node
+    assert bench.conv_flops_per_dof(8, 1, "convdiff") == 4 * 9 + 2 + 4 * 8 / 9
+    # a system's derivative sums scale with the components, its flux per node does not
+    assert bench.conv_flops_per_dof(7, 4, "euler") == 4 * 8 + (24 + 4 * 60 / 8) / 4
     assert bench.sweep_bytes(M, 1, 0, nv) == 8 * nv * M * 19
     assert bench.sweep_bytes(M, 1, 3, nv) - bench.sweep_bytes(M, 1, 0, nv) == 8 * nv * 3 * 11
 
