@@ -374,6 +374,19 @@ sisdc_status sisdc_mlp_train(sisdc_mlp mlp, const double* d_r, const double* d_d
                              int epochs, double lr, double* h_loss);
 /* d_z (+)= r + s MLP(r / s) for every element and component (add != 0 adds). */
 sisdc_status sisdc_mlp_apply(sisdc_mlp mlp, const double* d_r, double c, double* d_z, int add);
+/* Forward-pass kernel of sisdc_mlp_apply in the BF16 mode: enable != 0 (the
+ * default where it fits) = one fused persistent kernel on the tcgen05 tensor
+ * cores -- the patch rows gathered straight into swizzled shared-memory
+ * operand panels, the BF16 weights resident in shared memory (TMA), the FP32
+ * accumulators in tensor memory, bias + tanh and the output z fused into
+ * the epilogues; enable = 0: the patch matrix, three warp-level mma.sync
+ * GEMMs and a scatter kernel.  SISDC_E_ARG when the fused kernel does not
+ * fit the network (FP32 mode; hidden width not a multiple of 16 or above
+ * 128; more than 128 outputs). */
+sisdc_status sisdc_mlp_set_tc(sisdc_mlp mlp, int enable);
+/* Synchronise the model's stream; SISDC_E_TIMEOUT if a bounded wait of the
+ * fused forward pass gave up (its output is then invalid). */
+sisdc_status sisdc_mlp_sync(sisdc_mlp mlp);
 const char* sisdc_mlp_last_error(sisdc_mlp mlp);
 
 /* Log, for every implicit solve of the FP64 form on level index `level`, the

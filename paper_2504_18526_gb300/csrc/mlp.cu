@@ -23,6 +23,7 @@
 
 #include "../../include/sisdc.h"
 #include "ds.cuh"
+#include "mlp_tc.h"
 #include "ops.h"
 
 namespace sisdc {
@@ -461,6 +462,12 @@ struct sisdc_mlp_s {
     float* sinv = nullptr;                   // 1 / patch scale
     double* lacc = nullptr;                  // loss accumulator of a training epoch
     long long adam_t = 0;
+    // tcgen05 forward pass (mlp_tc.cu): transposed BF16 weights, their TMA
+    // descriptors, and whether it is available / selected
+    __nv_bfloat16 *W1T = nullptr, *W2T = nullptr, *W3T = nullptr;
+    alignas(64) unsigned char tmap[3][128];
+    int tc_ok = 0, use_tc = 1, K1p = 0, N3 = 0, nsm = 0;
+    int* derr = nullptr;
     std::string err;
     // offsets
     long long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
@@ -714,6 +721,23 @@ sisdc_status sisdc_mlp_create(sisdc_level lv, int hidden, unsigned long long see
         k_to_bf16<<<ew(p->nparam), 256>>>(p->theta, p->theta_b, p->nparam);
         e = cudaDeviceSynchronize();
     }
+    // the tcgen05 forward pass, where the network's shape fits it
+    if (e == cudaSuccess && p->bf16 && mlp_tc_eligible(p->n_in, p->H, p->q, nullptr)) {
+        p->K1p = (p->n_in + 63) / 64 * 64;
+        p->N3 = (p->q + 15) / 16 * 16;
+        al((void**)&p->W1T, (size_t)p->H * p->K1p * sizeof(__nv_bfloat16));
+        al((void**)&p->W2T, (size_t)p->H * 128 * sizeof(__nv_bfloat16));
+        al((void**)&p->W3T, (size_t)p->N3 * 128 * sizeof(__nv_bfloat16));
+        al((void**)&p->derr, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->derr, 0, sizeof(int));
+        int dev = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            p->tc_ok = mlp_tc_encode(p->tmap[0], p->W1T, p->H, p->K1p, p->H) &&
+                       mlp_tc_encode(p->tmap[1], p->W2T, p->H, 128, p->H) &&
+                       mlp_tc_encode(p->tmap[2], p->W3T, p->N3, 128, p->N3);
+    }
     if (e != cudaSuccess) {
         sisdc_mlp_destroy(p);
         return e == cudaErrorMemoryAllocation ? SISDC_E_OOM : SISDC_E_CUDA;
@@ -729,6 +753,7 @@ void sisdc_mlp_destroy(sisdc_mlp p) {
     cudaFree(p->X); cudaFree(p->H1); cudaFree(p->H2); cudaFree(p->dH); cudaFree(p->Y); cudaFree(p->T);
     cudaFree(p->dY); cudaFree(p->s); cudaFree(p->part); cudaFree(p->ws);
     cudaFree(p->ss); cudaFree(p->sinv); cudaFree(p->lacc); cudaFree(p->Xb);
+    cudaFree(p->W1T); cudaFree(p->W2T); cudaFree(p->W3T); cudaFree(p->derr);
     delete p;
 }
 
@@ -804,6 +829,22 @@ sisdc_status sisdc_mlp_train(sisdc_mlp p, const double* d_r, const double* d_dx,
 sisdc_status sisdc_mlp_apply(sisdc_mlp p, const double* d_r, double c, double* d_z, int add) {
     if (!p || !d_r || !d_z || !(c > 0.0)) return SISDC_E_ARG;
     try {
+        if (p->tc_ok && p->use_tc) {
+            // patch scales, then the fused gather + three layers + output on tcgen05
+            k_mlp_elem_ss<<<ew(p->rows), 256, 0, p->stream>>>(d_r, p->rows, p->q, p->ss);
+            k_mlp_scale<<<ew(p->rows), 256, 0, p->stream>>>(p->ss, p->nex, p->ney, p->q, p->rows, p->s, p->sinv);
+            mck(p, mlp_tc_pack(p->theta + p->oW1, p->theta + p->oW2, p->theta + p->oW3, p->n_in, p->H, p->q, p->K1p,
+                               p->N3, p->W1T, p->W2T, p->W3T, p->stream), "pack");
+            MlpTcArgs a{};
+            a.field = d_r; a.sinv = p->sinv; a.s = p->s; a.z = d_z; a.add = add;
+            a.b1 = p->theta + p->ob1; a.b2 = p->theta + p->ob2; a.b3 = p->theta + p->ob3;
+            a.nex = p->nex; a.ney = p->ney; a.q = p->q; a.n_in = p->n_in; a.H = p->H;
+            a.nP1 = p->K1p / 64; a.N3 = p->N3; a.rows = p->rows;
+            a.feat = (float)(0.1 * std::log(c / (p->h * p->h)));
+            a.err = p->derr;
+            mck(p, mlp_tc_forward(a, p->tmap[0], p->tmap[1], p->tmap[2], p->nsm, p->stream), "tcgen05 forward");
+            return SISDC_OK;
+        }
         gather(p, d_r, c);
         forward(p);
         const long long nq = p->rows * p->q;
@@ -811,6 +852,34 @@ sisdc_status sisdc_mlp_apply(sisdc_mlp p, const double* d_r, double c, double* d
         mck(p, cudaGetLastError(), "scatter");
     } catch (const MlpFail& f) {
         return f.st;
+    }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_mlp_set_tc(sisdc_mlp p, int enable) {
+    if (!p) return SISDC_E_ARG;
+    if (enable && !p->tc_ok) {
+        p->err = "the tcgen05 forward pass does not fit this network (BF16 mode, hidden width a multiple of 16 "
+                 "up to 128, at most 128 outputs) or no TMA encoder";
+        return SISDC_E_ARG;
+    }
+    p->use_tc = enable ? 1 : 0;
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_mlp_sync(sisdc_mlp p) {
+    if (!p) return SISDC_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    int flag = 0;
+    if (e == cudaSuccess && p->derr) e = cudaMemcpy(&flag, p->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        p->err = std::string("sync: ") + cudaGetErrorString(e);
+        return SISDC_E_CUDA;
+    }
+    if (flag) {
+        cudaMemset(p->derr, 0, sizeof(int));
+        p->err = "a wait of the tcgen05 forward pass timed out";
+        return SISDC_E_TIMEOUT;
     }
     return SISDC_OK;
 }

@@ -1,0 +1,335 @@
+// Fused forward pass of the element-patch MLP on the fifth-generation tensor
+// cores (tcgen05): one 128-row tile of patch rows per step of a persistent
+// CTA, all three layers chained through tensor memory.
+//
+//   layer 1: the patch rows are gathered from the FP64 residual, scaled by
+//            1/s and rounded to BF16 straight into the swizzled A panels in
+//            shared memory (no patch matrix in global memory); W1^T is
+//            resident in shared memory (loaded once per CTA by TMA);
+//            tcgen05.mma accumulates X W1 in TMEM (FP32);
+//   epilogue: TMEM -> registers (tcgen05.ld), + bias, tanh, BF16 -> the A
+//            panels of the next layer;
+//   layer 2 and 3 alike (W2^T, W3^T resident); the last epilogue adds the
+//            bias and writes z = r + s y (FP64) to the output field.
+//
+// One thread issues the MMAs and TMA copies; every wait on an mbarrier is
+// bounded (about 1 s) and records an error flag instead of hanging.  The
+// CTA frees its TMEM before it returns, also after an error.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ds.cuh"
+#include "mlp_tc.h"
+#include "tc.cuh"
+
+namespace sisdc {
+
+namespace {
+
+constexpr int TILE_M = 128;
+constexpr uint32_t PANEL_A = TILE_M * 128;      // bytes of one 64-wide K panel of a 128-row tile
+constexpr uint32_t TMEM_COLS = 128;
+
+struct Layout {
+    uint32_t w1, w2, w3, xs, hs, bias, bars, total;
+};
+
+__host__ __device__ inline Layout layout(int nP1, int H, int N3) {
+    Layout L{};
+    uint32_t o = 0;
+    L.w1 = o; o += (uint32_t)nP1 * H * 128;
+    L.w2 = o; o += 2u * H * 128;
+    L.w3 = o; o += 2u * N3 * 128;
+    L.xs = o; o += PANEL_A;
+    L.hs = o; o += 2 * PANEL_A;
+    L.bias = o; o += (uint32_t)(2 * H + N3) * 4;
+    o = (o + 15) & ~15u;
+    L.bars = o; o += 32;
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
+    return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const __grid_constant__ CUtensorMap m1,
+                                                       const __grid_constant__ CUtensorMap m2,
+                                                       const __grid_constant__ CUtensorMap m3) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    const Layout L = layout(a.nP1, a.H, a.N3);
+    uint8_t* W1s = base + L.w1;
+    uint8_t* W2s = base + L.w2;
+    uint8_t* W3s = base + L.w3;
+    uint8_t* Xs = base + L.xs;
+    uint8_t* Hs = base + L.hs;
+    float* sb1 = reinterpret_cast<float*>(base + L.bias);
+    float* sb2 = sb1 + a.H;
+    float* sb3 = sb2 + a.H;
+    uint64_t* tma_bar = reinterpret_cast<uint64_t*>(base + L.bars);
+    uint64_t* mma_bar = tma_bar + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < a.H; t += blockDim.x) {
+        sb1[t] = a.b1[t];
+        sb2[t] = a.b2[t];
+    }
+    for (int t = tid; t < a.N3; t += blockDim.x) sb3[t] = t < a.q ? a.b3[t] : 0.f;
+    if (tid == 0) {
+        tc::mbar_init(tma_bar, 1);
+        tc::mbar_init(mma_bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // resident weights: W1^T (nP1 panels), W2^T and W3^T (two panels each)
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)(a.nP1 + 2) * a.H * 128 + 2u * a.N3 * 128;
+        tc::mbar_arrive_expect_tx(tma_bar, bytes);
+        for (int p = 0; p < a.nP1; ++p) tc::tma_load_2d(W1s + (size_t)p * a.H * 128, &m1, tma_bar, 64 * p, 0);
+        for (int p = 0; p < 2; ++p) {
+            tc::tma_load_2d(W2s + (size_t)p * a.H * 128, &m2, tma_bar, 64 * p, 0);
+            tc::tma_load_2d(W3s + (size_t)p * a.N3 * 128, &m3, tma_bar, 64 * p, 0);
+        }
+    }
+    bool ok = __syncthreads_and(tc::mbar_wait(tma_bar, 0)) != 0;
+    uint32_t mph = 0;
+    const uint32_t id12 = tc::idesc_bf16_f32(TILE_M, a.H);
+    const uint32_t id3 = tc::idesc_bf16_f32(TILE_M, a.N3);
+    const int k1 = (a.n_in + 15) / 16, kh = a.H / 16;           // MMA K steps of 16
+    const int nel = a.nex * a.ney;
+    const long long ntiles = (a.rows + TILE_M - 1) / TILE_M;
+
+    // epilogue of layers 1 and 2: tanh(acc + bias) in BF16 into the A panels Hs
+    auto hidden_epilogue = [&](const float* bias) {
+        const int r = warp * 32 + lane;
+        for (int c0 = 0; c0 < a.H; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            uint32_t w[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w[k] = pack_bf16(tanhf(v[2 * k] + bias[c0 + 2 * k]), tanhf(v[2 * k + 1] + bias[c0 + 2 * k + 1]));
+            uint8_t* panel = Hs + (c0 >> 6) * PANEL_A;
+            const int k0 = c0 & 63;
+            *reinterpret_cast<uint4*>(panel + tc::sw128_offset(r, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(panel + tc::sw128_offset(r, k0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+    };
+    auto issue = [&](const uint8_t* Abase, const uint8_t* Bbase, uint32_t bpanel, int ksteps, int kfirst,
+                     uint32_t idesc, bool first) {
+        // K steps [kfirst, kfirst + ksteps) of panels 64 wide
+        for (int kk = 0; kk < ksteps; ++kk) {
+            const int k = kfirst + kk, p = k >> 2, s = k & 3;
+            const uint64_t ad = tc::sdesc_k_sw128(tc::smem_u32(Abase + p * PANEL_A + s * 32));
+            const uint64_t bd = tc::sdesc_k_sw128(tc::smem_u32(Bbase + p * bpanel + s * 32));
+            tc::mma_bf16(tmem, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+        }
+        tc::mma_commit(mma_bar);
+    };
+    // every thread waits; ok stays uniform over the block
+    auto wait_mma = [&]() {
+        const bool w = tc::mbar_wait(mma_bar, mph);
+        mph ^= 1;
+        ok = __syncthreads_and(w && ok) != 0;
+        tc::fence_after_sync();
+    };
+
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long row0 = tile * TILE_M;
+        // ---- layer 1: panels of the gathered patch rows ----------------------------
+        for (int p = 0; p < a.nP1 && ok; ++p) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = tid + 128 * i, r = c >> 3, kc = c & 7;
+                const long long grow = row0 + r;
+                const int t0 = 64 * p + 8 * kc;
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = 0.f;
+                if (grow < a.rows) {
+                    const int comp = (int)(grow / nel), el = (int)(grow - (long long)comp * nel);
+                    const int ex = el % a.nex, ey = el / a.nex;
+                    const float si = a.sinv[grow];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int t = t0 + e;
+                        if (t < 9 * a.q) {
+                            const int nb = t / a.q, node = t - nb * a.q;
+                            const int dy = nb / 3 - 1, dx = nb % 3 - 1;
+                            const int en = ((ey + dy + a.ney) % a.ney) * a.nex + (ex + dx + a.nex) % a.nex;
+                            v[e] = d2f_int(a.field[((long long)comp * nel + en) * a.q + node]) * si;
+                        } else if (t == 9 * a.q) {
+                            v[e] = a.feat;
+                        }
+                    }
+                }
+                *reinterpret_cast<uint4*>(Xs + tc::sw128_offset(r, 8 * kc)) =
+                    make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const int ks = min(4, k1 - 4 * p);
+                // Xs holds panel p only: its steps start at 0 within the buffer
+                for (int kk = 0; kk < ks; ++kk) {
+                    const uint64_t ad = tc::sdesc_k_sw128(tc::smem_u32(Xs + kk * 32));
+                    const uint64_t bd = tc::sdesc_k_sw128(tc::smem_u32(W1s + (size_t)p * a.H * 128 + kk * 32));
+                    tc::mma_bf16(tmem, ad, bd, id12, (p == 0 && kk == 0) ? 0u : 1u);
+                }
+                tc::mma_commit(mma_bar);
+            }
+            wait_mma();
+        }
+        if (!ok) break;
+        // ---- layer 2 ---------------------------------------------------------
+        hidden_epilogue(sb1);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue(Hs, W2s, (uint32_t)a.H * 128, kh, 0, id12, true);
+        }
+        wait_mma();
+        if (!ok) break;
+        // ---- layer 3 ---------------------------------------------------------
+        hidden_epilogue(sb2);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue(Hs, W3s, (uint32_t)a.N3 * 128, kh, 0, id3, true);
+        }
+        wait_mma();
+        if (!ok) break;
+        // ---- output: z (+)= r + s (acc + b3) ---------------------------------
+        {
+            const int r = warp * 32 + lane;
+            const long long grow = row0 + r;
+            const float s = grow < a.rows ? a.s[grow] : 0.f;
+            for (int c0 = 0; c0 < a.N3; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                if (grow < a.rows)
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int col = c0 + k;
+                        if (col < a.q) {
+                            const long long o = grow * a.q + col;
+                            const double val = a.field[o] + f2d_int((v[k] + sb3[col]) * s);
+                            a.z[o] = a.add ? a.z[o] + val : val;
+                        }
+                    }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(a.err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace
+
+bool mlp_tc_eligible(int n_in, int H, int q, size_t* smem) {
+    if (H < 16 || H > 128 || H % 16 != 0 || q < 1 || q > 128 || n_in < 1) return false;
+    const int nP1 = (n_in + 63) / 64;
+    const int N3 = (q + 15) / 16 * 16;
+    const Layout L = layout(nP1, H, N3);
+    const size_t need = (size_t)L.total + 1024;
+    if (smem) *smem = need;
+    return need <= 227 * 1024;
+}
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+}  // namespace
+
+// [rows][cols] BF16 row-major (cols a multiple of 64), boxes of 64 x box_rows,
+// 128-byte swizzle
+bool mlp_tc_encode(void* map, const void* ptr, int rows, int cols, int box_rows) {
+    EncodeTiledFn fn = encoder();
+    if (!fn || cols % 64 != 0 || box_rows < 1 || box_rows > 256) return false;
+    if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1u, 1u};
+    return fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t mlp_tc_forward(const MlpTcArgs& a, const void* m1, const void* m2, const void* m3, int nsm,
+                           cudaStream_t s) {
+    size_t smem = 0;
+    if (!mlp_tc_eligible(a.n_in, a.H, a.q, &smem)) return cudaErrorInvalidValue;
+    if (a.nP1 != (a.n_in + 63) / 64 || a.N3 != (a.q + 15) / 16 * 16) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (a.rows + TILE_M - 1) / TILE_M;
+    const int grid = (int)(ntiles < nsm ? ntiles : nsm);
+    k_mlp_fwd_tc<<<grid, 128, smem, s>>>(a, *reinterpret_cast<const CUtensorMap*>(m1),
+                                         *reinterpret_cast<const CUtensorMap*>(m2),
+                                         *reinterpret_cast<const CUtensorMap*>(m3));
+    return cudaGetLastError();
+}
+
+// W1^T [H][K1p], W2^T [H][128], W3^T [N3][128] in BF16 from the FP32 master
+// weights W1 [n_in][H], W2 [H][H], W3 [H][q] (zero padding)
+__global__ void k_mlp_pack_tc(const float* __restrict__ W1, const float* __restrict__ W2, const float* __restrict__ W3,
+                              int n_in, int H, int q, int K1p, int N3, __nv_bfloat16* __restrict__ W1T,
+                              __nv_bfloat16* __restrict__ W2T, __nv_bfloat16* __restrict__ W3T) {
+    const long long n1 = (long long)H * K1p, n2 = (long long)H * 128, n3 = (long long)N3 * 128;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n1 + n2 + n3;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < n1) {
+            const int h = (int)(t / K1p), k = (int)(t % K1p);
+            W1T[t] = __float2bfloat16(k < n_in ? W1[(long long)k * H + h] : 0.f);
+        } else if (t < n1 + n2) {
+            const long long u = t - n1;
+            const int h = (int)(u / 128), k = (int)(u % 128);
+            W2T[u] = __float2bfloat16(k < H ? W2[(long long)k * H + h] : 0.f);
+        } else {
+            const long long u = t - n1 - n2;
+            const int n = (int)(u / 128), k = (int)(u % 128);
+            W3T[u] = __float2bfloat16(n < q && k < H ? W3[(long long)k * q + n] : 0.f);
+        }
+    }
+}
+
+cudaError_t mlp_tc_pack(const float* W1, const float* W2, const float* W3, int n_in, int H, int q, int K1p, int N3,
+                        void* W1T, void* W2T, void* W3T, cudaStream_t s) {
+    k_mlp_pack_tc<<<256, 256, 0, s>>>(W1, W2, W3, n_in, H, q, K1p, N3, static_cast<__nv_bfloat16*>(W1T),
+                                      static_cast<__nv_bfloat16*>(W2T), static_cast<__nv_bfloat16*>(W3T));
+    return cudaGetLastError();
+}
+
+}  // namespace sisdc

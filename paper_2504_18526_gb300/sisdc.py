@@ -122,6 +122,8 @@ def load():
         "sisdc_mlp_train": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_double, P(c_double)]),
         "sisdc_mlp_apply": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_int]),
         "sisdc_mlp_last_error": (ctypes.c_char_p, [c_void_p]),
+        "sisdc_mlp_set_tc": (c_int, [c_void_p, c_int]),
+        "sisdc_mlp_sync": (c_int, [c_void_p]),
         "sisdc_set_solve_log": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int]),
         "sisdc_get_solve_log_count": (c_int, [c_void_p, P(c_int)]),
         "sisdc_solve_learned": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_int, P(c_int)]),
@@ -369,6 +371,14 @@ def sisdc_mlp_train(mlp, r, dx, cs, nsolves, epochs, lr):
 
 def sisdc_mlp_apply(mlp, r, c, z, add=False):
     _mcheck(load().sisdc_mlp_apply(mlp, _ptr(r), c, _ptr(z), 1 if add else 0), mlp)
+
+
+def sisdc_mlp_set_tc(mlp, enable):
+    _mcheck(load().sisdc_mlp_set_tc(mlp, 1 if enable else 0), mlp)
+
+
+def sisdc_mlp_sync(mlp):
+    _mcheck(load().sisdc_mlp_sync(mlp), mlp)
 
 
 def sisdc_set_solve_log(ctx, level, r=None, dx=None, cs=None, capacity=0):
