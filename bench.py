@@ -1189,6 +1189,31 @@ def mlp_arm(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t_inf = e0.elapsed_time(e1) / K
+        t_inf_tc = None
+        if mode == 1:
+            # the same inference through the fused tcgen05 kernel (gather, three
+            # layers and output in one persistent launch) against the mma.sync path
+            S.sisdc_mlp_set_tc(m, False)
+            for _ in range(max(args.warmup, 1)):
+                S.sisdc_mlp_apply(m, r[0], 3e-3, z)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for k in range(K):
+                S.sisdc_mlp_apply(m, r[k], 3e-3, z)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_inf_mma = e0.elapsed_time(e1) / K
+            S.sisdc_mlp_set_tc(m, True)
+            for _ in range(max(args.warmup, 1)):
+                S.sisdc_mlp_apply(m, r[0], 3e-3, z)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for k in range(K):
+                S.sisdc_mlp_apply(m, r[k], 3e-3, z)
+            e1.record(stream)
+            S.sisdc_mlp_sync(m)
+            t_inf_tc = e0.elapsed_time(e1) / K
+            t_inf = t_inf_mma
         if mode == 1:
             clocks = clk.stop()
         f_inf, f_train = mlp_flops(rows, n_in, H, q)
@@ -1196,6 +1221,10 @@ def mlp_arm(args):
                      "infer_ms": t_inf, "infer_rows_per_s": rows / (t_inf * 1e-3),
                      "train_gemm_tflops": f_train / (t_train * 1e-3) / 1e12,
                      "infer_gemm_tflops": f_inf / (t_inf * 1e-3) / 1e12}
+        if t_inf_tc is not None:
+            res[name].update({"infer_ms_tcgen05_fused": t_inf_tc, "infer_rows_per_s_tcgen05": rows / (t_inf_tc * 1e-3),
+                              "infer_gemm_tflops_tcgen05": f_inf / (t_inf_tc * 1e-3) / 1e12,
+                              "infer_ms_mma_sync": t_inf})
         S.sisdc_mlp_destroy(m)
     ctx.close()
     peak = 1940.5

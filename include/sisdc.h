@@ -396,6 +396,21 @@ const char* sisdc_mlp_last_error(sisdc_mlp mlp);
 sisdc_status sisdc_set_solve_log(sisdc_ctx ctx, int level, double* d_r, double* d_dx, double* d_c, int capacity);
 sisdc_status sisdc_get_solve_log_count(sisdc_ctx ctx, int* h_count);
 
+/* Learned initial guess inside the method (not in the paper): with mlp set
+ * (a model created for this level), every correction sweep of level index
+ * `level` (Algorithm 1, SI(1)/SI(2), FP64) runs composed from the
+ * single-operation kernels instead of the persistent sweep kernel, and
+ * before each implicit solve adds the network's correction of the nodal
+ * residual of the warm start, x0 = u^{k-1}_m + z (sisdc_mlp_apply), then
+ * runs Jacobi-PCG from x0 to the same cg_rtol: the result is the plain
+ * method's to the solver tolerance, the CG iteration count is what changes
+ * (sisdc_get_stats).  The network's scalar feature uses c = dt_m nu_tilde of
+ * lambda(u0) (read once per sweep; the solve uses its exact c).  mlp = NULL
+ * restores the persistent kernel.  SISDC_E_ARG for a mixed-precision level,
+ * SISDC_E_STATE when the context captures CUDA graphs (the sweep reads
+ * lambda on the host).  The caller keeps the model alive while it is set. */
+sisdc_status sisdc_set_learned(sisdc_ctx ctx, int level, sisdc_mlp mlp);
+
 /* Solve (I - c L) x = rhs to the context's cg_rtol: mode 0 = Jacobi-PCG from
  * d_x (as sisdc_solve); mode 1 = d_x += MLP(nodal residual), then PCG;
  * mode 2 = flexible CG (Polak-Ribiere) preconditioned by the MLP after the

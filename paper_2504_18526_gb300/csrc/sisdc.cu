@@ -60,6 +60,9 @@ struct sisdc_level_s {
     // child and the y tables below are used
     int rx = 1, ry = 1;
     double *d_Iy = nullptr, *d_Py = nullptr, *d_Ry = nullptr;
+    // learned initial guess of the implicit solves of this level's correction
+    // sweeps (sisdc_set_learned); nullptr = the persistent sweep kernel
+    sisdc_mlp learned = nullptr;
 };
 
 struct sisdc_ctx_s {
@@ -377,9 +380,14 @@ void refresh(sisdc_level_s* lv, const double* u0, const double* U) {
     lv->cache_U = U;
 }
 
+void sweep_learned(sisdc_level_s* lv, const double* u0, double* U, const double* G, double dt, int nsweeps);
+
 void sweep(sisdc_level_s* lv, const double* u0, double* U, const double* G, double dt, int nsweeps) {
     if (!lv->valid || lv->cache_u0 != u0 || lv->cache_U != U) refresh(lv, u0, U);
-    if (nsweeps > 0) run_sweep_kernel(lv, SW_CORRECT, u0, U, G, dt, nsweeps);
+    if (nsweeps > 0) {
+        if (lv->learned) sweep_learned(lv, u0, U, G, dt, nsweeps);
+        else run_sweep_kernel(lv, SW_CORRECT, u0, U, G, dt, nsweeps);
+    }
     if (lv->index < 8) lv->ctx->sweeps[lv->index] += nsweeps;
     lv->valid = true;
     lv->cache_u0 = u0;
@@ -392,6 +400,94 @@ void predict(sisdc_level_s* lv, const double* u0, double* U, double dt) {
     lv->valid = true;
     lv->cache_u0 = u0;
     lv->cache_U = U;
+}
+
+// The correction sweep of the persistent kernel (Algorithm 1 with the SI(1)
+// / SI(2) right-hand sides, FP64) composed on the host from the
+// single-operation kernels, with the learned initial guess before every
+// implicit solve: x0 = u^{k-1}_m + z, z = MLP correction of the nodal
+// residual of the warm start (sisdc_mlp_apply), then Jacobi-PCG from x0 to
+// the same tolerance.  Spectral-radius slots and caches as in the kernel
+// (old slots 0..M = lambda(u0), lambda(U_m) of the previous sweep; new
+// slot m+1 = lambda(u^k_m)).  The network's scalar feature takes
+// c = dt_m nu_tilde(lambda(u0)) (the solve itself uses its exact c).
+void sweep_learned(sisdc_level_s* lv, const double* u0, double* U, const double* G, double dt, int nsweeps) {
+    sisdc_ctx_s* c = lv->ctx;
+    const sisdc_problem& pr = c->prob;
+    const long long NV = lv->NV;
+    const double nd = nu_d(pr), fix = pr.nu_tilde;
+    double* lam_old = lv->lam;
+    double* lam_new = lv->lam + MMAX + 1;
+    auto coef_nut = [&](double dtm, double scale, const double* lam) {
+        // scale * dt_m * nu_tilde(lam)
+        if (fix > 0.0) return Coef{scale * dtm * fix, 0.0, nullptr};
+        return Coef{scale * dtm * nd, scale * 0.5 * dtm * dtm, lam};
+    };
+    for (int k = 0; k < nsweeps; ++k) {
+        double lam0 = 0.0;
+        check(c, cudaMemcpyAsync(&lam0, lam_old, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "lambda read");
+        check(c, cudaStreamSynchronize(c->stream), "sync");
+        check(c, launch_quad(lv->F, 0, lv->Qb, lv->tab.wnn.data(), lv->M, dt, NV, c->stream), "quad kernel");
+        c->launches++;
+        for (int m = 0; m < lv->M; ++m) {
+            const double dtm = dt * lv->tab.dtau[m];
+            const double* up = m ? Um(lv, U, m - 1) : u0;
+            double* um = Um(lv, U, m);
+            const double* Qm = lv->Qb + (long long)m * NV;
+            const double* Gm = G ? G + (long long)m * NV : nullptr;
+            double* LUm = lv->LU + (long long)m * NV;
+            double* CCm = lv->CC + (long long)m * NV;
+            if (dtm == 0.0) {                                    // Lobatto t_1 = t_0
+                Terms t;
+                t.add(up, 1.0);
+                t.add(Qm, 1.0);
+                if (Gm) t.add(Gm, 1.0);
+                k_lin(lv, um, t);
+            } else {
+                const double* lcur = m == 0 ? lam_old : lam_new + m;   // lambda(u^k_{m-1})
+                const Coef cnew = coef_nut(dtm, 1.0, lcur);
+                const double cfeat = dtm * (fix > 0.0 ? fix : nd + 0.5 * dtm * lam0 * lam0);
+                Terms t1;
+                t1.add(up, 1.0);
+                t1.add(Qm, 1.0);
+                if (Gm) t1.add(Gm, 1.0);
+                const Coef cold = coef_nut(dtm, -1.0, lam_old + m);
+                t1.add(LUm, cold.a0, cold.a2, cold.lam);
+                Terms t2 = t1;
+                if (m > 0) t1.add(lv->dC, dtm);
+                // stage 1: r0 = b - (x0 - c L x0) with the cached L x0, guess, solve
+                {
+                    Terms tr = t1;
+                    tr.add(um, -1.0);
+                    tr.add(LUm, cnew.a0, cnew.a2, cnew.lam);
+                    k_lin(lv, lv->cg_r, tr);
+                    const sisdc_status st = sisdc_mlp_apply(lv->learned, lv->cg_r, cfeat, um, 1);
+                    if (st != SISDC_OK) throw Fail{st};
+                    k_pcg(lv, um, t1, cnew);
+                }
+                if (pr.si_stages == 2) {
+                    k_conv(lv, um, lv->tmpc, nullptr);           // c(u^(1))
+                    t2.add(lv->tmpc, dtm);
+                    t2.add(CCm, -dtm);                            // c(u^{k-1}_m)
+                    k_lap(lv, um, lv->cg_p, APPLY_LAP);           // L x0 (x0 = u^(1))
+                    Terms tr = t2;
+                    tr.add(um, -1.0);
+                    tr.add(lv->cg_p, cnew.a0, cnew.a2, cnew.lam);
+                    k_lin(lv, lv->cg_r, tr);
+                    const sisdc_status st = sisdc_mlp_apply(lv->learned, lv->cg_r, cfeat, um, 1);
+                    if (st != SISDC_OK) throw Fail{st};
+                    k_pcg(lv, um, t2, cnew);
+                }
+            }
+            // node end: f(u^k_m), c(u^k_m) with its change, L u^k_m, lambda(u^k_m)
+            run_sweep_kernel(lv, SW_FEVAL, um, lv->U, nullptr, 1.0, 0, lv->F + (long long)m * NV);
+            check(c, cudaMemsetAsync(lam_new + m + 1, 0, sizeof(double), c->stream), "memset");
+            k_conv(lv, um, nullptr, lam_new + m + 1, CONV_DELTA, CCm, lv->dC);
+            k_lap(lv, um, LUm, APPLY_LAP);
+        }
+        check(c, cudaMemcpyAsync(lam_old + 1, lam_new + 1, lv->M * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream), "lambda slots");
+    }
 }
 
 // r = G - F^nn(U) (G may be null); needs valid caches
@@ -1206,6 +1302,21 @@ sisdc_status sisdc_set_solve_log(sisdc_ctx c, int level, double* d_r, double* d_
     c->log_c = d_c;
     c->log_cap = d_r ? capacity : 0;
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return SISDC_OK;
+}
+
+sisdc_status sisdc_set_learned(sisdc_ctx c, int level, sisdc_mlp mlp) {
+    if (!c || level < 0 || level >= (int)c->levels.size()) return SISDC_E_ARG;
+    sisdc_level_s* lv = c->levels[level];
+    if (mlp) {
+        if (lv->mix) return fail(c, SISDC_E_ARG, "the learned sweep runs the FP64 form only");
+        if (c->prob.use_graph)
+            return fail(c, SISDC_E_STATE, "the learned sweep runs eagerly (use_graph = 0): it reads lambda(u0) "
+                                          "on the host once per sweep");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SISDC_E_CUDA, cudaGetErrorString(e));
+    lv->learned = mlp;
     return SISDC_OK;
 }
 

@@ -126,6 +126,7 @@ def load():
         "sisdc_mlp_sync": (c_int, [c_void_p]),
         "sisdc_set_solve_log": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int]),
         "sisdc_get_solve_log_count": (c_int, [c_void_p, P(c_int)]),
+        "sisdc_set_learned": (c_int, [c_void_p, c_int, c_void_p]),
         "sisdc_solve_learned": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_int, P(c_int)]),
         "sisdc_solve_noalloc": (c_int, [P(sisdc_level_desc), c_int, c_double, c_void_p, c_void_p, c_double,
                                         c_int, c_void_p, P(c_int), ctypes.c_char_p, c_int]),
@@ -383,6 +384,10 @@ def sisdc_mlp_sync(mlp):
 
 def sisdc_set_solve_log(ctx, level, r=None, dx=None, cs=None, capacity=0):
     _check(load().sisdc_set_solve_log(ctx, level, _ptr(r), _ptr(dx), _ptr(cs), capacity), ctx)
+
+
+def sisdc_set_learned(ctx, level, mlp=None):
+    _check(load().sisdc_set_learned(ctx, level, mlp), ctx)
 
 
 def sisdc_get_solve_log_count(ctx):
