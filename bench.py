@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--per-instance", type=int, default=0,
                     help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--learned", action="store_true",
+                    help="train the element-patch network on logged solves and time the learned initial guess")
+    ap.add_argument("--learn-solves", type=int, default=10000, help="--learned: logged solves to train on")
+    ap.add_argument("--learn-chunk", type=int, default=400, help="--learned: solves logged per training epoch")
     ap.add_argument("--cfls", type=float, nargs="*", default=[64, 32, 16, 8, 4],
                     help="paper_convdiff: CFL numbers of the iteration study")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -1128,6 +1132,121 @@ def paper_convdiff_arm(args):
                       "seconds": time.perf_counter() - t0}))
 
 
+def learned_arm(args):
+    """The learned initial guess inside the method on the Navier-Stokes shear
+    layer (128^2 elements, P = 5/3): the network (325 -> 112 -> 112 -> 36,
+    BF16) is trained on the GPU on about 10^4 implicit solves logged from the
+    plain method's own fine-level sweeps (chunks of logged solves, one Adam
+    epoch per chunk); then the same window of time steps runs with the plain
+    persistent sweep kernel (CUDA graph), the plain composed sweep (eager)
+    and the learned composed sweep, each against an FP64 reference at dt/4:
+    time, CG iterations per solve and L2 error."""
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import inputs, sisdc as S
+    from paper_2504_18526_gb300.build import build
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build()
+    S.load()
+    w = workload(args)
+    stream = torch.cuda.Stream(device=dev)
+    fine = len(w["levels"]) - 1
+
+    def ctx_of(graph):
+        return S.Context(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, cg_maxit=2000, use_graph=graph)
+
+    ctx = ctx_of(0)
+    nc, n, M = ctx.info(-1)
+    hx, hy = np.zeros(n), np.zeros(n)
+    S.sisdc_level_coords(ctx.levels[-1], hx, hy)
+    lv = w["levels"][-1]
+    shp = (lv["nel"][1], lv["nel"][0], lv["P"] + 1, lv["P"] + 1)
+    u0, dt = initial_data(w, hx.reshape(shp), hy.reshape(shp))
+    ncyc, start = w["ncycles"], S.START_IDS[w["start"]]
+    nv = nc * n
+    # ---- training on logged solves of the plain method ----------------------
+    chunk = max(16, min(args.learn_chunk, 600))
+    lr_ = torch.zeros((chunk, nv), dtype=torch.float64, device=dev)
+    ldx = torch.zeros_like(lr_)
+    lc = torch.zeros(chunk, dtype=torch.float64, device=dev)
+    m = S.sisdc_mlp_create(ctx.levels[fine], 112, seed=11, bf16=1)
+    u = torch.from_numpy(np.ascontiguousarray(u0)).to(dev)
+    trained, steps_run, t_log, t_train = 0, 0, 0.0, 0.0
+    while trained < args.learn_solves:
+        S.sisdc_set_solve_log(ctx.ctx, fine, lr_, ldx, lc, chunk)
+        t0 = time.perf_counter()
+        while S.sisdc_get_solve_log_count(ctx.ctx) < chunk:
+            S.sisdc_step(ctx.ctx, u, steps_run * dt, dt, ncyc, start, 1)
+            steps_run += 1
+        t_log += time.perf_counter() - t0
+        cs = lc.cpu().numpy()
+        keep = np.nonzero((torch.abs(ldx).amax(dim=1).cpu().numpy() > 0) & (cs > 0))[0]
+        t0 = time.perf_counter()
+        if len(keep):
+            S.sisdc_mlp_train(m, lr_[keep].contiguous(), ldx[keep].contiguous(), cs[keep], len(keep), 1, 1e-3)
+        torch.cuda.synchronize()
+        t_train += time.perf_counter() - t0
+        trained += len(keep)
+    S.sisdc_set_solve_log(ctx.ctx, fine)
+    del lr_, ldx
+    torch.cuda.empty_cache()
+    # ---- the window: reference, plain kernel, plain composed, learned --------
+    win = max(2, args.steps)
+    ustart = u.clone()
+    ref = ctx_of(1)
+    ur = ustart.clone()
+    for k in range(4 * win):
+        S.sisdc_step(ref.ctx, ur, 0.0, dt / 4, 6, start, 1)
+    S.sisdc_sync(ref.ctx)
+    ref.close()
+    forms = {}
+    zero = S.sisdc_mlp_create(ctx.levels[fine], 112, seed=12, bf16=1)
+    npar = S.sisdc_mlp_info(zero)[3]
+    S.sisdc_mlp_params(zero, set_=np.zeros(npar, dtype=np.float32))   # correction z = r (no learning)
+    for name, graph, model in (("fp64_plain_kernel", 1, None), ("fp64_composed_identity_guess", 0, zero),
+                               ("fp64_composed_learned_guess", 0, m)):
+        c2 = ctx_of(graph)
+        if model is not None:
+            S.sisdc_set_learned(c2.ctx, fine, model)
+        uf = ustart.clone()
+        for _ in range(args.warmup):
+            S.sisdc_step(c2.ctx, uf, 0.0, dt, ncyc, start, 1)
+        S.sisdc_sync(c2.ctx)
+        uf.copy_(ustart)
+        S.sisdc_reset_stats(c2.ctx)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for _ in range(win):
+            S.sisdc_step(c2.ctx, uf, 0.0, dt, ncyc, start, 1)
+        a1.record(stream)
+        S.sisdc_sync(c2.ctx)
+        tms = a0.elapsed_time(a1)
+        st = S.sisdc_get_stats(c2.ctx)
+        err = float(torch.linalg.vector_norm(uf - ur) / torch.linalg.vector_norm(ur))
+        forms[name] = {"ms_per_step": tms / win, "cg_iters_per_solve": st["cg_iters"] / max(1, st["cg_solves"]),
+                       "cg_solves": st["cg_solves"], "rel_l2_error_vs_reference": err}
+        if model is not None:
+            S.sisdc_set_learned(c2.ctx, fine, None)
+        c2.close()
+    S.sisdc_mlp_destroy(zero)
+    S.sisdc_mlp_destroy(m)
+    ctx.close()
+    plain = forms["fp64_plain_kernel"]
+    print(json.dumps({
+        "metric": "learned initial guess: CG iterations and time at equal error", "workload": args.workload,
+        "training": {"solves": trained, "steps_logged": steps_run, "chunk": chunk, "log_s": t_log,
+                     "train_s": t_train, "network": "325-112-112-36 BF16 (tcgen05 inference)"},
+        "window_steps": win, "forms": forms,
+        "error_ratio_learned_over_plain": forms["fp64_composed_learned_guess"]["rel_l2_error_vs_reference"] /
+        max(1e-300, plain["rel_l2_error_vs_reference"]),
+        "iteration_ratio_learned_over_identity": forms["fp64_composed_learned_guess"]["cg_iters_per_solve"] /
+        max(1e-300, forms["fp64_composed_identity_guess"]["cg_iters_per_solve"]),
+        "time_ratio_learned_over_plain_kernel": forms["fp64_composed_learned_guess"]["ms_per_step"] /
+        plain["ms_per_step"]}))
+
+
 def mlp_flops(rows, n_in, H, q):
     """GEMM flops of one inference (forward) and one training step (forward,
     the five backward products) of the n_in -> H -> H -> q network."""
@@ -1271,6 +1390,8 @@ if __name__ == "__main__":
         stability_arm(a)
     elif a.workload == "paper_convdiff":
         paper_convdiff_arm(a)
+    elif a.learned:
+        learned_arm(a)
     elif a.workload == "mlp_ns_level":
         mlp_arm(a)
     else:

@@ -84,3 +84,27 @@ def test_mlp_flop_counts():
 def test_whole_job_value_weak_scaling():
     assert bench.whole_job_value(1000.0, 10, 1, 2.0) == 1000.0 * 10 / 2e-3
     assert bench.whole_job_value(1000.0, 10, 4, 2.0) == 4 * bench.whole_job_value(1000.0, 10, 1, 2.0)
+
+
+def test_converged_count_ten_percent_rule():
+    """errs[k] = error after k+1 iterations; converged at the first count
+    after which one more iteration changes the error by less than 10 %."""
+    assert bench.converged_count([1.0, 0.5, 0.46, 0.45]) == 2
+    assert bench.converged_count([1.0, 0.95]) == 1
+    assert bench.converged_count([1.0, 0.5, 0.2]) is None
+
+
+def test_oracle_sample_grid_bounded():
+    """Workloads whose fine level exceeds the CPU baseline's size bound are
+    sampled on a coarser element grid of the same physics."""
+    import argparse
+    a = argparse.Namespace(workload="euler256", small=False, oracle_nel=0)
+    assert bench.oracle_nel_for(a) == 64
+    a = argparse.Namespace(workload="burgers2d", small=False, oracle_nel=0)
+    assert bench.oracle_nel_for(a) == 0
+
+
+def test_kernel_digest_tracks_sources():
+    d1 = bench.kernel_digest(bench.ENS_KERNEL_SOURCES)
+    assert d1 == bench.kernel_digest(bench.ENS_KERNEL_SOURCES) and len(d1) == 16
+    assert d1 != bench.kernel_digest(bench.SWEEP_KERNEL_SOURCES)
