@@ -692,14 +692,14 @@ struct EnsSweeper {
             }
             __syncthreads();
             if (act) {
-                double s = 0.0, t = 0.0;          // the two derivative sums, interleaved
+                double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < NQ; ++k) {
-                    s += sD[i * NQ + k] * sFx[j * NQ + k];
-                    t += sD[j * NQ + k] * sFy[k * NQ + i];
-                }
+                for (int k = 0; k < NQ; ++k) s += sD[i * NQ + k] * sFx[j * NQ + k];
                 double cv = -I.sx * s;
-                cv -= I.sy * t;
+                s = 0.0;
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) s += sD[j * NQ + k] * sFy[k * NQ + i];
+                cv -= I.sy * s;
                 const double* fc = sf + (size_t)le * TRS;
                 if (i == 0) cv += fc[j];
                 if (i == NQ - 1) cv += fc[NQ + j];

@@ -70,26 +70,24 @@ __device__ __forceinline__ void sipg_face(const GG& g, const V* vo, const V* vn,
 //   DIM*NQ + [0, 4)    x faces: left jump, left average, right jump, right average
 //   DIM*NQ + [4, 8)    y faces, same order (2D)
 // sipg_opA_coeff gives the coefficient values.
-// The sums run in two interleaved partial sums per direction (stiffness
-// terms, face terms), so that consecutive FMAs do not wait on each other.
 template <int NQ, int DIM, class V>
 __device__ __forceinline__ V sipg_opA_pre(int i, int j, const V* u, const V* f, const V* cf) {
     constexpr int Q = DIM == 2 ? NQ * NQ : NQ;
     const V* cx = cf + DIM * NQ * Q;
-    V ax = V(0), bx = V(0);
+    V ax = V(0);
 #pragma unroll
     for (int k = 0; k < NQ; ++k) ax += cf[k * Q] * u[j * NQ + k];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) bx += cx[s * Q] * f[s * NQ + j];
+    for (int s = 0; s < 4; ++s) ax += cx[s * Q] * f[s * NQ + j];
     if constexpr (DIM == 1) {
-        return ax + bx;
+        return ax;
     } else {
-        V ay = V(0), by = V(0);
+        V ay = V(0);
 #pragma unroll
         for (int k = 0; k < NQ; ++k) ay += cf[(NQ + k) * Q] * u[k * NQ + i];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) by += cx[(4 + s) * Q] * f[(4 + s) * NQ + i];
-        return (ax + bx) + (ay + by);
+        for (int s = 0; s < 4; ++s) ay += cx[(4 + s) * Q] * f[(4 + s) * NQ + i];
+        return ax + ay;
     }
 }
 
@@ -102,7 +100,7 @@ template <int NQ, class V>
 __device__ __forceinline__ void sipg_opA_pre_xy(int i, int j, const V* u, const V* f, const V* cf, V& X, V& Y) {
     constexpr int Q = NQ * NQ;
     const V* cx = cf + 2 * NQ * Q;
-    V ax = V(0), ay = V(0), bx = V(0), by = V(0);
+    V ax = V(0), ay = V(0);
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
         ax += cf[k * Q] * u[j * NQ + k];
@@ -110,11 +108,11 @@ __device__ __forceinline__ void sipg_opA_pre_xy(int i, int j, const V* u, const 
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-        bx += cx[s * Q] * f[s * NQ + j];
-        by += cx[(4 + s) * Q] * f[(4 + s) * NQ + i];
+        ax += cx[s * Q] * f[s * NQ + j];
+        ay += cx[(4 + s) * Q] * f[(4 + s) * NQ + i];
     }
-    X = ax + bx;
-    Y = ay + by;
+    X = ax;
+    Y = ay;
 }
 
 // geometry of the unit element h_x = h_y = 2 (penalty 2 NQ^2 / h)
@@ -148,20 +146,16 @@ template <int NQ, class V>
 __device__ __forceinline__ void sipg_face_pre(const V* vo, const V* vn, int f, const V* Dh, V& jump, V& avg) {
     const V* ro = Dh + f * NQ;
     const V* rn = Dh + (f ^ 1) * NQ;
-    V od = V(0), nd = V(0), oe = V(0), ne = V(0);
+    V od = V(0), nd = V(0);
 #pragma unroll
-    for (int q = 0; q < NQ; q += 2) {
+    for (int q = 0; q < NQ; ++q) {
         od += ro[q] * vo[q];
         nd += rn[q] * vn[q];
-        if (q + 1 < NQ) {
-            oe += ro[q + 1] * vo[q + 1];
-            ne += rn[q + 1] * vn[q + 1];
-        }
     }
     const int end = (f & 1) ? NQ - 1 : 0;
     const V ov = vo[end], nv = vn[NQ - 1 - end];
     jump = (f & 1) ? ov - nv : nv - ov;
-    avg = (od + oe) + (nd + ne);
+    avg = od + nd;
 }
 
 }  // namespace sisdc
