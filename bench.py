@@ -54,7 +54,9 @@ def parse():
                     help="train the element-patch network on logged solves and time the learned initial guess")
     ap.add_argument("--learn-solves", type=int, default=10000, help="--learned: logged solves to train on")
     ap.add_argument("--learn-chunk", type=int, default=400, help="--learned: solves logged per training epoch")
-    ap.add_argument("--cfls", type=float, nargs="*", default=[64, 32, 16, 8, 4],
+    ap.add_argument("--part", default="all", choices=["all", "table", "study"],
+                    help="paper_convdiff: the error table, the CFL iteration study, or both")
+    ap.add_argument("--cfls", type=float, nargs="*", default=[64, 32, 16, 8, 4, 2, 1],
                     help="paper_convdiff: CFL numbers of the iteration study")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-nel", type=int, default=0, help=argparse.SUPPRESS)
@@ -1036,7 +1038,7 @@ def convdiff_run(S, dev, nels, P, Ms, nu, cfl, ncycles, start="cascade", T=5.0, 
     """One run of u_t + u_x = nu u_xx on the periodic unit interval to time T
     (the wave packet), levels with nels[l] elements of degree P and Ms[l]
     Radau-Right nodes, dt from the CFL number on the finest grid
-    (dx = dx_e / (2 P^2), lambda = 1), ncycles V-cycles + post-sweep per step
+    (dx = dx_e / (2 delta(P)), lambda = 1), ncycles V-cycles + post-sweep per step
     (one level: predictor + ncycles sweeps).  Returns (GLL L2 error at T,
     steps); the error is inf when the run blew up."""
     import math
@@ -1049,7 +1051,7 @@ def convdiff_run(S, dev, nels, P, Ms, nu, cfl, ncycles, start="cascade", T=5.0, 
     nc, n, M = ctx.info(-1)
     X = np.zeros(n)
     S.sisdc_level_coords(ctx.levels[-1], X, None)
-    dx = (1.0 / nels[-1]) / (2.0 * P * P)
+    dx = (1.0 / nels[-1]) / (2.0 * inputs.cfl_delta(P))
     nsteps = int(math.ceil(T / (cfl * dx) - 1e-9))
     dt = T / nsteps
     du = torch.from_numpy(inputs.wave_packet(X, 0.0, nu).ravel().copy()).to(dev)
@@ -1100,18 +1102,19 @@ def paper_convdiff_arm(args):
     S.load()
     t0 = time.perf_counter()
     table = {}
-    for mesh in CONVDIFF_TABLE_MESHES:
+    for mesh in (CONVDIFF_TABLE_MESHES if args.part in ("all", "table") else ()):
         for cfl in CONVDIFF_TABLE_CFLS:
             e, n = convdiff_run(S, dev, mesh, 12, (3, 5, 7), 1e-3, cfl, 10)
             table["%d,%d,%d@%d" % (mesh + (cfl,))] = {"error": e, "steps": n}
     orders = {}
-    for k in range(1, len(CONVDIFF_TABLE_MESHES)):
+    for k in (range(1, len(CONVDIFF_TABLE_MESHES)) if table else ()):
         for cfl in CONVDIFF_TABLE_CFLS:
             a = table["%d,%d,%d@%d" % (CONVDIFF_TABLE_MESHES[k - 1] + (cfl,))]["error"]
             b = table["%d,%d,%d@%d" % (CONVDIFF_TABLE_MESHES[k] + (cfl,))]["error"]
             orders["space %s@%d" % (CONVDIFF_TABLE_MESHES[k], cfl)] = math.log2(a / b)
     study = {}
-    for nu, nels, Ms in ((1e-3, (16, 32, 64), (3, 5, 7)), (0.0, (32, 64), (5, 7))):
+    for nu, nels, Ms in (((1e-3, (16, 32, 64), (3, 5, 7)), (0.0, (32, 64), (5, 7)))
+                         if args.part in ("all", "study") else ()):
         for cfl in args.cfls:
             ml, sd = [], []
             for C in range(1, 13):

@@ -28,6 +28,7 @@ namespace sisdc {
 namespace {
 
 constexpr int TILE_M = 128;
+constexpr int THREADS = 512;                     // 16 warps: 4 per TMEM lane quarter
 constexpr uint32_t PANEL_A = TILE_M * 128;      // bytes of one 64-wide K panel of a 128-row tile
 constexpr uint32_t TMEM_COLS = 128;
 
@@ -41,11 +42,11 @@ __host__ __device__ inline Layout layout(int nP1, int H, int N3) {
     L.w1 = o; o += (uint32_t)nP1 * H * 128;
     L.w2 = o; o += 2u * H * 128;
     L.w3 = o; o += 2u * N3 * 128;
-    L.xs = o; o += PANEL_A;
+    L.xs = o; o += 2 * PANEL_A;                  // double-buffered gather panels
     L.hs = o; o += 2 * PANEL_A;
     L.bias = o; o += (uint32_t)(2 * H + N3) * 4;
     o = (o + 15) & ~15u;
-    L.bars = o; o += 32;
+    L.bars = o; o += 64;
     L.total = o;
     return L;
 }
@@ -55,9 +56,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const __grid_constant__ CUtensorMap m1,
-                                                       const __grid_constant__ CUtensorMap m2,
-                                                       const __grid_constant__ CUtensorMap m3) {
+// Threads: 16 warps.  Warp w reads TMEM lane quarter w % 4 (rows 32 (w % 4) ..
+// + 31) and takes the 16-column accumulator chunks c with c % 4 == w / 4 in
+// the epilogues; all threads gather the patch panels.  Layer 1 runs over the
+// K panels with two gather buffers: panel p is gathered into buffer p % 2
+// while the MMAs of panel p - 1 run; a buffer is refilled only after the
+// commit of the MMAs that read it has arrived on that buffer's barrier.
+__global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const MlpTcArgs a, const __grid_constant__ CUtensorMap m1,
+                                                           const __grid_constant__ CUtensorMap m2,
+                                                           const __grid_constant__ CUtensorMap m3) {
     extern __shared__ uint8_t smraw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const Layout L = layout(a.nP1, a.H, a.N3);
@@ -71,9 +78,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
     float* sb3 = sb2 + a.H;
     uint64_t* tma_bar = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* mma_bar = tma_bar + 1;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mma_bar + 1);
+    uint64_t* xbar = tma_bar + 2;                // [2]: MMAs that read gather buffer b are done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tma_bar + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, cgrp = warp >> 2;
     for (int t = tid; t < a.H; t += blockDim.x) {
         sb1[t] = a.b1[t];
         sb2[t] = a.b2[t];
@@ -82,6 +91,8 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
     if (tid == 0) {
         tc::mbar_init(tma_bar, 1);
         tc::mbar_init(mma_bar, 1);
+        tc::mbar_init(xbar, 1);
+        tc::mbar_init(xbar + 1, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(tslot, TMEM_COLS);
@@ -102,35 +113,35 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
     }
     bool ok = __syncthreads_and(tc::mbar_wait(tma_bar, 0)) != 0;
     uint32_t mph = 0;
+    uint32_t xcommit[2] = {0, 0}, xwait[2] = {0, 0};   // commits to / waits consumed on xbar[b]
     const uint32_t id12 = tc::idesc_bf16_f32(TILE_M, a.H);
     const uint32_t id3 = tc::idesc_bf16_f32(TILE_M, a.N3);
     const int k1 = (a.n_in + 15) / 16, kh = a.H / 16;           // MMA K steps of 16
     const int nel = a.nex * a.ney;
     const long long ntiles = (a.rows + TILE_M - 1) / TILE_M;
+    const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int row_e = quarter * 32 + lane;                      // the epilogue row of this thread
 
     // epilogue of layers 1 and 2: tanh(acc + bias) in BF16 into the A panels Hs
     auto hidden_epilogue = [&](const float* bias) {
-        const int r = warp * 32 + lane;
-        for (int c0 = 0; c0 < a.H; c0 += 16) {
+        for (int c0 = 16 * cgrp; c0 < a.H; c0 += 64) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld16(tq + (uint32_t)c0, v);
             uint32_t w[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) w[k] = pack_bf16(tanhf(v[2 * k] + bias[c0 + 2 * k]), tanhf(v[2 * k + 1] + bias[c0 + 2 * k + 1]));
             uint8_t* panel = Hs + (c0 >> 6) * PANEL_A;
             const int k0 = c0 & 63;
-            *reinterpret_cast<uint4*>(panel + tc::sw128_offset(r, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4*>(panel + tc::sw128_offset(r, k0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<uint4*>(panel + tc::sw128_offset(row_e, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(panel + tc::sw128_offset(row_e, k0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
     };
-    auto issue = [&](const uint8_t* Abase, const uint8_t* Bbase, uint32_t bpanel, int ksteps, int kfirst,
-                     uint32_t idesc, bool first) {
-        // K steps [kfirst, kfirst + ksteps) of panels 64 wide
-        for (int kk = 0; kk < ksteps; ++kk) {
-            const int k = kfirst + kk, p = k >> 2, s = k & 3;
-            const uint64_t ad = tc::sdesc_k_sw128(tc::smem_u32(Abase + p * PANEL_A + s * 32));
-            const uint64_t bd = tc::sdesc_k_sw128(tc::smem_u32(Bbase + p * bpanel + s * 32));
-            tc::mma_bf16(tmem, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+    auto issue = [&](const uint8_t* Bbase, uint32_t bpanel, int ksteps, uint32_t idesc) {
+        for (int k = 0; k < ksteps; ++k) {
+            const int p = k >> 2, s4 = k & 3;
+            const uint64_t ad = tc::sdesc_k_sw128(tc::smem_u32(Hs + p * PANEL_A + s4 * 32));
+            const uint64_t bd = tc::sdesc_k_sw128(tc::smem_u32(Bbase + p * bpanel + s4 * 32));
+            tc::mma_bf16(tmem, ad, bd, idesc, k == 0 ? 0u : 1u);
         }
         tc::mma_commit(mma_bar);
     };
@@ -141,14 +152,27 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
         ok = __syncthreads_and(w && ok) != 0;
         tc::fence_after_sync();
     };
+    // consume the outstanding commit on gather buffer b (at most one)
+    auto drain = [&](int b) {
+        bool w = true;
+        if (xwait[b] < xcommit[b]) {
+            w = tc::mbar_wait(xbar + b, xwait[b] & 1);
+            ++xwait[b];
+        }
+        return w;
+    };
 
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const long long row0 = tile * TILE_M;
         // ---- layer 1: panels of the gathered patch rows ----------------------------
         for (int p = 0; p < a.nP1 && ok; ++p) {
+            const int b = p & 1;
+            uint8_t* Xb = Xs + b * PANEL_A;
+            ok = __syncthreads_and(drain(b) && ok) != 0;      // the MMAs that read Xb are done
+            if (!ok) break;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int c = tid + 128 * i, r = c >> 3, kc = c & 7;
+            for (int i = 0; i < TILE_M * 8 / THREADS; ++i) {
+                const int c = tid + THREADS * i, r = c >> 3, kc = c & 7;
                 const long long grow = row0 + r;
                 const int t0 = 64 * p + 8 * kc;
                 float v[8];
@@ -171,7 +195,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
                         }
                     }
                 }
-                *reinterpret_cast<uint4*>(Xs + tc::sw128_offset(r, 8 * kc)) =
+                *reinterpret_cast<uint4*>(Xb + tc::sw128_offset(r, 8 * kc)) =
                     make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
             }
             tc::fence_async_smem();
@@ -179,16 +203,18 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
             if (tid == 0) {
                 tc::fence_after_sync();
                 const int ks = min(4, k1 - 4 * p);
-                // Xs holds panel p only: its steps start at 0 within the buffer
                 for (int kk = 0; kk < ks; ++kk) {
-                    const uint64_t ad = tc::sdesc_k_sw128(tc::smem_u32(Xs + kk * 32));
+                    const uint64_t ad = tc::sdesc_k_sw128(tc::smem_u32(Xb + kk * 32));
                     const uint64_t bd = tc::sdesc_k_sw128(tc::smem_u32(W1s + (size_t)p * a.H * 128 + kk * 32));
                     tc::mma_bf16(tmem, ad, bd, id12, (p == 0 && kk == 0) ? 0u : 1u);
                 }
-                tc::mma_commit(mma_bar);
+                tc::mma_commit(xbar + b);
             }
-            wait_mma();
+            ++xcommit[b];
         }
+        // all layer-1 MMAs complete (the last commits of both buffers)
+        ok = __syncthreads_and(drain(0) && drain(1) && ok) != 0;
+        tc::fence_after_sync();
         if (!ok) break;
         // ---- layer 2 ---------------------------------------------------------
         hidden_epilogue(sb1);
@@ -197,7 +223,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue(Hs, W2s, (uint32_t)a.H * 128, kh, 0, id12, true);
+            issue(W2s, (uint32_t)a.H * 128, kh, id12);
         }
         wait_mma();
         if (!ok) break;
@@ -208,18 +234,17 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(const MlpTcArgs a, const 
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue(Hs, W3s, (uint32_t)a.N3 * 128, kh, 0, id3, true);
+            issue(W3s, (uint32_t)a.N3 * 128, kh, id3);
         }
         wait_mma();
         if (!ok) break;
         // ---- output: z (+)= r + s (acc + b3) ---------------------------------
         {
-            const int r = warp * 32 + lane;
-            const long long grow = row0 + r;
+            const long long grow = row0 + row_e;
             const float s = grow < a.rows ? a.s[grow] : 0.f;
-            for (int c0 = 0; c0 < a.N3; c0 += 16) {
+            for (int c0 = 16 * cgrp; c0 < a.N3; c0 += 64) {
                 float v[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                tc::tmem_ld16(tq + (uint32_t)c0, v);
                 if (grow < a.rows)
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
@@ -296,7 +321,7 @@ cudaError_t mlp_tc_forward(const MlpTcArgs& a, const void* m1, const void* m2, c
     if (e != cudaSuccess) return e;
     const long long ntiles = (a.rows + TILE_M - 1) / TILE_M;
     const int grid = (int)(ntiles < nsm ? ntiles : nsm);
-    k_mlp_fwd_tc<<<grid, 128, smem, s>>>(a, *reinterpret_cast<const CUtensorMap*>(m1),
+    k_mlp_fwd_tc<<<grid, THREADS, smem, s>>>(a, *reinterpret_cast<const CUtensorMap*>(m1),
                                          *reinterpret_cast<const CUtensorMap*>(m2),
                                          *reinterpret_cast<const CUtensorMap*>(m3));
     return cudaGetLastError();

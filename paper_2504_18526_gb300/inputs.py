@@ -162,10 +162,37 @@ def max_wave_speed(pde, u, gamma=1.4, adv=(1.0, 0.0)):
     raise ValueError(pde)
 
 
+_DELTA = {}
+
+
+def cfl_delta(P):
+    """delta of the CFL definition (Sec. 8): the largest eigenvalue magnitude
+    of the convection problem u_t + u_x = 0 on the standard element [-1, 1]
+    with a one-sided (inflow) Dirichlet condition, in the degree-P GLL
+    collocation discretization -- the derivative matrix on the P+1 GLL
+    nodes with the inflow node removed.  It grows like P^2 (about 0.09-0.15
+    P^2 for P = 4..15)."""
+    if P not in _DELTA:
+        n = P + 1
+        # GLL nodes: -1, 1 and the roots of P_P'
+        inner = np.polynomial.legendre.Legendre.basis(P).deriv().roots().real if P > 1 else np.array([])
+        x = np.concatenate([[-1.0], np.sort(inner), [1.0]])
+        # derivative matrix of the Lagrange basis on x (barycentric weights)
+        bw = np.array([1.0 / np.prod([x[j] - x[k] for k in range(n) if k != j]) for j in range(n)])
+        D = np.zeros((n, n))
+        for i in range(n):
+            for j in range(n):
+                if i != j:
+                    D[i, j] = (bw[j] / bw[i]) / (x[i] - x[j])
+            D[i, i] = -np.sum(D[i])
+        _DELTA[P] = float(np.max(np.abs(np.linalg.eigvals(D[1:, 1:]))))
+    return _DELTA[P]
+
+
 def cfl_dt(cfl, h_elem, P, speed):
-    """dt = CFL * dx / lam_max with dx = h_e / (2 delta), delta = P^2
+    """dt = CFL * dx / lam_max with dx = h_e / (2 delta), delta = cfl_delta(P)
     (the CFL definition of the numerical experiments, Sec. 8)."""
-    return cfl * (h_elem / (2.0 * P * P)) / speed
+    return cfl * (h_elem / (2.0 * cfl_delta(P))) / speed
 
 
 def initial_state(name, X, Y, seed_extra=0):

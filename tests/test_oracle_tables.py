@@ -157,3 +157,20 @@ def test_l2_projection(Pf, Pc):
     assert np.max(np.abs(P @ u - c_ls)) < 1e-12
     ones = np.ones(Pf + 1)
     assert abs(ones @ (wf * (Ix @ (P @ u))) - wf @ u) < 1e-13
+
+
+def test_cfl_delta_is_the_inflow_advection_eigenvalue():
+    """The delta of the CFL definition (Sec. 8: the largest eigenvalue of the
+    convection problem on the standard element with a one-sided Dirichlet
+    condition, ~P^2) as the input recipe computes it, against the oracle's
+    own GLL tables, and its growth like P^2."""
+    import numpy as np
+    from oracle.tables import diff_matrix, gll
+    from paper_2504_18526_gb300 import inputs
+    for P in range(1, 16):
+        x, _ = gll(P)
+        D = diff_matrix(x)
+        want = np.max(np.abs(np.linalg.eigvals(D[1:, 1:])))
+        assert abs(inputs.cfl_delta(P) - want) < 1e-9 * want
+    r = [inputs.cfl_delta(P) / P ** 2 for P in (8, 12, 15)]
+    assert 0.08 < min(r) and max(r) < 0.12
