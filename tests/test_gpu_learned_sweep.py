@@ -5,7 +5,7 @@ the network's correction to the warm start of every implicit solve.
 * with any network the step's result is the plain method's to the solver
   tolerance: with solves to rtol 1e-14 the learned form matches the CPU
   oracle to 1e-12 per step (2D Burgers, Navier-Stokes);
-* a network trained on the plain method's own logged solves (Burgers, CFL 4)
+* a network trained on the plain method's own logged solves (Burgers, CFL 0.5)
   reaches the same tolerance in fewer CG iterations inside the time steps,
   and the state agrees with the plain form's to the solver tolerance.
 """
@@ -68,7 +68,7 @@ def test_learned_sweep_saves_iterations_inside_steps(dev):
     w = inputs.scaled("burgers2d", nel=(8, 8))
     X, Y = oracle_space(w, w["levels"][-1]).coords()
     u0 = inputs.burgers2d_initial(X, Y)
-    dt = inputs.cfl_dt(4.0, 1.0 / 8, 7, inputs.max_wave_speed("burgers", u0))
+    dt = inputs.cfl_dt(0.5, 1.0 / 8, 7, inputs.max_wave_speed("burgers", u0))
     fine = 1
     # training data: the plain method's own fine-level solves
     ctx = S.Context(w, cg_rtol=1e-10, cg_maxit=2000)
@@ -108,7 +108,7 @@ def test_learned_sweep_saves_iterations_inside_steps(dev):
         c2.close()
     S.sisdc_mlp_destroy(m)
     (ip, sp_, up), (il, sl, ul) = res[False], res[True]
-    print("burgers 8x8 CFL 4, 4 steps: plain %d CG iterations in %d solves, learned guess %d in %d"
+    print("burgers 8x8 CFL 0.5, 4 steps: plain %d CG iterations in %d solves, learned guess %d in %d"
           % (ip, sp_, il, sl))
     assert sl == sp_
     assert il < ip
