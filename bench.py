@@ -733,7 +733,7 @@ ENS_KERNEL_SOURCES = ("ens.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh", 
 # group's arrays exceed L2 in both cases), and the digest of the kernel
 # sources it was measured on; traffic is reported as null for any other
 # kernel version or form.
-ENS_TRAFFIC = {"digest": None, "bytes_per_node": None, "P": 8, "form": "fp64"}
+ENS_TRAFFIC = {"digest": "8d9082ba56c91840", "bytes_per_node": 3655.0, "P": 8, "form": "fp64"}
 
 
 def ens_cfg_apply(S, ens, cfg):

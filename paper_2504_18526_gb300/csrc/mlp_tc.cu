@@ -33,7 +33,7 @@ constexpr uint32_t PANEL_A = TILE_M * 128;      // bytes of one 64-wide K panel 
 constexpr uint32_t TMEM_COLS = 128;
 
 struct Layout {
-    uint32_t w1, w2, w3, xs, hs, bias, bars, total;
+    uint32_t w1, w2, w3, xs, hs, bias, nb, bars, total;
 };
 
 __host__ __device__ inline Layout layout(int nP1, int H, int N3) {
@@ -45,6 +45,7 @@ __host__ __device__ inline Layout layout(int nP1, int H, int N3) {
     L.xs = o; o += 2 * PANEL_A;                  // double-buffered gather panels
     L.hs = o; o += 2 * PANEL_A;
     L.bias = o; o += (uint32_t)(2 * H + N3) * 4;
+    L.nb = o; o += TILE_M * 10 * 4;              // per tile row: nine neighbour offsets, 1/s
     o = (o + 15) & ~15u;
     L.bars = o; o += 64;
     L.total = o;
@@ -76,6 +77,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const MlpTcArgs a, co
     float* sb1 = reinterpret_cast<float*>(base + L.bias);
     float* sb2 = sb1 + a.H;
     float* sb3 = sb2 + a.H;
+    int* snb = reinterpret_cast<int*>(base + L.nb);           // [row][9] field offsets (int: NV < 2^31)
+    float* ssi = reinterpret_cast<float*>(snb + TILE_M * 9);   // [row] 1/s
     uint64_t* tma_bar = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* mma_bar = tma_bar + 1;
     uint64_t* xbar = tma_bar + 2;                // [2]: MMAs that read gather buffer b are done
@@ -162,38 +165,65 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const MlpTcArgs a, co
         return w;
     };
 
+    // the gather: a thread always fills 16-byte chunk kc = tid % 8 of a panel
+    // row, for rows tid / 8 and tid / 8 + 64 of the tile
+    constexpr int RPT = TILE_M * 8 / THREADS;                   // rows per thread (2)
+    const int kc = tid & 7, rbase = tid >> 3;
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const long long row0 = tile * TILE_M;
+        // per row: the nine neighbour elements' offsets into the field, and 1/s
+        // (the first barrier of the panel loop publishes them)
+        for (int t = tid; t < TILE_M * 9; t += THREADS) {
+            const int r = t / 9, k = t - r * 9;
+            const long long grow = row0 + r;
+            int off = 0;
+            if (grow < a.rows) {
+                const int comp = (int)(grow / nel), el = (int)(grow - (long long)comp * nel);
+                const int ex = el % a.nex, ey = el / a.nex;
+                const int dy = k / 3 - 1, dx = k % 3 - 1;
+                const int en = ((ey + dy + a.ney) % a.ney) * a.nex + (ex + dx + a.nex) % a.nex;
+                off = (comp * nel + en) * a.q;
+            }
+            snb[t] = off;
+            if (k == 0) ssi[r] = grow < a.rows ? a.sinv[grow] : 0.f;
+        }
         // ---- layer 1: panels of the gathered patch rows ----------------------------
         for (int p = 0; p < a.nP1 && ok; ++p) {
             const int b = p & 1;
             uint8_t* Xb = Xs + b * PANEL_A;
+            // this thread's eight input columns of panel p: (neighbour, node), or
+            // the feature (nb = 9), or padding (nb = 10)
+            int nbk[8], nodek[8];
+            {
+                const int t0 = 64 * p + 8 * kc;
+                int nb = t0 / a.q, node = t0 - nb * a.q;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int t = t0 + e;
+                    nbk[e] = t < 9 * a.q ? nb : (t == 9 * a.q ? 9 : 10);
+                    nodek[e] = node;
+                    if (++node == a.q) {
+                        node = 0;
+                        ++nb;
+                    }
+                }
+            }
             ok = __syncthreads_and(drain(b) && ok) != 0;      // the MMAs that read Xb are done
             if (!ok) break;
 #pragma unroll
-            for (int i = 0; i < TILE_M * 8 / THREADS; ++i) {
-                const int c = tid + THREADS * i, r = c >> 3, kc = c & 7;
-                const long long grow = row0 + r;
-                const int t0 = 64 * p + 8 * kc;
+            for (int i = 0; i < RPT; ++i) {
+                const int r = rbase + 64 * i;
+                const bool in = row0 + r < a.rows;
+                const int* nb9 = snb + r * 9;
+                const float si = ssi[r];
                 float v[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = 0.f;
-                if (grow < a.rows) {
-                    const int comp = (int)(grow / nel), el = (int)(grow - (long long)comp * nel);
-                    const int ex = el % a.nex, ey = el / a.nex;
-                    const float si = a.sinv[grow];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int t = t0 + e;
-                        if (t < 9 * a.q) {
-                            const int nb = t / a.q, node = t - nb * a.q;
-                            const int dy = nb / 3 - 1, dx = nb % 3 - 1;
-                            const int en = ((ey + dy + a.ney) % a.ney) * a.nex + (ex + dx + a.nex) % a.nex;
-                            v[e] = d2f_int(a.field[((long long)comp * nel + en) * a.q + node]) * si;
-                        } else if (t == 9 * a.q) {
-                            v[e] = a.feat;
-                        }
-                    }
+                for (int e = 0; e < 8; ++e) {
+                    const int nb = nbk[e];
+                    float x = 0.f;
+                    if (in && nb < 9) x = d2f_int(__ldg(a.field + nb9[nb] + nodek[e])) * si;
+                    else if (in && nb == 9) x = a.feat;
+                    v[e] = x;
                 }
                 *reinterpret_cast<uint4*>(Xb + tc::sw128_offset(r, 8 * kc)) =
                     make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
@@ -317,6 +347,7 @@ cudaError_t mlp_tc_forward(const MlpTcArgs& a, const void* m1, const void* m2, c
     size_t smem = 0;
     if (!mlp_tc_eligible(a.n_in, a.H, a.q, &smem)) return cudaErrorInvalidValue;
     if (a.nP1 != (a.n_in + 63) / 64 || a.N3 != (a.q + 15) / 16 * 16) return cudaErrorInvalidValue;
+    if (a.rows * (long long)a.q >= (1LL << 31)) return cudaErrorInvalidValue;   // int field offsets
     cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long ntiles = (a.rows + TILE_M - 1) / TILE_M;
