@@ -73,6 +73,7 @@ struct EnsSweeper {
     int solve_parity;
     EnsLocal* L;          // this block's per-instance state [nloc]
     double* dinv_tab;     // this block's Jacobi factors [nloc][Q]
+    float* dinv32;        // the same rounded to FP32 (mixed form)
     int nloc;
     const int* loc_inst;  // this block's instances [nloc]
 
@@ -152,6 +153,7 @@ struct EnsSweeper {
         loc_inst = a.loc_inst + (size_t)blockIdx.x * a.lmax;
         L = reinterpret_cast<EnsLocal*>(a.loc) + (size_t)blockIdx.x * a.lmax;
         dinv_tab = a.loc_dinv + (size_t)blockIdx.x * a.lmax * Q;
+        dinv32 = a.loc_dinv32 + (size_t)blockIdx.x * a.lmax * Q;
         pre = nloc <= ENS_LSMEM;
         if (pre) {
             const int words = (int)(sizeof(EnsInst) / 8);
@@ -312,6 +314,51 @@ struct EnsSweeper {
         }
     }
 
+    // Face traces of a tile's elements from their nodal values in shared memory:
+    // per face f and row k the value at the face node and the half-scaled
+    // normal derivative sum_q Dh[f][q] u(line) -- the two numbers a neighbour
+    // needs to form the SIPG jump and average across that face.
+    __device__ void write_traces(int nle, long long e0, const double* tu, double* T) const {
+        const int per = 4 * NQ;
+        for (int t = threadIdx.x; t < nle * per; t += blockDim.x) {
+            const int l = t / per, rem = t - l * per, f = rem / NQ, k = rem - f * NQ;
+            const double* u = tu + l * Q;
+            const double* ro = sDh + f * NQ;
+            double d = 0.0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) d += ro[q] * u[line_node(f, k, q)];
+            double* o = T + ((e0 + l) * 4 + f) * 2 * NQ;
+            o[k] = u[line_node(f, k, (f & 1) ? NQ - 1 : 0)];
+            o[NQ + k] = d;
+        }
+    }
+
+    // SIPG face data of the new search direction p = z + beta p_old from the
+    // traces of z and p_old (the traces are linear in the nodal values): own
+    // faces also store p's traces for the next iteration
+    __device__ void faces_traced(const EnsInst& I, int nle, long long e0, double beta, const double* Tpold,
+                                 double* Tpcur) {
+        const int per = 4 * NQ;
+        for (int t = threadIdx.x; t < nle * per; t += blockDim.x) {
+            const int l = t / per, rem = t - l * per, f = rem / NQ, k = rem - f * NQ;
+            const long long e = e0 + l, en = neighbour(I, e, f);
+            const long long oo = (e * 4 + f) * 2 * NQ + k, on = (en * 4 + (f ^ 1)) * 2 * NQ + k;
+            double vo = __ldcg(a.tz + oo), dd = __ldcg(a.tz + oo + NQ);
+            double vn = __ldcg(a.tz + on), dn = __ldcg(a.tz + on + NQ);
+            if (beta != 0.0) {
+                vo += beta * __ldcg(Tpold + oo);
+                dd += beta * __ldcg(Tpold + oo + NQ);
+                vn += beta * __ldcg(Tpold + on);
+                dn += beta * __ldcg(Tpold + on + NQ);
+            }
+            Tpcur[oo] = vo;
+            Tpcur[oo + NQ] = dd;
+            double* o = sf + (l * 4 + f) * 2 * NQ;
+            o[k] = (f & 1) ? vo - vn : vn - vo;
+            o[NQ + k] = dd + dn;
+        }
+    }
+
     // (A u) of the thread's node: unit-element sums scaled by the instance's aspect ratio
     template <class V>
     __device__ V opA(const EnsInst& I, const V* tu, const V* tf, const V* cf) const {
@@ -354,7 +401,9 @@ struct EnsSweeper {
                 const double c = dtm * nut(I, dtm);
                 double ms, dg;
                 mass_diag(I, q % NQ, q / NQ, ms, dg);
-                dinv_tab[(size_t)li * Q + q] = 1.0 / (ms + c * dg);
+                const double dv = 1.0 / (ms + c * dg);
+                dinv_tab[(size_t)li * Q + q] = dv;
+                if (MIX) dinv32[(size_t)li * Q + q] = d2f_int(dv);
             }
         }
         for (int li = 0; li < nloc; ++li) {
@@ -365,7 +414,9 @@ struct EnsSweeper {
                 for (int t = threadIdx.x; t < Q; t += blockDim.x) {
                     double ms, dg;
                     mass_diag(I, t % NQ, t / NQ, ms, dg);
-                    dinv_tab[(size_t)li * Q + t] = 1.0 / (ms + c * dg);
+                    const double dv = 1.0 / (ms + c * dg);
+                    dinv_tab[(size_t)li * Q + t] = dv;
+                    if (MIX) dinv32[(size_t)li * Q + t] = d2f_int(dv);
                 }
             if (threadIdx.x == 0) {
                 EnsLocal& s = L[li];
@@ -442,6 +493,12 @@ struct EnsSweeper {
                 acc[0] += mb * mb * dinv;
                 acc[1] += rr * zz;
             }
+            if (a.tz) {                                   // traces of z for the first direction
+                __syncthreads();
+                if (act) su[le * Q + node] = Z[id];
+                __syncthreads();
+                write_traces(nle, e0, su, a.tz);
+            }
         });
         if (!bar()) return false;
         totals(part, 0, [](const EnsLocal&) { return true; }, [&](EnsLocal& s, double v) { s.tol2 = fmax(rtol2 * v, 1e-300); s.fin = isfinite(v); });
@@ -457,6 +514,8 @@ struct EnsSweeper {
         for (int par = 0;; par ^= 1) {
             const double* pold = par ? P1 : P0;
             double* pcur = par ? P0 : P1;
+            const double* Tpold = par ? a.tp1 : a.tp0;
+            double* Tpcur = par ? a.tp0 : a.tp1;
             count_active(cnt, 1);
             tiles<1>(part + (size_t)2 * a.ninst * G, 1, [&](const EnsInst& I, long long e0, int nle, int li, double* acc) {
                 const bool act = le < nle;
@@ -469,10 +528,13 @@ struct EnsSweeper {
                     su[le * Q + node] = pn;
                 }
                 __syncthreads();
-                faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) {
-                    const long long idn = en * Q + nd;
-                    return znew(__ldcg(Z + idn), beta, beta == 0.0 ? 0.0 : __ldcg(pold + idn));
-                });
+                if (a.tz)
+                    faces_traced(I, nle, e0, beta, Tpold, Tpcur);
+                else
+                    faces<double>(I, nle, e0, su, sf, sDh, [&](long long en, int nd) {
+                        const long long idn = en * Q + nd;
+                        return znew(__ldcg(Z + idn), beta, beta == 0.0 ? 0.0 : __ldcg(pold + idn));
+                    });
                 __syncthreads();
                 if (act) {
                     const double Apv = mass_of(I) * pn + c * opA<double>(I, su, sf, sA);
@@ -485,15 +547,21 @@ struct EnsSweeper {
             totals(part + (size_t)2 * a.ninst * G, 0, [](const EnsLocal& s) { return s.act != 0; },
                    [](EnsLocal& s, double v) { s.alpha = s.rz / v; });
             tiles<1>(part + (size_t)3 * a.ninst * G, 1, [&](const EnsInst&, long long e0, int nle, int li, double* acc) {
+                double zz = 0.0;
                 if (le < nle) {
                     const long long id = (e0 + le) * Q + node;
                     const double alpha = L[li].alpha, dinv = dinv_tab[(size_t)li * Q + node];
                     x[id] = __ldcg(x + id) + alpha * __ldcg(pcur + id);
                     const double rr = __ldcg(a.r + id) - alpha * __ldcg(AP + id);
-                    const double zz = rr * dinv;
+                    zz = rr * dinv;
                     a.r[id] = rr;
                     Z[id] = zz;
                     acc[0] += rr * zz;
+                }
+                if (a.tz) {                               // traces of the new z
+                    if (le < nle) su[le * Q + node] = zz;
+                    __syncthreads();
+                    write_traces(nle, e0, su, a.tz);
                 }
             });
             if (!bar()) return false;
@@ -590,17 +658,17 @@ struct EnsSweeper {
                     const bool act = le < nle;
                     const long long id = (e0 + le) * Q + node;
                     const RT betar = (RT)L[li].beta, cr = (RT)L[li].c;
-                    const double* dv = dinv_tab + (size_t)li * Q;
+                    const float* dv = dinv32 + (size_t)li * Q;
                     RT pn = RT(0);
                     if (act) {
-                        pn = pnew<RT>(__ldcg(RF + id), to_v<RT>(dv[node]), betar, betar == RT(0) ? RT(0) : __ldcg(pold + id));
+                        pn = pnew<RT>(__ldcg(RF + id), RT(dv[node]), betar, betar == RT(0) ? RT(0) : __ldcg(pold + id));
                         pcur[id] = pn;
                         ru[le * Q + node] = pn;
                     }
                     __syncthreads();
                     faces<RT>(I, nle, e0, ru, rf, rDh, [&](long long en, int nd) {
                         const long long idn = en * Q + nd;
-                        return pnew<RT>(__ldcg(RF + idn), to_v<RT>(dv[nd]), betar, betar == RT(0) ? RT(0) : __ldcg(pold + idn));
+                        return pnew<RT>(__ldcg(RF + idn), RT(dv[nd]), betar, betar == RT(0) ? RT(0) : __ldcg(pold + idn));
                     });
                     __syncthreads();
                     if (act) {
@@ -618,7 +686,7 @@ struct EnsSweeper {
                     if (le < nle) {
                         const long long id = (e0 + le) * Q + node;
                         const double alpha = L[li].alpha;
-                        const RT alphar = (RT)alpha, dinvr = to_v<RT>(dinv_tab[(size_t)li * Q + node]);
+                        const RT alphar = (RT)alpha, dinvr = RT(dinv32[(size_t)li * Q + node]);
                         x[id] = __ldcg(x + id) + alpha * to_f64(__ldcg(pcur + id));
                         const RT rr = __ldcg(RF + id) - alphar * __ldcg(AP + id);
                         RF[id] = rr;

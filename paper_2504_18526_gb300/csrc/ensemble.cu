@@ -130,8 +130,10 @@ struct sisdc_ens_s {
     std::vector<int> group_of, index_in_group;
     long long total = 0;
     long long maxN = 0;
+    long long maxT = 0;                 // largest level's face-trace array (doubles)
     // shared scratch (launches are serialised on the stream)
     double *cg_r = nullptr, *cg_p = nullptr, *cg_p2 = nullptr, *cg_Ap = nullptr, *cg_rf = nullptr;
+    double *cg_tz = nullptr, *cg_tp0 = nullptr, *cg_tp1 = nullptr;   // FP64 CG face traces
     double* part = nullptr;
     size_t part_cap = 0;
     void* loc = nullptr;
@@ -300,6 +302,7 @@ void build_level(sisdc_ens_s* c, EnsGroup& g, int which, int P, int M, bool fine
     L.Qb = take(MV); L.G = take(MV); L.V = take(MV); L.R = take(MV);
     L.u0 = take(N); L.c0 = take(N); L.dC = take(N); L.tmpc = take(N);
     c->maxN = std::max(c->maxN, N);
+    c->maxT = std::max(c->maxT, L.nel * 8LL * L.nq);
 }
 
 // Tiles of epb elements per instance (never straddling two), owned
@@ -365,7 +368,7 @@ void configure(sisdc_ens_s* c, EnsLevel& L, int epb, int grid) {
     if (nd > c->dinv_cap) {
         cudaFree(c->loc_dinv);
         c->loc_dinv = nullptr;
-        dmalloc(c, &c->loc_dinv, nd);
+        dmalloc(c, &c->loc_dinv, nd + (nd + 1) / 2);         // FP64 factors, then their FP32 copy
         c->dinv_cap = nd;
     }
     if (c->gexec) {
@@ -400,6 +403,7 @@ void run_sweep(sisdc_ens_s* c, EnsGroup& g, int which, int mode, const double* G
     a.lmax = L.lmax;
     a.loc = c->loc;
     a.loc_dinv = c->loc_dinv;
+    a.loc_dinv32 = reinterpret_cast<float*>(c->loc_dinv + c->dinv_cap);
     a.N = L.N;
     a.D = L.d_tab;
     a.K = L.d_tab + L.nq * L.nq;
@@ -416,6 +420,7 @@ void run_sweep(sisdc_ens_s* c, EnsGroup& g, int which, int mode, const double* G
     a.G = G;
     a.F = L.F; a.CC = L.CC; a.LU = L.LU; a.Qb = L.Qb; a.c0 = L.c0; a.dC = L.dC; a.tmpc = L.tmpc;
     a.r = c->cg_r; a.p = c->cg_p; a.p2 = c->cg_p2; a.Ap = c->cg_Ap; a.rf = c->cg_rf;
+    a.tz = c->cg_tz; a.tp0 = c->cg_tp0; a.tp1 = c->cg_tp1;
     a.part = c->part;
     a.bar_count = c->d_bar;
     a.bar_exit = c->d_bar + 1;
@@ -568,6 +573,9 @@ void destroy_all(sisdc_ens_s* c) {
     cudaFree(c->cg_p2);
     cudaFree(c->cg_Ap);
     cudaFree(c->cg_rf);
+    cudaFree(c->cg_tz);
+    cudaFree(c->cg_tp0);
+    cudaFree(c->cg_tp1);
     cudaFree(c->part);
     cudaFree(c->loc);
     cudaFree(c->loc_dinv);
@@ -665,6 +673,9 @@ sisdc_status sisdc_ens_create(const sisdc_ens_instance* inst, int n, const sisdc
         dmalloc(c, &c->cg_p2, c->maxN);
         dmalloc(c, &c->cg_Ap, c->maxN);
         dmalloc(c, &c->cg_rf, c->maxN);
+        dmalloc(c, &c->cg_tz, c->maxT);
+        dmalloc(c, &c->cg_tp0, c->maxT);
+        dmalloc(c, &c->cg_tp1, c->maxT);
     } catch (const Fail& f) {
         destroy_all(c);
         delete c;

@@ -202,6 +202,10 @@ struct EnsArgs {
     int lmax;
     void* loc;              // [grid][lmax] per-block solve state
     double* loc_dinv;       // [grid][lmax][Q] per-block Jacobi factors
+    float* loc_dinv32;      // [grid][lmax][Q] the same factors rounded to FP32 (mixed form)
+    // FP64 CG face traces [element][face][value | derivative][NQ]: of z (tz) and of the
+    // search direction (tp0 / tp1, alternating like p / p2); nullable: faces recomputed
+    double *tz, *tp0, *tp1;
     long long N;            // nodes of the level
     const double *D, *K, *w, *dl;   // degree-P tables; dl = h * (diagonal of the 1D SIPG line operator)
     int mode, nsweeps, stages, M;
