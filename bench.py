@@ -1134,6 +1134,8 @@ def paper_convdiff_arm(args):
                 "mlsdc_errors_per_cycles": ml, "sdc_errors_per_sweeps": sd,
                 "mlsdc_cycles": c_ml, "mlsdc_fine_sweeps": None if c_ml is None else c_ml + 1,
                 "sdc_sweeps": c_sd}
+            print("study nu=%g CFL %g: %s (%.0f s)" % (nu, cfl, json.dumps(study["nu=%g@CFL%g" % (nu, cfl)]),
+                                                      time.perf_counter() - t0), file=sys.stderr, flush=True)
     print(json.dumps({"metric": "paper 1D convection-diffusion studies", "workload": "paper_convdiff",
                       "error_table": table, "orders": orders, "cfl_study": study,
                       "seconds": time.perf_counter() - t0}))
