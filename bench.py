@@ -12,7 +12,9 @@ ABI (sisdc_ens_step): every row of the hot path runs in it.
 
 Other workloads (--workload): burgers2d, euler_vortex, euler256 (the vortex
 on 256^2 elements), ns_shear, convdiff1d (sisdc_step), stability_map,
-mlp_ns_level.
+mlp_ns_level, paper_convdiff (the Sec. 8 convection-diffusion studies),
+burgers_front and sod (the Sec. 8 shock-capturing studies with artificial
+viscosity).
 
 Output: one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores instead (bounded samples of the same workload).
@@ -1141,6 +1143,140 @@ def paper_convdiff_arm(args):
                       "seconds": time.perf_counter() - t0}))
 
 
+BURGERS_FRONT_VARIANTS = (
+    # (name, levels (nel_x, P, M) coarse to fine, start): the rows of the paper's
+    # low-resolution iteration table (Sec. 8, Burgers moving front)
+    ("SDC 40xP8 M7", ((40, 8, 7),), None),
+    ("MLSDC {40,40,40} P8 FMG1", ((40, 8, 3), (40, 8, 5), (40, 8, 7)), "fmg1"),
+    ("MLSDC {10,20,40} P8 FMG1", ((10, 8, 3), (20, 8, 5), (40, 8, 7)), "fmg1"),
+    ("MLSDC {40,40,40} P{2,4,8} FMG1", ((40, 2, 3), (40, 4, 5), (40, 8, 7)), "fmg1"),
+)
+
+
+def shock_run(S, dev, w, levels, start, ncycles, dt, nsteps, rtol=1e-12, timed=False):
+    """One run of a shock-capturing workload (artificial viscosity on every
+    level) with the given levels (nel_x, P, M): nsteps steps of dt, ncycles
+    V-cycles + post-sweep per step (one level: predictor + ncycles sweeps).
+    Returns the final state (numpy, fine level), its coordinates and, when
+    timed, the ms per step of a second, graph-replayed pass."""
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import inputs
+    wl = dict(w)
+    wl["levels"] = [dict(nel=(ne, 1), P=P, M=M) for ne, P, M in levels]
+    ctx = S.Context(wl, cg_rtol=rtol, cg_maxit=20000, use_graph=1)
+    nc, n, M = ctx.info(-1)
+    X = np.zeros(n)
+    Y = np.zeros(n)
+    S.sisdc_level_coords(ctx.levels[-1], X, Y)
+    P = levels[-1][1]
+    shape = (1, levels[-1][0], P + 1, P + 1)
+    X = X.reshape(shape)
+    u0 = inputs.initial_state(w["name"], X, Y.reshape(shape))
+    du = torch.from_numpy(np.ascontiguousarray(u0).ravel().copy()).to(dev)
+    st = S.START_IDS[start or "cascade"]
+    for k in range(nsteps):
+        S.sisdc_step(ctx.ctx, du, k * dt, dt, ncycles, st, 1)
+    S.sisdc_sync(ctx.ctx)
+    u = du.cpu().numpy().reshape((nc,) + shape)
+    ms = None
+    if timed:
+        d2 = torch.from_numpy(np.ascontiguousarray(u0).ravel().copy()).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(nsteps):
+            S.sisdc_step(ctx.ctx, d2, k * dt, dt, ncycles, st, 1)
+        e1.record(stream)
+        S.sisdc_sync(ctx.ctx)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+    ctx.close()
+    return u, X, ms
+
+
+def shock_arm(args):
+    """The paper's shock-capturing experiments with the Persson-Peraire
+    artificial viscosity (Sec. 8): the Burgers moving front (under-resolved,
+    nu = 1e-2, t in [0, 0.1]: fine iterations until convergence per CFL for
+    single-level SDC and three MLSDC variants, the 10 % rule on the L2 error
+    against the exact front away from the periodic seam) and Sod's shock tube
+    (32 steps to t = 0.2, CFL ~ 7: density and velocity errors against the
+    exact Riemann solution after C V-cycles of MLSDC and N sweeps of SDC,
+    and the velocity overshoot)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2504_18526_gb300 import inputs, sisdc as S
+    from paper_2504_18526_gb300.build import build
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    build()
+    S.load()
+    t0 = time.perf_counter()
+    w = dict(inputs.WORKLOADS[args.workload])
+    w["name"] = args.workload
+    out = {"metric": "paper shock-capturing studies", "workload": args.workload}
+    if args.workload == "burgers_front":
+        lo, hi = w["window"]
+        h = (w["hi"][0] - w["lo"][0]) / 40
+        table = {}
+        for name, levels, start in BURGERS_FRONT_VARIANTS:
+            row = {}
+            for cfl in args.cfls:
+                dt0 = inputs.cfl_dt(cfl, h, 8, 2.0)                    # lam_max = 2 u_1 = 2
+                nsteps = int(math.ceil(w["T"] / dt0 - 1e-9))
+                dt = w["T"] / nsteps
+                errs = []
+                for k in range(1, 21):
+                    nc = k - 1 if start is None else k
+                    u, X, _ = shock_run(S, dev, w, levels, start, nc, dt, nsteps)
+                    ex = inputs.burgers_front(X, w["T"], w["nu"])
+                    win = (X >= lo) & (X <= hi)
+                    e = float(np.sqrt(np.mean(((u[0] - ex[0]) ** 2)[np.broadcast_to(win, u[0].shape)])))
+                    errs.append(e if math.isfinite(e) else float("inf"))
+                    if converged_count(errs) or not math.isfinite(errs[-1]):
+                        break
+                c = converged_count(errs)
+                fine = None if c is None else (c if start is None else c + 1)
+                row["%g" % cfl] = {"fine_iterations": fine, "errors": errs, "steps": nsteps}
+            table[name] = row
+            print("front %s: %s (%.0f s)" % (name, {k: v["fine_iterations"] for k, v in row.items()},
+                                              time.perf_counter() - t0), file=sys.stderr, flush=True)
+        out["fine_iterations_until_convergence"] = table
+    else:
+        dt = w["T"] / w["nsteps"]
+        levels = tuple((lv["nel"][0], lv["P"], lv["M"]) for lv in w["levels"])
+        ps, us = inputs._sod_star()
+        res = {}
+        for name, lv, start, counts in (("MLSDC P{3,5} M{5,7} Cascade", levels, "cascade", range(1, 7)),
+                                        ("SDC P5 M7", levels[-1:], None, range(1, 9))):
+            rows = []
+            for k in counts:
+                nc = k - 1 if start is None else k
+                u, X, ms = shock_run(S, dev, w, lv, start, nc, dt, w["nsteps"], timed=(k == 3))
+                ex = inputs.sod_state(X, w["T"])
+                half = np.broadcast_to(X <= 1.0, u[0].shape)
+                v = u[1] / u[0]
+                rows.append({"iterations": k, "fine_sweeps": k if start is None else k + 1,
+                             "rho_l1": float(np.mean(np.abs(u[0] - ex[0])[half])),
+                             "v_l1": float(np.mean(np.abs(v - ex[1] / ex[0])[half])),
+                             "v_max_over_ustar": float(v[half].max() / us),
+                             "ms_per_step": ms})
+            res[name] = rows
+            print("sod %s: %s (%.0f s)" % (name, [(r["iterations"], round(r["rho_l1"], 5)) for r in rows],
+                                            time.perf_counter() - t0), file=sys.stderr, flush=True)
+        out["sod"] = res
+        out["dt"] = dt
+        rho_e, v_e, p_e = inputs.sod_primitive(np.linspace(0.0, 1.0, 4001), w["T"])
+        lam = float(np.max(np.abs(v_e) + np.sqrt(w["gamma"] * p_e / rho_e)))   # lam_max at t = 0.2
+        h = (w["hi"][0] - w["lo"][0]) / levels[-1][0]
+        out["cfl"] = dt * lam / (h / (2.0 * inputs.cfl_delta(levels[-1][1])))
+    out["seconds"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 def learned_arm(args):
     """The learned initial guess inside the method on the Navier-Stokes shear
     layer (128^2 elements, P = 5/3): the network (325 -> 112 -> 112 -> 36,
@@ -1399,6 +1535,8 @@ if __name__ == "__main__":
         stability_arm(a)
     elif a.workload == "paper_convdiff":
         paper_convdiff_arm(a)
+    elif a.workload in ("burgers_front", "sod"):
+        shock_arm(a)
     elif a.learned:
         learned_arm(a)
     elif a.workload == "mlp_ns_level":

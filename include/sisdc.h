@@ -177,6 +177,28 @@ typedef void* (*sisdc_alloc_fn)(size_t bytes, void* cuda_stream, void* user);
 typedef void (*sisdc_release_fn)(void* ptr, size_t bytes, void* cuda_stream, void* user);
 sisdc_status sisdc_set_allocator(sisdc_ctx ctx, sisdc_alloc_fn alloc, sisdc_release_fn release, void* user);
 
+/* Persson-Peraire artificial viscosity in f (Sec. 6, "Spatial
+ * discretization": the diffusion matrix of the DG right-hand side
+ * supplemented by an artificial viscosity; Sec. 8 uses it for the Burgers
+ * moving front with d_s = c_s = 0.5 and for Sod's shock tube with d_s = 2,
+ * c_s = 0.4).  The paper defers the form to its companion; this library's
+ * reading: on every element the orthonormal-Legendre coefficients of the
+ * sensor component `comp` (0 <= comp < ncomp; u_1 for Burgers, the density
+ * for Euler) give s_e = log10(energy of the degree-P modes / total energy);
+ * eps_e = c_s h/P lam_e r(s_e) with h the smaller element side, lam_e the
+ * element's largest convective spectral radius and r = 0 below
+ * s0 - d_s, 1 above s0 + d_s, (1 + sin(pi (s_e - s0) / (2 d_s))) / 2
+ * between, s0 = log10(1/P^4).  f gains div(eps grad u) on every component
+ * (BR1: derivatives lifted with central face values, scaled by eps_e, then
+ * the divergence with central face values), evaluated at every state f is
+ * evaluated at, and nu_tilde gains c_s h/P lam_max.  A correction sweep of
+ * several iterations runs as single-sweep launches.  Must be called before
+ * the first sisdc_create_level (SISDC_E_STATE otherwise); c_s = 0 switches
+ * it off; d_s <= 0, c_s < 0 or a bad component is SISDC_E_ARG.  Levels then
+ * hold M x nel + dim x M x ncomp x nodes more doubles.  Not available with
+ * the learned sweep (sisdc_set_learned). */
+sisdc_status sisdc_set_av(sisdc_ctx ctx, double d_s, double c_s, int comp);
+
 /* Add a level (Sec. 6.1).  Levels must be added from coarse (l = 1) to fine
  * (l = L); adjacent levels must share the element grid (p-coarsening in
  * space, Sec. 6.2) and node kind (p-coarsening in time).  Work arrays are

@@ -178,6 +178,8 @@ class DGSpace:
         hy2 = self.hy / 2.0 if dim == 2 else 1.0
         self.mass = (hy2 * wy)[:, None] * ((self.hx / 2.0) * self.w)[None, :]
         self.diagA = self._diag_A()
+        # artificial viscosity (oracle.av): None, or dict(kappa=d_s, cs=c_s, comp=sensor component)
+        self.av = None
 
     # ---- geometry -------------------------------------------------------
     def coords(self):
@@ -274,13 +276,27 @@ class DGSpace:
         return -self.A(u) / self.mass
 
     def diff(self, u):
-        """Physical diffusion term of f: nu L u, or the Navier-Stokes viscous
-        term (zero for Euler)."""
+        """Diffusion term of f: nu L u, or the Navier-Stokes viscous term
+        (zero for Euler), plus the artificial viscosity term when set."""
         if getattr(self.pde, "viscous", False):
-            return self.visc(u)
-        if self.pde.nu == 0.0:
-            return np.zeros_like(u)
-        return self.pde.nu * self.lap(u)
+            out = self.visc(u)
+        elif self.pde.nu == 0.0:
+            out = np.zeros_like(u)
+        else:
+            out = self.pde.nu * self.lap(u)
+        if self.av is not None:
+            from . import av
+            out = out + av.av_term(self, u, av.viscosity(self, u, **self.av))
+        return out
+
+    @property
+    def av_nu_lam(self):
+        """c_s h / P: the artificial viscosity's share of nu_tilde per unit of
+        lam_max (0 without artificial viscosity)."""
+        if self.av is None:
+            return 0.0
+        from . import av
+        return self.av["cs"] * av.h_min(self) / self.P
 
     # ---- viscous term (BR1) -------------------------------------------------
     def _lift_derivative(self, v, axis, h, sign):

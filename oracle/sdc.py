@@ -14,7 +14,8 @@ and f(u) = conv(u) + diff(u) (Sec. 2, f = -d_x f_c + d_x f_d).
 
 SI operator (Sec. 3.3, eq. H_SI(1)):
     H(u_a, u_b, u_c, dt_m) = dt_m [ c(u_a) + nu_tilde(u_b) L u_c ],
-    nu_tilde(u_b) = nu_d + dt_m / 2 * lam_max(u_b)^2.
+    nu_tilde(u_b) = nu_d + dt_m / 2 * lam_max(u_b)^2
+(plus c_s h / P * lam_max(u_b) with artificial viscosity, oracle.av).
 Predictors SI(1)/SI(2) (eqs. sdc:incremental_predictor_si1/_si2), the
 incremental corrector with Delta H for SI(1)/SI(2) (eqs. DeltaH_SI1,
 DeltaH_SI2) plus the FAS term g (Sec. 4.3, eq. ml-sdc:incremental;
@@ -48,7 +49,8 @@ def nutilde(space, u_b, dtm):
     fix = getattr(space, "nu_tilde_fix", 0.0)
     if fix > 0.0:
         return fix
-    return space.nu_d + 0.5 * dtm * space.lam_max(u_b) ** 2
+    lam = space.lam_max(u_b)
+    return space.nu_d + getattr(space, "av_nu_lam", 0.0) * lam + 0.5 * dtm * lam ** 2
 
 
 def f_eval(space, u):

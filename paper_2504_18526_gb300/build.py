@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(OUT_DIR, "libsisdc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
-SOURCES = (["ops_sipg.cu", "ops_conv.cu", "ops_misc.cu", "tables.cpp", "sisdc.cu", "noalloc.cu", "mlp.cu", "mlp_tc.cu",
+SOURCES = (["ops_sipg.cu", "ops_conv.cu", "ops_misc.cu", "ops_av.cu", "tables.cpp", "sisdc.cu", "noalloc.cu", "mlp.cu", "mlp_tc.cu",
             "sweep_dispatch.cu", "sweep_cd_1dhi.cu", "stab.cu", "ensemble.cu", "ens_lo.cu", "ens_hi.cu", "ens_lo_mix.cu", "ens_hi_mix.cu"] +
            ["sweep_%s_%s%s.cu" % (p, h, m) for p in ("cd", "bu", "eu", "ns") for h in ("lo", "hi") for m in ("", "_mix")])
 

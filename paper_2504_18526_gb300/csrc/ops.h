@@ -79,6 +79,7 @@ struct SweepArgs {
     double nu;              // physical diffusion in f
     double nu_d;            // nu_d of nu_tilde = nu_d + dt_m/2 lam_max^2
     double nu_tilde_fix;    // > 0: constant nu_tilde instead of the formula
+    double nu_lam;          // artificial viscosity's share of nu_tilde per unit of lam_max (c_s h / P)
     double mu, kappa;       // Navier-Stokes viscosity and heat conductivity
     double* FV;             // Navier-Stokes viscous flux scratch [6][N]: F_v^x, F_v^y of
                             // the momentum and energy components
@@ -161,6 +162,25 @@ struct TransferArgs {
     const double* Sy;
 };
 cudaError_t launch_transfer(const TransferArgs& a, cudaStream_t s);
+
+// ---- artificial viscosity (ops_av.cu) ----------------------------------------
+// F_s += div(eps grad U_s) for the n states U_s (each [ncomp][N]), eps per
+// element from the modal decay of component `comp` (Persson-Peraire)
+struct AvArgs {
+    Geo g;
+    int pde;                // convective flux of the spectral radius (NS: Euler's)
+    double gamma, ax, ay;
+    int comp;               // sensor component
+    double s0, kappa;       // sensor threshold log10(1/P^4) and ramp half-width d_s
+    double eps_scale;       // c_s h / P
+    const double* vinv;     // [nq*nq] nodal -> orthonormal Legendre coefficients
+    const double* U;        // [n][ncomp*N]
+    double* F;              // [n][ncomp*N], added to
+    double* eps;            // [n][nel] scratch (the viscosities, kept for inspection)
+    double* grad;           // [n][dim][ncomp*N] scratch
+    int n;
+};
+cudaError_t launch_av(const AvArgs& a, cudaStream_t s);
 
 // diagnostics: scratch holds partials and, at offset ncomp*NORM_BLOCKS*3,
 // the result [ncomp][3] = (L2 norm of u - ref, mass of u, max |u - ref|)

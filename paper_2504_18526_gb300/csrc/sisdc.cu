@@ -63,6 +63,10 @@ struct sisdc_level_s {
     // learned initial guess of the implicit solves of this level's correction
     // sweeps (sisdc_set_learned); nullptr = the persistent sweep kernel
     sisdc_mlp learned = nullptr;
+    // artificial viscosity (sisdc_set_av): modal matrix, per-element
+    // viscosities [M][nel] and BR1 derivatives [M][dim][NV]
+    const double* d_vinv = nullptr;
+    double *av_eps = nullptr, *av_grad = nullptr;
 };
 
 struct sisdc_ctx_s {
@@ -90,6 +94,10 @@ struct sisdc_ctx_s {
     int log_cap = 0;
     int* d_log_count = nullptr;
     int max_grid = 0;
+    // Persson-Peraire artificial viscosity in f (sisdc_set_av)
+    bool av_on = false;
+    double av_kappa = 0.0, av_cs = 0.0;
+    int av_comp = 0;
     // caller's allocator for the level work arrays (sisdc_set_allocator)
     sisdc_alloc_fn ualloc = nullptr;
     sisdc_release_fn urelease = nullptr;
@@ -285,6 +293,39 @@ void k_transfer(sisdc_level_s* fine, int op, const double* in, double* out, int 
 
 
 // ---- method building blocks ----------------------------------------------------
+// the artificial viscosity's share of nu_tilde per unit of lam_max: c_s h / P,
+// h the smaller element side (0 without artificial viscosity)
+double av_nu_lam(const sisdc_level_s* lv) {
+    const sisdc_ctx_s* c = lv->ctx;
+    if (!c->av_on) return 0.0;
+    const double h = lv->desc.dim == 2 ? std::min(lv->geo.hx, lv->geo.hy) : lv->geo.hx;
+    return c->av_cs * h / lv->desc.P;
+}
+
+// F_s += div(eps grad U_s) for the n states U_s, F_s (artificial viscosity of
+// f, evaluated at the same states as the rest of f)
+void av_add(sisdc_level_s* lv, const double* U, double* F, int n) {
+    sisdc_ctx_s* c = lv->ctx;
+    AvArgs a{};
+    a.g = lv->geo;
+    a.pde = c->prob.pde == SISDC_PDE_NS ? SISDC_PDE_EULER : c->prob.pde;
+    a.gamma = c->prob.gamma;
+    a.ax = c->prob.adv[0];
+    a.ay = c->prob.adv[1];
+    a.comp = c->av_comp;
+    a.s0 = std::log10(1.0 / std::pow((double)lv->desc.P, 4));
+    a.kappa = c->av_kappa;
+    a.eps_scale = av_nu_lam(lv);
+    a.vinv = lv->d_vinv;
+    a.U = U;
+    a.F = F;
+    a.eps = lv->av_eps;
+    a.grad = lv->av_grad;
+    a.n = n;
+    check(c, launch_av(a, c->stream), "artificial viscosity kernels");
+    c->launches += 3;
+}
+
 // One cooperative launch of the persistent sweep kernel (sweep.cuh).
 void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, const double* G, double dt,
                       int nsweeps, double* fout = nullptr) {
@@ -298,6 +339,7 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
     a.nu = nu_phys(c->prob);
     a.nu_d = nu_d(c->prob);
     a.nu_tilde_fix = c->prob.nu_tilde;
+    a.nu_lam = av_nu_lam(lv);
     a.mu = c->prob.pde == SISDC_PDE_NS ? c->prob.mu : 0.0;
     a.kappa = kappa_ns(c->prob);
     a.FV = lv->FV;
@@ -370,6 +412,13 @@ void run_sweep_kernel(sisdc_level_s* lv, int mode, const double* u0, double* U, 
         c->ev_used += 2;
     }
     c->launches++;
+    // artificial viscosity: f at the states the kernel just evaluated f at
+    // (every node, or the one state of SW_FEVAL); a correction launch runs
+    // one sweep then (sweep())
+    if (c->av_on) {
+        if (mode == SW_FEVAL) av_add(lv, u0, fout, 1);
+        else av_add(lv, U, lv->F, lv->M);
+    }
 }
 
 // Caches f(U_m), c(U_m), L U_m, c(u0) and the spectral-radius slots of (u0, U).
@@ -386,6 +435,8 @@ void sweep(sisdc_level_s* lv, const double* u0, double* U, const double* G, doub
     if (!lv->valid || lv->cache_u0 != u0 || lv->cache_U != U) refresh(lv, u0, U);
     if (nsweeps > 0) {
         if (lv->learned) sweep_learned(lv, u0, U, G, dt, nsweeps);
+        else if (lv->ctx->av_on)            // f gains its viscosity term between sweeps
+            for (int k = 0; k < nsweeps; ++k) run_sweep_kernel(lv, SW_CORRECT, u0, U, G, dt, 1);
         else run_sweep_kernel(lv, SW_CORRECT, u0, U, G, dt, nsweeps);
     }
     if (lv->index < 8) lv->ctx->sweeps[lv->index] += nsweeps;
@@ -700,6 +751,23 @@ sisdc_status sisdc_set_allocator(sisdc_ctx c, sisdc_alloc_fn alloc, sisdc_releas
     return SISDC_OK;
 }
 
+sisdc_status sisdc_set_av(sisdc_ctx c, double d_s, double c_s, int comp) {
+    if (!c) return SISDC_E_ARG;
+    if (!c->levels.empty()) return fail(c, SISDC_E_STATE, "artificial viscosity must be set before the first level");
+    if (c_s == 0.0) {
+        c->av_on = false;
+        return SISDC_OK;
+    }
+    if (!(d_s > 0.0) || !(c_s > 0.0) || !std::isfinite(d_s) || !std::isfinite(c_s))
+        return fail(c, SISDC_E_ARG, "artificial viscosity: d_s and c_s must be positive and finite");
+    if (comp < 0 || comp >= c->prob.ncomp) return fail(c, SISDC_E_ARG, "artificial viscosity: bad sensor component");
+    c->av_on = true;
+    c->av_kappa = d_s;
+    c->av_cs = c_s;
+    c->av_comp = comp;
+    return SISDC_OK;
+}
+
 sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_level* out) {
     if (!c || !d || !out) return SISDC_E_ARG;
     *out = nullptr;
@@ -770,6 +838,15 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
         delete lv;
         return fail(c, SISDC_E_ARG, "table construction failed");
     }
+    // nodal-to-modal matrix of the artificial-viscosity sensor
+    const size_t off_vinv = htab.size();
+    if (c->av_on) {
+        htab.resize(off_vinv + nq * nq);
+        if (!modal_matrix(d->P, htab.data() + off_vinv)) {
+            delete lv;
+            return fail(c, SISDC_E_ARG, "table construction failed");
+        }
+    }
     // transfers to the coarser level
     std::vector<double> ttab;
     size_t off_Ix = 0, off_Px = 0, off_Rx = 0, off_It = 0, off_Pt = 0, off_Rt = 0, off_one = 0;
@@ -835,7 +912,8 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     const long long NV = lv->NV, MV = (long long)lv->M * NV;
     const long long ntr = (long long)c->prob.ncomp * lv->nel * 2 * d->dim * 2 * nq;
     const long long nfv = c->prob.pde == SISDC_PDE_NS ? 6 * lv->N : 0;
-    const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1) + nfv;
+    const long long nav = c->av_on ? (long long)lv->M * lv->nel + (long long)d->dim * MV : 0;
+    const long long total = 8 * MV + 2 * NV + 3 * NV + 4 * NV + 2 * ntr + 2 * (MMAX + 1) + nfv + nav;
     lv->mem_bytes = total * sizeof(double);
     if (e == cudaSuccess) e = level_alloc(c, &lv->d_mem, lv->mem_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(lv->d_mem, 0, lv->mem_bytes, c->stream);
@@ -860,6 +938,11 @@ sisdc_status sisdc_create_level(sisdc_ctx c, const sisdc_level_desc* d, sisdc_le
     lv->trx = take(ntr); lv->trp = take(ntr);
     lv->lam = take(2 * (MMAX + 1));
     lv->FV = nfv ? take(nfv) : nullptr;
+    if (c->av_on) {
+        lv->av_eps = take((long long)lv->M * lv->nel);
+        lv->av_grad = take((long long)d->dim * MV);
+        lv->d_vinv = lv->d_tab + off_vinv;
+    }
     if (lv->index > 0) {
         double* t = lv->d_tab + htab.size();
         lv->d_Ix = t + off_Ix; lv->d_Px = t + off_Px; lv->d_Rx = t + off_Rx;
@@ -1310,6 +1393,7 @@ sisdc_status sisdc_set_learned(sisdc_ctx c, int level, sisdc_mlp mlp) {
     sisdc_level_s* lv = c->levels[level];
     if (mlp) {
         if (lv->mix) return fail(c, SISDC_E_ARG, "the learned sweep runs the FP64 form only");
+        if (c->av_on) return fail(c, SISDC_E_ARG, "the learned sweep has no artificial viscosity");
         if (c->prob.use_graph)
             return fail(c, SISDC_E_STATE, "the learned sweep runs eagerly (use_graph = 0): it reads lambda(u0) "
                                           "on the host once per sweep");

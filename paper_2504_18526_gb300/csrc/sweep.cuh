@@ -1024,7 +1024,7 @@ struct Sweeper {
     }
 
     __device__ double nut(double dtm, double lam) const {
-        return a.nu_tilde_fix > 0.0 ? a.nu_tilde_fix : a.nu_d + 0.5 * dtm * lam * lam;
+        return a.nu_tilde_fix > 0.0 ? a.nu_tilde_fix : a.nu_d + a.nu_lam * lam + 0.5 * dtm * lam * lam;
     }
     __device__ double* Um(double* U, int m) const { return U + (long long)m * NV; }
     __device__ const double* Um(const double* U, int m) const { return U + (long long)m * NV; }

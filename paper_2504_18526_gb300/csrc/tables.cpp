@@ -446,3 +446,45 @@ bool fds_tables(int P, double h, double* S, double* lam) {
 
 }  // namespace sisdc
 
+
+namespace sisdc {
+
+// Nodal-to-modal matrix of the artificial-viscosity sensor: the inverse of
+// V[i][k] = sqrt((2k+1)/2) P_k(x_i) on the GLL nodes x_i (orthonormal
+// Legendre modes), by Gauss-Jordan elimination with partial pivoting in long
+// double.  out[k * (P+1) + i]: coefficient of mode k from nodal value i.
+bool modal_matrix(int P, double* out) {
+    const int n = P + 1;
+    std::vector<ld> x, w;
+    gll_ld(P, &x, &w);
+    std::vector<ld> A(n * 2 * n, 0.0L);      // [V | I]
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < n; ++k) {
+            ld p, dp;
+            legendre(k, x[i], &p, &dp);
+            A[i * 2 * n + k] = sqrtl((2.0L * k + 1.0L) / 2.0L) * p;
+        }
+        A[i * 2 * n + n + i] = 1.0L;
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabsl(A[r * 2 * n + c]) > fabsl(A[piv * 2 * n + c])) piv = r;
+        if (fabsl(A[piv * 2 * n + c]) < 1e-30L) return false;
+        if (piv != c)
+            for (int k = 0; k < 2 * n; ++k) std::swap(A[c * 2 * n + k], A[piv * 2 * n + k]);
+        const ld d = A[c * 2 * n + c];
+        for (int k = 0; k < 2 * n; ++k) A[c * 2 * n + k] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const ld f = A[r * 2 * n + c];
+            if (f == 0.0L) continue;
+            for (int k = 0; k < 2 * n; ++k) A[r * 2 * n + k] -= f * A[c * 2 * n + k];
+        }
+    }
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i < n; ++i) out[k * n + i] = (double)A[k * 2 * n + n + i];
+    return true;
+}
+
+}  // namespace sisdc

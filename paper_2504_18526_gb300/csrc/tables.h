@@ -29,6 +29,10 @@ void h_transfer_matrices(int Pf, int Pc, int l2, std::vector<double>* I2, std::v
 // of (element block, GLL mass), M-orthonormal; lam[i] ascending.
 bool fds_tables(int P, double h, double* S, double* lam);
 
+// Nodal-to-modal matrix of degree P (orthonormal Legendre modes on the GLL
+// nodes): out[k * (P+1) + i], mode k from nodal value i.
+bool modal_matrix(int P, double* out);
+
 // Per-direction L2 projection from degree Pf to Pc under the fine GLL
 // quadrature: (I^T W_f I)^{-1} I^T W_f, row-major (Pc+1) x (Pf+1).
 std::vector<double> l2_projection_matrix(int Pf, int Pc);

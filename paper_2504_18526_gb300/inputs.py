@@ -62,6 +62,24 @@ WORKLOADS = {
         levels=[dict(nel=(128, 128), P=3, M=3), dict(nel=(128, 128), P=5, M=5)],
         nodes="radau_right", cfl=0.5, nsteps=100, ncycles=3, start="cascade",
         shear_delta=1.0 / 80.0, perturb_amp=0.05),
+    # the viscous Burgers moving front (Sec. 8, the spatially under-resolved case:
+    # 10/20/40 elements of degree 8) as the x-momentum u_1 = w / 2 of the
+    # two-component Burgers system on one element row (u_2 = 0, data constant
+    # in y), with the artificial viscosity d_s = c_s = 0.5
+    "burgers_front": dict(
+        id=7, pde="burgers", dim=2, ncomp=2, nu=1e-2,
+        lo=(-1.0, 0.0), hi=(1.0, 2.0),
+        levels=[dict(nel=(10, 1), P=8, M=3), dict(nel=(20, 1), P=8, M=5), dict(nel=(40, 1), P=8, M=7)],
+        nodes="radau_right", T=0.1, start="fmg1", av=dict(kappa=0.5, cs=0.5, comp=0),
+        window=(-0.75, 0.75)),
+    # Sod's shock tube (Sec. 8: 80 elements of degree 5/3 on [0, 1], M = 7/5, 32
+    # steps to t = 0.2, Cascade start, d_s = 2, c_s = 0.4) mirrored to the
+    # periodic [0, 2] (walls at x = 0 and 1 by symmetry) on one element row
+    "sod": dict(
+        id=8, pde="euler", dim=2, ncomp=4, gamma=1.4,
+        lo=(0.0, 0.0), hi=(2.0, 2.0),
+        levels=[dict(nel=(160, 1), P=3, M=5), dict(nel=(160, 1), P=5, M=7)],
+        nodes="radau_right", T=0.2, nsteps=32, start="cascade", av=dict(kappa=2.0, cs=0.4, comp=0)),
     # 512 independent 2D convection-diffusion problems of mixed sizes and degrees
     "ensemble512": dict(
         id=5, pde="convdiff", dim=2, ncomp=1, ninst=512, nel_range=(8, 48), P_range=(3, 8),
@@ -195,6 +213,95 @@ def cfl_dt(cfl, h_elem, P, speed):
     return cfl * (h_elem / (2.0 * cfl_delta(P))) / speed
 
 
+def burgers_front(X, t, nu=1e-2):
+    """Exact moving front of w_t + (w^2/2)_x = nu w_xx, w = 1 - tanh((x + 0.5 - t) / (2 nu))
+    (Sec. 8), as the state (u_1, u_2) = (w / 2, 0) of the two-component Burgers
+    system, whose x-momentum equation u_t + (u^2)_x = nu u_xx it solves."""
+    X = np.asarray(X, dtype=float)
+    return np.stack([0.5 * (1.0 - np.tanh((X + 0.5 - t) / (2.0 * nu))), np.zeros_like(X)])
+
+
+def _sod_star(gamma=1.4, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1)):
+    """Pressure and velocity between the two nonlinear waves of a Riemann
+    problem of the Euler equations (Newton iteration on the pressure
+    function of the exact solution, both waves as shocks or rarefactions)."""
+    g = gamma
+    (rl, ul, pl), (rr, ur, pr) = left, right
+    cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+
+    def fk(p, rk, pk, ck):
+        if p > pk:                                   # shock
+            A, B = 2.0 / ((g + 1.0) * rk), (g - 1.0) / (g + 1.0) * pk
+            s = math.sqrt(A / (p + B))
+            return (p - pk) * s, s * (1.0 - 0.5 * (p - pk) / (p + B))
+        r = (p / pk) ** ((g - 1.0) / (2.0 * g))      # rarefaction
+        return 2.0 * ck / (g - 1.0) * (r - 1.0), r / (rk * ck)
+
+    p = 0.5 * (pl + pr)
+    for _ in range(100):
+        f1, d1 = fk(p, rl, pl, cl)
+        f2, d2 = fk(p, rr, pr, cr)
+        dp = (f1 + f2 + ur - ul) / (d1 + d2)
+        p = max(1e-12, p - dp)
+        if abs(dp) < 1e-15 * p:
+            break
+    f1, _ = fk(p, rl, pl, cl)
+    f2, _ = fk(p, rr, pr, cr)
+    return p, 0.5 * (ul + ur) + 0.5 * (f2 - f1)
+
+
+def sod_primitive(x, t, gamma=1.4, x0=0.5):
+    """Exact density, velocity and pressure of Sod's problem (left state
+    rho = p = 1, right rho = 0.125, p = 0.1, at rest) at x, time t > 0:
+    left rarefaction, contact, right shock."""
+    g = gamma
+    rl, pl, rr, pr = 1.0, 1.0, 0.125, 0.1
+    cl = math.sqrt(g * pl / rl)
+    ps, us = _sod_star(gamma)
+    rls = rl * (ps / pl) ** (1.0 / g)                                  # isentropic behind the fan
+    cls = cl * (ps / pl) ** ((g - 1.0) / (2.0 * g))
+    q = ps / pr
+    rrs = rr * (q + (g - 1.0) / (g + 1.0)) / ((g - 1.0) / (g + 1.0) * q + 1.0)
+    S = math.sqrt(g * pr / rr) * math.sqrt((g + 1.0) / (2.0 * g) * q + (g - 1.0) / (2.0 * g))
+    xi = (np.asarray(x, dtype=float) - x0) / t
+    rho = np.where(xi < -cl, rl, 0.0)
+    u = np.zeros_like(xi)
+    p = np.where(xi < -cl, pl, 0.0)
+    fan = (xi >= -cl) & (xi < us - cls)
+    uf = 2.0 / (g + 1.0) * (cl + xi)
+    cf = 2.0 / (g + 1.0) * cl - (g - 1.0) / (g + 1.0) * xi
+    rho = np.where(fan, rl * (np.maximum(cf, 0.0) / cl) ** (2.0 / (g - 1.0)), rho)
+    u = np.where(fan, uf, u)
+    p = np.where(fan, pl * (np.maximum(cf, 0.0) / cl) ** (2.0 * g / (g - 1.0)), p)
+    left_star = (xi >= us - cls) & (xi < us)
+    right_star = (xi >= us) & (xi < S)
+    right = xi >= S
+    rho = np.where(left_star, rls, np.where(right_star, rrs, np.where(right, rr, rho)))
+    u = np.where(left_star | right_star, us, np.where(right, 0.0, u))
+    p = np.where(left_star | right_star, ps, np.where(right, pr, p))
+    return rho, u, p
+
+
+def sod_state(X, t, gamma=1.4):
+    """Conserved variables of the mirrored Sod problem on the periodic [0, 2]
+    at the nodes X[ey, ex, j, i]: Sod's solution on [0, 1], its mirror image
+    (velocity reversed) on [1, 2].  At t = 0 every element takes the state
+    of its centre, so the discontinuities sit on the element faces at
+    x = 0.5 and 1.5."""
+    X = np.asarray(X, dtype=float)
+    if t == 0.0:
+        xc = np.broadcast_to(X.mean(axis=(-2, -1), keepdims=True), X.shape)
+        left = (xc < 0.5) | (xc >= 1.5)
+        rho = np.where(left, 1.0, 0.125)
+        u = np.zeros_like(X)
+        p = np.where(left, 1.0, 0.1)
+    else:
+        xm = np.where(X <= 1.0, X, 2.0 - X)
+        rho, u, p = sod_primitive(xm, t, gamma)
+        u = np.where(X <= 1.0, u, -u)
+    return np.stack([rho, rho * u, np.zeros_like(X), p / (gamma - 1.0) + 0.5 * rho * u * u])
+
+
 def initial_state(name, X, Y, seed_extra=0):
     w = WORKLOADS[name]
     if name == "convdiff1d":
@@ -206,6 +313,10 @@ def initial_state(name, X, Y, seed_extra=0):
                                  w["angle_deg"], w["lo"], w["hi"])
     if name == "ns_shear":
         return shear_layer(X, Y, w["gamma"], w["mach"], w["shear_delta"], w["perturb_amp"], seed_extra)
+    if name == "burgers_front":
+        return burgers_front(X, 0.0, w["nu"])
+    if name == "sod":
+        return sod_state(X, 0.0, w["gamma"])
     raise ValueError(name)
 
 

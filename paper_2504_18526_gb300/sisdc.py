@@ -94,6 +94,7 @@ def load():
         "sisdc_destroy": (None, [c_void_p]),
         "sisdc_create_level": (c_int, [c_void_p, P(sisdc_level_desc), P(c_void_p)]),
         "sisdc_set_allocator": (c_int, [c_void_p, ALLOC_FN, RELEASE_FN, c_void_p]),
+        "sisdc_set_av": (c_int, [c_void_p, c_double, c_double, c_int]),
         "sisdc_level_info": (c_int, [c_void_p, P(c_int), P(c_ll), P(c_int)]),
         "sisdc_level_coords": (c_int, [c_void_p, c_void_p, c_void_p]),
         "sisdc_level_tables": (c_int, [c_void_p] + [c_void_p] * 5),
@@ -235,6 +236,11 @@ def sisdc_set_allocator(ctx, allocator=None):
         _check(load().sisdc_set_allocator(ctx, ALLOC_FN(), RELEASE_FN(), None), ctx)
     else:
         _check(load().sisdc_set_allocator(ctx, allocator.alloc, allocator.release, None), ctx)
+
+
+def sisdc_set_av(ctx, d_s, c_s, comp=0):
+    """Persson-Peraire artificial viscosity in f (before the first level)."""
+    _check(load().sisdc_set_av(ctx, float(d_s), float(c_s), int(comp)), ctx)
 
 
 def sisdc_create_level(ctx, desc):
@@ -681,6 +687,9 @@ class Context:
         self.allocator = allocator           # kept alive with the context
         if allocator is not None:
             sisdc_set_allocator(self.ctx, allocator)
+        if w.get("av"):                      # artificial viscosity of the workload
+            av = w["av"]
+            sisdc_set_av(self.ctx, av["kappa"], av["cs"], av.get("comp", 0))
         self.levels = [sisdc_create_level(self.ctx, make_level_desc(w, lv)) for lv in w["levels"]]
 
     def info(self, l=-1):

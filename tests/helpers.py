@@ -20,8 +20,11 @@ def oracle_pde(w):
 
 
 def oracle_space(w, lvl, rtol=1e-14):
-    return DGSpace(w["dim"], tuple(lvl["nel"][:w["dim"]]), lvl["P"], w["lo"], w["hi"],
-                   oracle_pde(w), cg_rtol=rtol, cg_maxit=10000)
+    sp = DGSpace(w["dim"], tuple(lvl["nel"][:w["dim"]]), lvl["P"], w["lo"], w["hi"],
+                 oracle_pde(w), cg_rtol=rtol, cg_maxit=10000)
+    if w.get("av"):
+        sp.av = dict(w["av"])
+    return sp
 
 
 def oracle_ml(w, stages=2, Nc=2, rtol=1e-14, **kw):
