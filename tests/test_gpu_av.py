@@ -154,10 +154,11 @@ def test_sod_full_size_parity(dev):
 
 
 def test_sod_32_steps_against_exact(dev):
-    """32 steps of MLSDC (3 V-cycles each) to t = 0.2: density within 1 % (L1
-    on [0, 1]) of the exact Riemann solution, no velocity overshoot beyond
-    5 % of u*, mass conserved to round-off (Rusanov, SIPG and the BR1
-    viscosity are all conservative)."""
+    """32 steps of MLSDC (3 V-cycles each) to t = 0.2: density within 5e-3 (L1
+    on [0, 1]) of the exact Riemann solution (the oracle reaches 1.95e-3), the
+    velocity overshoot at the shock below 15 % of u* (the oracle: 8.9 %), mass
+    conserved to round-off (Rusanov, SIPG and the BR1 viscosity are all
+    conservative)."""
     w = inputs.WORKLOADS["sod"]
     sp = oracle_space(w, w["levels"][-1])
     X, _ = sp.coords()
@@ -174,10 +175,10 @@ def test_sod_32_steps_against_exact(dev):
     half = np.broadcast_to(X <= 1.0, X.shape)
     rho_err = np.sum((sp.mass * np.abs(u[0] - ex[0]))[half]) / np.sum(sp.mass[None, None] * half)
     assert np.all(np.isfinite(u))
-    assert rho_err < 1e-2, rho_err
+    assert rho_err < 5e-3, rho_err
     ps, us = inputs._sod_star()
     v = u[1] / u[0]
-    assert v[half].max() < 1.05 * us
+    assert v[half].max() < 1.15 * us
     m0, m1 = np.sum(sp.mass * u0[0]), np.sum(sp.mass * u[0])
     assert abs(m1 - m0) < 1e-12 * m0
 
