@@ -47,6 +47,8 @@ enum PcgPrec : int { PCG_JACOBI = 0, PCG_FDS = 1 };
 
 cudaError_t launch_traces(const Geo& g, const double* u, double* tr, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+// out = M^-1 in per node (GLL mass), all components
+cudaError_t launch_minv(const Geo& g, const double* in, double* out, cudaStream_t s);
 // Grid size for the cooperative PCG kernel of this geometry (0 if unsupported).
 int pcg_grid(const Geo& g, int* block);
 cudaError_t launch_pcg(const PCGArgs& a, int grid, int block, cudaStream_t s);

@@ -520,6 +520,26 @@ static cudaError_t apply_impl(const ApplyArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// out = M^-1 in (the diagonal GLL mass of every node), for all components
+__global__ void k_minv(const Geo g, const double* __restrict__ in, double* __restrict__ out) {
+    const long long n = (long long)g.ncomp * g.N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(idx % g.q), j = t / g.nq, i = t - j * g.nq;
+        double mass = 0.5 * g.hx * g.w[i];
+        if (g.dim == 2) mass *= 0.5 * g.hy * g.w[j];
+        out[idx] = in[idx] / mass;
+    }
+}
+
+cudaError_t launch_minv(const Geo& g, const double* in, double* out, cudaStream_t s) {
+    const long long n = (long long)g.ncomp * g.N;
+    const long long want = (n + 255) / 256;
+    const unsigned grid = (unsigned)(want < 152LL * 32 ? (want > 0 ? want : 1) : 152LL * 32);
+    k_minv<<<grid, 256, 0, s>>>(g, in, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
 #define X(n) case n: return a.g.dim == 1 ? apply_impl<n, 1>(a, s) : apply_impl<n, 2>(a, s);
 #define X1(n) case n: return a.g.dim == 1 ? apply_impl<n, 1>(a, s) : cudaErrorInvalidValue;

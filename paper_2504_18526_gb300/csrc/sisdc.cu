@@ -1491,7 +1491,10 @@ sisdc_status sisdc_solve_learned(sisdc_level lv, sisdc_mlp mlp, double cval, con
             tr.add(R, 1.0);
             tr.add(AP, -alpha);
             k_lin(lv, R, tr);
-            nodal_residual_into(lv, x, rhs, cval, lv->tmpc);
+            // the network's input, the nodal residual rhs - (x - c L x), is M^-1 R
+            // of the recurrence residual: no operator application per iteration
+            check(c, launch_minv(lv->geo, R, lv->tmpc, c->stream), "mass scaling kernel");
+            c->launches++;
             st = sisdc_mlp_apply(mlp, lv->tmpc, cval, Z, 0);
             if (st != SISDC_OK) return fail(c, st, "MLP application failed");
             Terms td;
