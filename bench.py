@@ -716,17 +716,22 @@ def main_arm(args):
 def kernel_digest(files):
     """Short digest of the kernel sources and the workload definitions (ties
     a stored ncu traffic figure to the kernel version and the workload it was
-    measured on)."""
+    measured on).  An entry "ensemble_instances" stands for the ensemble's
+    instance draw (sizes, degrees, coefficients, time steps), not for a file."""
     import hashlib
     h = hashlib.sha256()
     for f in files:
+        if f == "ensemble_instances":
+            from paper_2504_18526_gb300 import inputs
+            h.update(json.dumps(inputs.ensemble_instances(), sort_keys=True).encode())
+            continue
         path = os.path.join(ROOT, "paper_2504_18526_gb300", f if f.endswith(".py") else os.path.join("csrc", f))
         with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-ENS_KERNEL_SOURCES = ("ens.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh", "inputs.py")
+ENS_KERNEL_SOURCES = ("ens.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh", "ensemble_instances")
 
 # DRAM traffic of the dominant ensemble launch (a fine-level correction sweep
 # of the P = 8 group, FP64 form): dram__bytes_read.sum + dram__bytes_write.sum
@@ -735,7 +740,7 @@ ENS_KERNEL_SOURCES = ("ens.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh", 
 # group's arrays exceed L2 in both cases), and the digest of the kernel
 # sources it was measured on; traffic is reported as null for any other
 # kernel version or form.
-ENS_TRAFFIC = {"digest": "8d9082ba56c91840", "bytes_per_node": 3655.0, "P": 8, "form": "fp64"}
+ENS_TRAFFIC = {"digest": "68180cecf2bbe356", "bytes_per_node": 7150.1, "P": 8, "form": "fp64"}
 
 
 def ens_cfg_apply(S, ens, cfg):
