@@ -60,6 +60,8 @@ def parse():
                     help="paper_convdiff: the error table, the CFL iteration study, or both")
     ap.add_argument("--cfls", type=float, nargs="*", default=[64, 32, 16, 8, 4, 2, 1],
                     help="paper_convdiff: CFL numbers of the iteration study")
+    ap.add_argument("--nus", type=float, nargs="*", default=None,
+                    help="paper_convdiff study: the viscosities to run (1e-3 and/or 0; default both)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-nel", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--shard", type=int, default=0, help=argparse.SUPPRESS)
@@ -1126,6 +1128,8 @@ def paper_convdiff_arm(args):
     study = {}
     for nu, nels, Ms in (((1e-3, (16, 32, 64), (3, 5, 7)), (0.0, (32, 64), (5, 7)))
                          if args.part in ("all", "study") else ()):
+        if args.nus is not None and nu not in args.nus:
+            continue
         for cfl in args.cfls:
             ml, sd = [], []
             for C in range(1, 13):
