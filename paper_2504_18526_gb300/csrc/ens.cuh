@@ -900,8 +900,12 @@ struct EnsSweeper {
     }
 };
 
-template <int NQ, bool MIX>
-__global__ void __launch_bounds__(512, 1) k_ens_sweep(const __grid_constant__ EnsArgs a) {
+// MINB = 1: up to 128 registers per thread (one 512-thread block per SM);
+// MINB = 2: at most 64 (two such blocks, or four of 256 threads, per SM) --
+// more resident warps to hide the FP64 and shared-memory latencies, fewer
+// registers per thread; the same arithmetic, so both give identical bits.
+template <int NQ, bool MIX, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_ens_sweep(const __grid_constant__ EnsArgs a) {
     EnsSweeper<NQ, MIX> s(a);
     if (a.mode == SW_REFRESH) s.refresh();
     else if (a.mode == SW_PREDICT) s.predict();
@@ -915,22 +919,23 @@ size_t ens_smem(int epb) {
 }
 
 // blocks per SM for a block of epb*Q threads (0 if it cannot run)
-template <int NQ, bool MIX>
+template <int NQ, bool MIX, int MINB = 1>
 int ens_occupancy_impl(int epb) {
     if (epb < 1 || epb * NQ * NQ > 512) return 0;
     const int bs = warp_round(epb * NQ * NQ);
     const size_t sh = ens_smem<NQ, MIX>(epb);
     // the attribute covers the largest tile, so that every shape stays launchable
     const size_t shmax = ens_smem<NQ, MIX>(512 / (NQ * NQ));
-    if (cudaFuncSetAttribute(k_ens_sweep<NQ, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax) !=
+    if (cudaFuncSetAttribute(k_ens_sweep<NQ, MIX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax) !=
         cudaSuccess)
         return 0;
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ens_sweep<NQ, MIX>, bs, sh) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ens_sweep<NQ, MIX, MINB>, bs, sh) != cudaSuccess)
+        return 0;
     return per;
 }
 
-template <int NQ, bool MIX>
+template <int NQ, bool MIX, int MINB = 1>
 cudaError_t ens_launch_impl(const EnsArgs& a, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -942,7 +947,7 @@ cudaError_t ens_launch_impl(const EnsArgs& a, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ens_sweep<NQ, MIX>, a);
+    return cudaLaunchKernelEx(&cfg, k_ens_sweep<NQ, MIX, MINB>, a);
 }
 
 }  // namespace sisdc

@@ -38,14 +38,25 @@ cudaError_t ens_launch_lo(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 cudaError_t ens_launch_hi(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 cudaError_t ens_launch_lo_mix(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 cudaError_t ens_launch_hi_mix(const EnsArgs& a, int nq, int grid, cudaStream_t s);
+int ens_occupancy_lo2(int nq, int epb);
+int ens_occupancy_hi2(int nq, int epb);
+cudaError_t ens_launch_lo2(const EnsArgs& a, int nq, int grid, cudaStream_t s);
+cudaError_t ens_launch_hi2(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 
 int ens_occupancy(int nq, int mix, int epb) {
     if (mix) return nq < 6 ? ens_occupancy_lo_mix(nq, epb) : ens_occupancy_hi_mix(nq, epb);
     return nq < 6 ? ens_occupancy_lo(nq, epb) : ens_occupancy_hi(nq, epb);
 }
 
-cudaError_t launch_ens_sweep(const EnsArgs& a, int nq, int mix, int grid, cudaStream_t s) {
+// blocks per SM of the register-capped FP64 variant (0: none for the mixed form)
+int ens_occupancy_capped(int nq, int mix, int epb) {
+    if (mix) return 0;
+    return nq < 6 ? ens_occupancy_lo2(nq, epb) : ens_occupancy_hi2(nq, epb);
+}
+
+cudaError_t launch_ens_sweep(const EnsArgs& a, int nq, int mix, int grid, cudaStream_t s, int capped) {
     if (mix) return nq < 6 ? ens_launch_lo_mix(a, nq, grid, s) : ens_launch_hi_mix(a, nq, grid, s);
+    if (capped) return nq < 6 ? ens_launch_lo2(a, nq, grid, s) : ens_launch_hi2(a, nq, grid, s);
     return nq < 6 ? ens_launch_lo(a, nq, grid, s) : ens_launch_hi(a, nq, grid, s);
 }
 
@@ -102,6 +113,7 @@ struct EnsLevel {
            *d_one = nullptr;
     // launch configuration
     int epb = 0, grid = 0, lmax = 0;
+    int capped = 0;             // 1: the register-capped kernel (more blocks per SM than the plain one holds)
     long long ntiles = 0;
     int4* d_tiles = nullptr;
     int* d_nloc = nullptr;
@@ -348,6 +360,8 @@ void configure(sisdc_ens_s* c, EnsLevel& L, int epb, int grid) {
     L.epb = epb;
     L.grid = grid;
     L.lmax = lmax;
+    // more co-resident blocks than the plain kernel holds: the register-capped one
+    L.capped = grid > ens_occupancy(L.nq, L.mix ? 1 : 0, epb) * c->nsm ? 1 : 0;
     L.ntiles = nt;
     // shared scratch large enough for this configuration
     const size_t np = (size_t)(2 * 4 * L.hinst.size() + 2) * grid;
@@ -438,7 +452,7 @@ void run_sweep(sisdc_ens_s* c, EnsGroup& g, int which, int mode, const double* G
         }
         check(c, cudaEventRecord(c->ev[c->ev_used], c->stream), "timing event");
     }
-    check(c, launch_ens_sweep(a, L.nq, L.mix ? 1 : 0, L.grid, c->stream), "ensemble sweep kernel");
+    check(c, launch_ens_sweep(a, L.nq, L.mix ? 1 : 0, L.grid, c->stream, L.capped), "ensemble sweep kernel");
     if (timed) {
         check(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream), "timing event");
         c->ev_used += 2;
@@ -873,7 +887,8 @@ sisdc_status sisdc_ens_autotune(sisdc_ens c, const double* u, int nsweeps, int* 
                 const int emax = std::max(1, 512 / L.Q);
                 for (int epb = emax; epb >= 1; epb = epb > 1 ? epb / 2 : 0) {
                     if (epb * L.Q < 32 && epb != emax) break;
-                    const int per = ens_occupancy(L.nq, L.mix ? 1 : 0, epb);
+                    const int per = std::max(ens_occupancy(L.nq, L.mix ? 1 : 0, epb),
+                                             ens_occupancy_capped(L.nq, L.mix ? 1 : 0, epb));
                     for (int b = 1; b <= per; b *= 2) cand.push_back({epb, b * c->nsm});
                     if (epb == 1) break;
                 }
@@ -939,7 +954,8 @@ sisdc_status sisdc_ens_set_tiles(sisdc_ens c, int group, int fine, int epb, int 
     if (epb * L.Q > 512) return fail(c, SISDC_E_ARG, "a tile holds at most 512 nodes");
     try {
         check(c, cudaStreamSynchronize(c->stream), "sync");
-        const int per = ens_occupancy(L.nq, L.mix ? 1 : 0, epb);
+        const int per = std::max(ens_occupancy(L.nq, L.mix ? 1 : 0, epb),
+                                 ens_occupancy_capped(L.nq, L.mix ? 1 : 0, epb));
         if (per < 1 || grid > per * c->nsm) return fail(c, SISDC_E_ARG, "grid exceeds the co-resident blocks");
         configure(c, L, epb, grid);
         L.valid = false;
