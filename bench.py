@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="8x8 elements (profiling case)")
     ap.add_argument("--ninst", type=int, default=0, help="ensemble: first N instances only (profiling case)")
     ap.add_argument("--no-autotune", action="store_true", help="default tile shapes (no sisdc_autotune)")
+    ap.add_argument("--capped", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--per-instance", type=int, default=0,
                     help="ensemble: also time this many sampled instances stepped one by one (single-problem path)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
@@ -806,6 +807,14 @@ def ensemble_arm(args):
 
     u0_host = exact_field(lambda d: 0.0)
     u0 = torch.from_numpy(u0_host).to(dev)
+    if args.no_autotune and args.capped:
+        # profiling case: every level with its largest tile and two blocks per SM
+        # (the register-capped kernel of the FP64 form)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        for g in range(S.sisdc_ens_num_groups(E.ens)):
+            for fine in (0, 1):
+                P = int(S.sisdc_ens_config(E.ens)[2 * g + (0 if fine else 1)][1])   # rows: fine, coarse
+                S.sisdc_ens_set_tiles(E.ens, g, fine, max(1, 512 // ((P + 1) ** 2)), 2 * nsm)
     cfg = S.sisdc_ens_config(E.ens) if args.no_autotune else S.sisdc_ens_autotune(E.ens, u0, 1)
     u = u0.clone()
     S.sisdc_ens_step(E.ens, u, args.warmup)
