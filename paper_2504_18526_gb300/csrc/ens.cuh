@@ -903,7 +903,10 @@ struct EnsSweeper {
 // MINB = 1: up to 128 registers per thread (one 512-thread block per SM);
 // MINB = 2: at most 64 (two such blocks, or four of 256 threads, per SM) --
 // more resident warps to hide the FP64 and shared-memory latencies, fewer
-// registers per thread; the same arithmetic, so both give identical bits.
+// registers per thread.  The same arithmetic per thread; the host picks the
+// capped kernel when a level's grid has more blocks than the plain kernel
+// keeps resident (the tile-to-block assignment, and with it the order of the
+// per-instance partial sums, follows the grid).
 template <int NQ, bool MIX, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_ens_sweep(const __grid_constant__ EnsArgs a) {
     EnsSweeper<NQ, MIX> s(a);

@@ -40,21 +40,26 @@ cudaError_t ens_launch_lo_mix(const EnsArgs& a, int nq, int grid, cudaStream_t s
 cudaError_t ens_launch_hi_mix(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 int ens_occupancy_lo2(int nq, int epb);
 int ens_occupancy_hi2(int nq, int epb);
+int ens_occupancy_lo_mix2(int nq, int epb);
+int ens_occupancy_hi_mix2(int nq, int epb);
 cudaError_t ens_launch_lo2(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 cudaError_t ens_launch_hi2(const EnsArgs& a, int nq, int grid, cudaStream_t s);
+cudaError_t ens_launch_lo_mix2(const EnsArgs& a, int nq, int grid, cudaStream_t s);
+cudaError_t ens_launch_hi_mix2(const EnsArgs& a, int nq, int grid, cudaStream_t s);
 
 int ens_occupancy(int nq, int mix, int epb) {
     if (mix) return nq < 6 ? ens_occupancy_lo_mix(nq, epb) : ens_occupancy_hi_mix(nq, epb);
     return nq < 6 ? ens_occupancy_lo(nq, epb) : ens_occupancy_hi(nq, epb);
 }
 
-// blocks per SM of the register-capped FP64 variant (0: none for the mixed form)
+// blocks per SM of the register-capped variant
 int ens_occupancy_capped(int nq, int mix, int epb) {
-    if (mix) return 0;
+    if (mix) return nq < 6 ? ens_occupancy_lo_mix2(nq, epb) : ens_occupancy_hi_mix2(nq, epb);
     return nq < 6 ? ens_occupancy_lo2(nq, epb) : ens_occupancy_hi2(nq, epb);
 }
 
 cudaError_t launch_ens_sweep(const EnsArgs& a, int nq, int mix, int grid, cudaStream_t s, int capped) {
+    if (mix && capped) return nq < 6 ? ens_launch_lo_mix2(a, nq, grid, s) : ens_launch_hi_mix2(a, nq, grid, s);
     if (mix) return nq < 6 ? ens_launch_lo_mix(a, nq, grid, s) : ens_launch_hi_mix(a, nq, grid, s);
     if (capped) return nq < 6 ? ens_launch_lo2(a, nq, grid, s) : ens_launch_hi2(a, nq, grid, s);
     return nq < 6 ? ens_launch_lo(a, nq, grid, s) : ens_launch_hi(a, nq, grid, s);

@@ -250,7 +250,7 @@ struct EnsArgs {
 };
 // blocks per SM of the ensemble kernel for tiles of epb elements (0: unavailable)
 int ens_occupancy(int nq, int mix, int epb);
-// the same for the FP64 kernel compiled for at most 64 registers per thread
+// the same for the kernel compiled for at most 64 registers per thread
 int ens_occupancy_capped(int nq, int mix, int epb);
 cudaError_t launch_ens_sweep(const EnsArgs& a, int nq, int mix, int grid, cudaStream_t s, int capped);
 
