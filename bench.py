@@ -737,13 +737,15 @@ def kernel_digest(files):
 ENS_KERNEL_SOURCES = ("ens.cuh", "sipg.cuh", "pde.cuh", "common.cuh", "ds.cuh", "ensemble_instances")
 
 # DRAM traffic of the dominant ensemble launch (a fine-level correction sweep
-# of the P = 8 group, FP64 form): dram__bytes_read.sum + dram__bytes_write.sum
+# of the P = 8 group, FP64 form, the register-capped kernel with tiles of 6
+# elements on two blocks per SM, the autotuner's pick):
+# dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu capture of that launch on the first 96 instances of the draw,
 # per fine node of the group (the traffic grows with the group's nodes: the
 # group's arrays exceed L2 in both cases), and the digest of the kernel
 # sources it was measured on; traffic is reported as null for any other
 # kernel version or form.
-ENS_TRAFFIC = {"digest": "68180cecf2bbe356", "bytes_per_node": 7150.1, "P": 8, "form": "fp64"}
+ENS_TRAFFIC = {"digest": "0c0a871f4df879fd", "bytes_per_node": 7258.4, "P": 8, "form": "fp64"}
 
 
 def ens_cfg_apply(S, ens, cfg):
