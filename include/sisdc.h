@@ -506,7 +506,8 @@ sisdc_status sisdc_ens_step(sisdc_ens ens, double* d_u, int nsteps);
 
 /* Tile-shape autotuner: for every level of every degree group, times
  * `nsweeps` correction sweeps from the state d_u (spread over the nodes) for
- * each candidate (elements per tile, blocks per SM) and keeps the fastest.
+ * each candidate (elements per tile, blocks per SM, including the
+ * register-capped build's larger block counts) and keeps the fastest.
  * d_u is not modified.  h_config (nullable) receives the result as for
  * sisdc_ens_config.  Synchronous. */
 sisdc_status sisdc_ens_autotune(sisdc_ens ens, const double* d_u, int nsweeps, int* h_config);
@@ -518,7 +519,12 @@ int sisdc_ens_num_groups(sisdc_ens ens);
 /* Set the tile shape of one level (fine != 0: fine level) of group `group`
  * (groups in increasing degree): epb elements per tile (epb (P+1)^2 <= 512
  * threads), `grid` persistent blocks (at most the co-resident count; fewer
- * when the level has fewer tiles).  Synchronous. */
+ * when the level has fewer tiles).  Each kernel is built twice: for up to 128
+ * registers per thread and capped at 64; a grid with more blocks than the
+ * first build keeps resident on the SMs runs the capped build (the
+ * co-resident count above is the larger of the two).  The order of the
+ * per-instance partial sums follows the grid, so results of different grids
+ * agree to rounding.  Synchronous. */
 sisdc_status sisdc_ens_set_tiles(sisdc_ens ens, int group, int fine, int epb, int grid);
 
 /* Synchronise and report device error flags (as sisdc_sync). */
