@@ -108,3 +108,14 @@ def test_kernel_digest_tracks_sources():
     d1 = bench.kernel_digest(bench.ENS_KERNEL_SOURCES)
     assert d1 == bench.kernel_digest(bench.ENS_KERNEL_SOURCES) and len(d1) == 16
     assert d1 != bench.kernel_digest(bench.SWEEP_KERNEL_SOURCES)
+
+
+def test_burgers_front_variants_are_valid_level_lists():
+    """Every variant of the shock-capturing arm's front table: levels coarse to
+    fine, element grids equal or 2:1, degrees and node counts non-decreasing,
+    the finest level the paper's 40 elements of degree 8 with 7 nodes."""
+    for name, levels, start in bench.BURGERS_FRONT_VARIANTS:
+        assert levels[-1] == (40, 8, 7), name
+        assert (start is None) == (len(levels) == 1), name
+        for (n0, p0, m0), (n1, p1, m1) in zip(levels, levels[1:]):
+            assert n1 in (n0, 2 * n0) and p1 >= p0 and m1 >= m0, name
