@@ -22,6 +22,10 @@ mlsdc      space-time transfers, FAS right-hand side, V-cycle, Cascade and
 dahlquist  the scalar Fourier-mode problem of Sec. 5 driven through the same
            sdc/mlsdc code (stability function R(z))
 mlp        FP64 reference of the element-patch MLP (forward/backward)
+fds        element-wise fast-diagonalisation preconditioner (Sec. 8's fast
+           diagonalisation solver, element-local reading)
+av         Persson-Peraire artificial viscosity added to f (Sec. 6; the form
+           follows the stated readings)
 
 Parity status of every function is listed in the module docstrings.
 """
