@@ -232,3 +232,33 @@ def test_burgers_front_solves_the_momentum_equation():
     uxx = (u(x + h, t) - 2 * u(x, t) + u(x - h, t)) / h ** 2
     assert np.max(np.abs(ut + fx - nu * uxx)) < 1e-3 * np.max(np.abs(ut))
     assert u(np.array([-1.0]), 0.0)[0] == pytest.approx(1.0) and u(np.array([1.0]), 0.0)[0] == pytest.approx(0.0)
+
+
+def test_mlsdc_with_viscosity_converges_to_its_collocation_solution():
+    """The viscosity is part of f: V-cycles of the front set-up (2:1
+    h-coarsening, FMG_1 start, viscosity switched on by the steep front) drive
+    the fine collocation residual F^nn(U) = U_m - U_{m-1} - dt S f(U), f with
+    the viscosity term, towards zero (slowly: the scalar nu_tilde carries the
+    viscosity's largest value into the smooth elements too); without the term
+    in the sweeps' f (a planted slip) the iteration settles at a residual of
+    the size of the term."""
+    from oracle.sdc import Fnn
+    from tests.helpers import oracle_ml
+    w = inputs.scaled("burgers_front", levels=[dict(nel=(4, 1), P=4, M=3), dict(nel=(8, 1), P=4, M=3)])
+    ml = oracle_ml(w, rtol=1e-14)
+    fine = ml.levels[-1]
+    X, _ = fine.space.coords()
+    u0 = inputs.burgers_front(X, 0.0, w["nu"])
+    assert av.viscosity(fine.space, u0, **w["av"]).max() > 0.0
+    dt = 0.002
+    res = []
+    for nc in (4, 24):
+        _, Us = ml.step(u0, dt, nc, start="fmg1", return_levels=True)
+        res.append(np.max(np.abs(Fnn(fine, u0, Us[-1], dt))))
+    assert res[1] < 1e-7 and res[1] < res[0] / 1000.0
+    for lv in ml.levels:                                   # planted: f without the viscosity in the sweeps
+        lv.space.av = None
+    _, Us2 = ml.step(u0, dt, 24, start="fmg1", return_levels=True)
+    for lv in ml.levels:
+        lv.space.av = dict(w["av"])
+    assert np.max(np.abs(Fnn(fine, u0, Us2[-1], dt))) > 1e-3
